@@ -1,0 +1,248 @@
+"""Pins of the FP64 oracle to facts fixed by the paper and by mathematics.
+
+None of these re-types the oracle's formulas: the references are explicit
+constraint matrices built from problem (original), an exact active-set NNLS
+solve of the dual of (regularize), closed forms, and the inequalities of the
+paper's theorems.  CPU only.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1407_7220_gb300 import datagen
+from tests import dense_qp as D
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def _inst(N=20, n=2, seed=7, recipe="sq2"):
+    X, yb, _ = datagen.make(recipe, N=N, n=n, seed=seed)
+    return X, yb
+
+
+# --------------------------------------------------------------------------
+# Step 1 closed form (Fig. 2 step 1, K = N) against the explicit Lagrangian
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("N,n", [(7, 3), (9, 1), (6, 5)])
+def test_step1_matches_explicit_lagrangian_minimizer(N, n):
+    rng = np.random.default_rng(N * 10 + n)
+    X = rng.normal(size=(N, n))
+    h = rng.normal(size=N) + 3.0
+    gamma = 0.37
+    T = rng.exponential(size=(N, N))
+    np.fill_diagonal(T, 0.0)
+    mu = rng.exponential(size=N)
+    y, xi = O.eta(T, mu, X, h, gamma)
+    # minimizer of 1/2||y-h||^2 + gamma/2||xi||^2 - theta^T C eta: H eta = htil + C^T theta
+    _, eta = D.dense_dual(X, h, gamma, T, mu)
+    np.testing.assert_allclose(y, eta[:N], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(xi.ravel(), eta[N:], rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("N,n", [(7, 3), (8, 2)])
+def test_residual_matches_explicit_constraint_rows(N, n):
+    rng = np.random.default_rng(5)
+    X = rng.normal(size=(N, n))
+    y = rng.normal(size=N)
+    xi = rng.normal(size=(N, n))
+    G = O.residual(y, xi, X)
+    A1, A2, pairs = D.constraint_matrices(X)
+    Gd = A1 @ y + A2 @ xi.ravel()
+    for v, (l1, l2) in zip(Gd, pairs):
+        assert abs(G[l1, l2] - v) < 1e-12
+    assert np.all(np.diag(G) == 0.0)
+
+
+# --------------------------------------------------------------------------
+# Lipschitz constant, Eq. (eq:lischitz)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("N,n,gamma", [(8, 2, 0.5), (10, 3, 1.0), (6, 1, 0.05)])
+def test_lipschitz_bound_dominates_true_constant(N, n, gamma):
+    rng = np.random.default_rng(N + n)
+    X = rng.uniform(-1, 1, size=(N, n))
+    L = O.lipschitz(X, gamma)
+    C, _ = D.big_C(X)
+    smax2 = np.linalg.norm(C, 2) ** 2
+    Hinv = np.concatenate([np.ones(N), np.full(N * n, 1.0 / gamma)])
+    lam = np.linalg.eigvalsh((C * Hinv) @ C.T)[-1]  # Lipschitz constant of grad g_gamma
+    assert L >= lam * (1 - 1e-12)
+    if gamma <= 1.0:
+        assert L * gamma >= smax2 * (1 - 1e-12)  # L_g = sigma_max(C)^2 / gamma is dominated
+    # the bound is the sum 1 + ||A_1||^2 + ||A_2||^2: each term exact
+    A1, A2, _ = D.constraint_matrices(X)
+    a1 = np.linalg.norm(A1, 2) ** 2
+    a2 = np.linalg.norm(A2, 2) ** 2
+    assert abs(a1 - 2 * N) < 1e-9 * N
+    np.testing.assert_allclose(L * gamma, 1 + a1 + a2, rtol=1e-10)
+
+
+# --------------------------------------------------------------------------
+# N = 2, n = 1: closed form of (regularize)
+# --------------------------------------------------------------------------
+def test_two_points_closed_form():
+    # For x_1 < x_2, gap D = x_2 - x_1, the optimal slopes are xi_1 = min(0, d/D),
+    # xi_2 = max(0, d/D) with d = y_2 - y_1, so (regularize) reduces to
+    # min 1/2(y1-yb1)^2 + 1/2(y2-yb2)^2 + gamma/2 d^2/D^2, solved by
+    # d = (yb2 - yb1) / (1 + 2 gamma / D^2) and y1 + y2 = yb1 + yb2.
+    for yb, gamma in (([0.3, 1.1], 0.2), ([1.0, -0.5], 0.05)):
+        X = np.array([[-0.4], [0.6]])
+        yb = np.array(yb)
+        Dx = 1.0
+        d = (yb[1] - yb[0]) / (1 + 2 * gamma / Dx ** 2)
+        m = yb.mean()
+        y_ref = np.array([m - d / 2, m + d / 2])
+        xi_ref = np.array([min(0.0, d / Dx), max(0.0, d / Dx)])
+        s = O.Solver(X, yb, gamma=gamma, restart=True)
+        s.solve(1e-13, 200000, check_every=10)
+        np.testing.assert_allclose(s.y_hat, y_ref, rtol=0, atol=1e-10)
+        np.testing.assert_allclose(s.xi[:, 0], xi_ref, rtol=0, atol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# Brute force: exact dual NNLS at N = 20 (recipe (1))
+# --------------------------------------------------------------------------
+def _nnls_reference(X, yb, gamma):
+    s = O.shift(yb)
+    y, xi, T, dual = D.solve_regularized_nnls(X, yb + s, gamma)
+    # the NNLS point is itself checked through the explicit matrices:
+    A1, A2, pairs = D.constraint_matrices(X)
+    g = A1 @ y + A2 @ xi.ravel()
+    th = D.theta_vec(T, pairs)
+    scale = max(1.0, np.ptp(yb))
+    assert g.min() >= -1e-9 * scale            # primal feasibility
+    assert th.min() >= 0.0                      # dual feasibility
+    assert np.abs(th * g).max() <= 1e-9 * scale ** 2  # complementary slackness
+    assert y.min() > 0.0                        # the shifted y >= 0 rows are inactive
+    return y - s, xi, T, dual, s
+
+
+@pytest.mark.parametrize("gamma,restart,n", [(0.1, True, 2), (0.01, True, 2), (0.1, False, 2), (0.05, True, 1),
+                                             (0.1, True, 3)])
+def test_oracle_converges_to_nnls_bruteforce(gamma, restart, n):
+    X, yb = _inst(N=20, n=n, seed=11)
+    y_ref, xi_ref, _, _, _ = _nnls_reference(X, yb, gamma)
+    s = O.Solver(X, yb, gamma=gamma, restart=restart)
+    k = s.solve(1e-11, 3_000_000, check_every=100)
+    assert s.metrics["kkt"] <= 1e-11, (k, s.metrics)
+    assert s.mu1.max() == 0.0                   # y >= 0 rows inactive after the shift
+    rel = np.abs(s.y_hat - y_ref).max() / np.abs(y_ref).max()
+    assert rel <= 1e-8, rel
+    np.testing.assert_allclose(s.xi, xi_ref, rtol=0, atol=1e-6 * max(1.0, np.abs(xi_ref).max()))
+
+
+# --------------------------------------------------------------------------
+# Invariants at every iteration
+# --------------------------------------------------------------------------
+def test_invariants_every_iteration():
+    X, yb = _inst(N=15, n=2, seed=3)
+    s = O.Solver(X, yb, gamma=0.1)
+    for _ in range(60):
+        s.iterate(1)
+        m = s.metrics
+        T = s.theta1
+        # sum_l (A_1^T theta)_l = 0 because every row of A_1 sums to zero
+        assert abs(m["sum_check"]) <= 1e-12 * max(1.0, T.sum())
+        assert T.min() >= 0.0 and s.mu1.min() >= 0.0
+        assert np.all(np.diag(T) == 0.0) and np.all(np.diag(s.theta2) == 0.0)
+        # metrics agree with the explicit-matrix definitions
+        A1, A2, pairs = D.constraint_matrices(X)
+        g = A1 @ s.y_shifted + A2 @ s.xi.ravel()
+        npairs = len(pairs)
+        viol = np.concatenate([np.minimum(g, 0.0), np.minimum(s.y_shifted, 0.0)])
+        assert abs(m["infeas"] - np.linalg.norm(viol) / np.sqrt(npairs)) <= 1e-12
+        th = np.concatenate([D.theta_vec(T, pairs), s.mu1])
+        gap = th @ np.concatenate([g, s.y_shifted])
+        assert abs(m["gap"] - gap / npairs) <= 1e-12 * max(1.0, abs(gap))
+        dd, _ = D.dense_dual(X, s.h, s.gamma, T, s.mu1)
+        assert abs(m["dual"] - dd) <= 1e-10 * max(1.0, abs(dd))
+
+
+# --------------------------------------------------------------------------
+# Convergence behaviour the paper states
+# --------------------------------------------------------------------------
+def test_dual_gradient_ascent_is_monotone():
+    # momentum = 0 is the paper's comparator (dual gradient ascent, Sec. III);
+    # with step 1/L on an L-smooth concave function the dual value never decreases.
+    X, yb = _inst(N=15, n=2, seed=4)
+    s = O.Solver(X, yb, gamma=0.05, momentum=False)
+    prev = -np.inf
+    for _ in range(300):
+        s.iterate(1)
+        d = s.metrics["dual"]
+        assert d >= prev - 1e-12 * abs(d)
+        prev = d
+
+
+@pytest.mark.parametrize("gamma", [0.1, 0.02])
+def test_apg_rate_and_theorem1_bounds(gamma):
+    # Sec. II-D: rho* - rho(eta_l) <= 2 L ||eta_0 - eta*||^2 / (l + 1)^2 (eta_0 = 0 here);
+    # Theorem 1: ||(A_1 y_d + A_2 xi_d)_-||_2 <= sqrt(2 delta / gamma) sigma_max(C).
+    X, yb = _inst(N=12, n=2, seed=9)
+    s = O.Solver(X, yb, gamma=gamma)
+    _, _, Tstar, _, _ = _nnls_reference(X, yb, gamma)
+    dstar, _ = D.dense_dual(X, s.h, gamma, Tstar, np.zeros(12))
+    C, pairs = D.big_C(X)
+    smax = np.linalg.norm(C, 2)
+    A1, A2, _ = D.constraint_matrices(X)
+    nrm2 = np.sum(Tstar ** 2)
+    for ell in range(1, 400):
+        s.iterate(1)
+        m = s.metrics
+        delta = dstar - m["dual"]
+        assert delta >= -1e-10 * abs(dstar)
+        assert delta <= 2 * s.L * nrm2 / (ell + 1) ** 2 * (1 + 1e-9) + 1e-12
+        g = A1 @ s.y_shifted + A2 @ s.xi.ravel()
+        infeas = np.linalg.norm(np.minimum(g, 0.0))
+        assert infeas <= np.sqrt(2 * max(delta, 0.0) / gamma) * smax * (1 + 1e-9) + 1e-12
+
+
+def test_unique_fitted_values_from_any_start():
+    # y* is unique for N >= n + 1 (after problem (original)); at gamma > 0 the
+    # strongly convex (regularize) has a unique (y, xi) even though theta* is not unique.
+    X, yb = _inst(N=14, n=2, seed=12)
+    a = O.Solver(X, yb, gamma=0.1, restart=True)
+    a.solve(1e-11, 3_000_000, check_every=100)
+    rng = np.random.default_rng(0)
+    th0 = rng.exponential(0.3, size=(14, 14))
+    b = O.Solver(X, yb, gamma=0.1, restart=True, theta0=th0)
+    b.solve(1e-11, 3_000_000, check_every=100)
+    assert not np.allclose(a.theta1, b.theta1, atol=1e-6)  # different dual points ...
+    np.testing.assert_allclose(a.y_hat, b.y_hat, rtol=0, atol=1e-8)  # ... same fit
+
+
+def test_shift_is_exact():
+    # A_1 1 = 0, so shifting ybar by any constant changes y by the same constant
+    # and leaves the fitted values unchanged.
+    X, yb = _inst(N=12, n=2, seed=2)
+    a = O.Solver(X, yb, gamma=0.1, restart=True)
+    a.solve(1e-11, 2_000_000, check_every=100)
+    b = O.Solver(X, yb, gamma=0.1, restart=True, s=O.shift(yb) + 3.25)
+    b.solve(1e-11, 2_000_000, check_every=100)
+    np.testing.assert_allclose(a.y_hat, b.y_hat, rtol=0, atol=1e-8)
+
+
+def test_restart_and_plain_papg_same_limit():
+    X, yb = _inst(N=16, n=2, seed=21)
+    a = O.Solver(X, yb, gamma=0.1, restart=False)
+    a.solve(1e-11, 3_000_000, check_every=100)
+    b = O.Solver(X, yb, gamma=0.1, restart=True)
+    b.solve(1e-11, 3_000_000, check_every=100)
+    np.testing.assert_allclose(a.y_hat, b.y_hat, rtol=0, atol=1e-8)
+
+
+def test_planted_sign_error_is_caught():
+    # A mistake planted in an explicit-matrix copy (the sign of the xi term)
+    # must disagree with the oracle's Step 1 -- this shows the explicit-matrix
+    # pin can see such a mistake.
+    rng = np.random.default_rng(1)
+    N, n = 6, 2
+    X = rng.normal(size=(N, n))
+    h = rng.normal(size=N)
+    T = rng.exponential(size=(N, N))
+    np.fill_diagonal(T, 0)
+    mu = np.zeros(N)
+    y, xi = O.eta(T, mu, X, h, 0.5)
+    A1, A2, pairs = D.constraint_matrices(X)
+    th = D.theta_vec(T, pairs)
+    bad_xi = (-A2.T @ th) / 0.5
+    assert np.abs(bad_xi - xi.ravel()).max() > 1e-3
