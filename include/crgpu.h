@@ -1,0 +1,162 @@
+/*
+ * crgpu.h -- C ABI of the GB300 P-APG convex-regression solver.
+ *
+ * Method: Aybat & Wang, "A Parallel Method for Large Scale Convex Regression
+ * Problems" (arXiv:1407.7220).  The library solves problem (regularize)
+ * (Sec. II-C)
+ *
+ *     min_{y in R^N, xi in R^{N x n}}  1/2 ||y - ybar||^2 + gamma/2 ||xi||^2
+ *     s.t.  y_{l1} - y_{l2} - xi_{l2}^T (x_{l1} - x_{l2}) >= 0   for all l1 != l2,
+ *
+ * by P-APG (Fig. 2) on its dual (lambda_dual) with every one of the N(N-1)
+ * pairwise constraints dualized (the partition of Sec. II-A taken to
+ * singletons, K = N).  Step 1 of P-APG then has a closed form (the "fold"),
+ * Step 2 is the projected update of the N x N multiplier array, and Steps 3-4
+ * are the momentum of Fig. 2.  The y >= 0 rows of C (Eq. (eq:C)) are kept and
+ * made inactive by the shift of the observations described after
+ * Eq. (omega_primal).
+ *
+ * Conventions for every entry point:
+ *  - Host pointers are plain C arrays; "device" pointers are CUDA device
+ *    addresses on the handle's device.  Matrices are row-major.
+ *  - X is N x n (row l = x_l), ybar has N entries.
+ *  - The library copies every input; outputs go to caller-owned buffers.
+ *  - No C++ exception crosses this boundary.  Every call returns a cr_status;
+ *    on failure cr_last_error(h) returns a message (per handle).
+ *  - A handle is used by one host thread at a time.  Work is enqueued on the
+ *    handle's stream (cr_options.stream, or a stream the library creates).
+ *  - There is no CPU fallback: without a usable sm_103a device every call
+ *    that needs one returns CR_ECUDA.
+ */
+#ifndef CRGPU_H
+#define CRGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cr_ctx *cr_handle;
+
+typedef enum {
+    CR_OK = 0,
+    CR_NOT_CONVERGED = 1, /* cr_solve reached max_iter (not an error) */
+    CR_EINVAL = -1,       /* invalid argument (sizes, gamma <= 0, non-finite input, N < n + 1) */
+    CR_ENOMEM = -2,       /* device or host allocation failed */
+    CR_ECUDA = -3,        /* CUDA runtime error (message in cr_last_error) */
+    CR_ETIMEOUT = -4,     /* a bounded device-side wait gave up; the handle must be reset */
+    CR_ENUMERIC = -5,     /* a non-finite value appeared in the iteration */
+    CR_ESTATE = -6        /* call not valid in the handle's current state */
+} cr_status;
+
+/* Storage type of the multiplier array theta (math is FP32 in every case). */
+enum { CR_THETA_F32 = 0, CR_THETA_BF16 = 1, CR_THETA_F16 = 2 };
+
+/* Iteration driver. */
+enum {
+    CR_DRIVER_AUTO = 0,       /* persistent if the cooperative launch fits, else phase kernels */
+    CR_DRIVER_PERSISTENT = 1, /* one cooperative launch runs many iterations (bounded grid barriers) */
+    CR_DRIVER_PHASES = 2      /* one kernel launch per phase per iteration */
+};
+
+typedef struct {
+    double gamma;   /* Tikhonov parameter of (regularize), > 0.  The paper gives no value; default 1e-2 */
+    double L;       /* step constant L_g of Eq. (eq:lischitz); <= 0: the closed-form bound
+                       (1 + 2N + max_l lambda_max(sum_m (x_m-x_l)(x_m-x_l)^T)) / gamma */
+    double shift;   /* observation shift s (after Eq. (omega_primal)); < 0: max(0,-min ybar) + range(ybar) */
+    int32_t theta_dtype;      /* CR_THETA_F32 / _BF16 / _F16 */
+    int32_t stochastic_round; /* 1: unbiased stochastic rounding of every theta store (counter-based hash) */
+    int32_t kkt_every;        /* cr_solve evaluates the KKT residual every this many iterations (>= 1) */
+    int32_t momentum;         /* 1: P-APG (Fig. 2); 0: dual gradient ascent (the paper's comparator, Sec. III) */
+    int32_t restart;          /* NOT IN THE PAPER. 1: reset the momentum (t <- 1) when the dual value decreases */
+    int32_t driver;           /* CR_DRIVER_* */
+    int32_t grid;             /* CTAs used by the pair pass; 0 = tuned per device and size */
+    int32_t fp16_exponent;    /* CR_THETA_F16 only: theta is stored as theta * 2^fp16_exponent */
+    uint64_t seed;            /* seed of the stochastic-rounding hash */
+    void *stream;             /* cudaStream_t; NULL = a stream owned by the handle */
+    int32_t barrier_timeout_ms; /* bound of every device-side grid-barrier wait; 0 = 4000 ms.  A wait
+                                   that runs out sets an error word, every CTA returns, and the call
+                                   reports CR_ETIMEOUT (the context stays usable; cr_reset recovers) */
+    int32_t test_barrier_extra; /* test hook, 0 in use: barriers wait for this many extra arrivals
+                                   that never come, so the bounded wait runs out on purpose */
+    int32_t profile;          /* 1: record CUDA events around every kernel launch (see cr_profile) */
+    int32_t reserved[5];
+} cr_options;
+
+/* Fills *opt with the defaults documented above. */
+void cr_options_default(cr_options *opt);
+
+/* Creates a solver for one instance.  X: host, N x n row-major FP64; ybar: host, N FP64.
+ * opt may be NULL (defaults).  Requires n >= 1, N >= n + 1 (uniqueness of y*, stated after
+ * problem (original)) and finite inputs, else CR_EINVAL.  The state is Iteration 0 of Fig. 2
+ * (theta^(1)_0 = theta^(2)_1 = 0, t_1 = 1).  Device memory: two N x ceil16(N) theta arrays of
+ * the chosen dtype plus O(N n) vectors and O(N^2/32) partial sums. */
+cr_status cr_create(const double *X, const double *ybar, int64_t N, int32_t n, const cr_options *opt,
+                    cr_handle *out);
+
+/* Same as cr_create with device-resident FP32 inputs (e.g. torch tensors), copied on the
+ * handle's stream. */
+cr_status cr_create_device(const float *dX, const float *dybar, int64_t N, int32_t n,
+                           const cr_options *opt, cr_handle *out);
+
+/* Returns the handle to Iteration 0 of Fig. 2 (theta = 0, t = 1). */
+cr_status cr_reset(cr_handle h);
+
+/* Enqueues k iterations of P-APG (Fig. 2, steps 1-4) on the handle's stream and returns
+ * without waiting.  Each iteration streams the multiplier array once (read theta^(1)_l,
+ * theta^(1)_{l-1}; write theta^(1)_{l+1}). */
+cr_status cr_iterate(cr_handle h, int64_t k);
+
+/* Runs iterations until the KKT residual (see cr_kkt_residual) at the current dual iterate
+ * is <= tol -- checked every kkt_every iterations with an FP32 screen and confirmed in FP64 --
+ * or until max_iter more iterations.  Blocks.  *iters_done (nullable) receives the iterations
+ * run by this call.  Returns CR_OK on convergence, CR_NOT_CONVERGED at max_iter. */
+cr_status cr_solve(cr_handle h, double tol, int64_t max_iter, int64_t *iters_done);
+
+/* FP64 objective values at the current dual iterate theta^(1)_l and its minimizer
+ * eta = (y, xi) (Step 1 map):  primal = 1/2||y - ybar||^2 + gamma/2||xi||^2,
+ * dual = g_gamma(theta) (Eq. (eq:g_gamma)), gap = primal - dual = theta^T C eta
+ * (the paper's duality gap, Sec. III).  Any pointer may be NULL.  Blocks. */
+cr_status cr_objective(cr_handle h, double *primal, double *dual, double *gap);
+
+/* FP64 KKT residual at the current dual iterate (Sec. III metrics plus the reading used by
+ * this library): with sigma = max(1, max ybar - min ybar) and g_p = (C eta)_p,
+ *   pri  = max(max_p (-g_p)_+, max_l (-y_l)_+) / sigma
+ *   comp = max(max_p theta_p |g_p|, max_l mu_l |y_l|) / sigma^2
+ *   kkt  = max(pri, comp)           (stationarity holds exactly by the closed form)
+ *   infeas_norm = ||(A_1 y + A_2 xi)_-||_2 / sqrt(N^2 - N)    (Sec. III)
+ *   gap_norm    = theta^T C eta / (N^2 - N)                    (Sec. III)
+ * Every per-pair term is evaluated in FP64.  Any pointer may be NULL.  Blocks. */
+cr_status cr_kkt_residual(cr_handle h, double *kkt, double *infeas_norm, double *gap_norm);
+
+/* Fitted values yhat (N, shift removed) and subgradients xi (N x n, row-major) at the current
+ * dual iterate, in FP64, to host buffers (either may be NULL).  Blocks. */
+cr_status cr_get_solution(cr_handle h, double *yhat, double *xi);
+
+/* Iterations run since creation/reset, momentum restarts so far, the step constant L used,
+ * and the shift s.  Any pointer may be NULL. */
+cr_status cr_get_info(cr_handle h, int64_t *iters, int64_t *restarts, double *L, double *shift);
+
+/* Kernel timing collected since the last call when cr_options.profile = 1 (CUDA events on the
+ * handle's stream around each launch).  kind: 0 = pair pass (Step 2 + fused adjoint, the
+ * multiplier-array stream), 1 = folds (Step 1 and reductions), 2 = KKT passes, 3 = persistent
+ * launches (all phases of many iterations).  *ms = summed device time, *launches = count.
+ * Blocks; resets the counters. */
+cr_status cr_profile(cr_handle h, int32_t kind, double *ms, int64_t *launches);
+
+/* Releases every resource of the handle (NULL is a no-op). */
+void cr_destroy(cr_handle h);
+
+/* Static description of a status code. */
+const char *cr_status_str(cr_status s);
+
+/* Last error message recorded on the handle ("" if none).  Valid until the next call. */
+const char *cr_last_error(cr_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CRGPU_H */

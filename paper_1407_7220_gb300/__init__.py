@@ -1,0 +1,223 @@
+"""GB300 P-APG convex-regression solver: thin Python binding of libcrgpu.so.
+
+The library implements P-APG (Fig. 2 of Aybat & Wang, arXiv:1407.7220) on the
+dual of problem (regularize) with every pairwise constraint dualized; see
+``include/crgpu.h`` for the C ABI.  This module only marshals arguments
+(ctypes): every step of the iteration runs in the CUDA kernels of the
+library.  There is no CPU fallback -- if the library is missing or no usable
+GPU is present, the calls raise.
+
+Names mirror the C ABI (``cr_create``, ``cr_iterate``, ``cr_solve``,
+``cr_objective``, ``cr_kkt_residual``, ``cr_get_solution``, ...).  The
+``Solver`` class wraps one handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = [
+    "CrError", "Options", "Solver", "lib", "library_path", "exported_symbols",
+    "THETA_F32", "THETA_BF16", "THETA_F16", "DRIVER_AUTO", "DRIVER_PERSISTENT", "DRIVER_PHASES",
+    "CR_OK", "CR_NOT_CONVERGED",
+]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(HERE, "libcrgpu.so")
+
+CR_OK, CR_NOT_CONVERGED, CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ETIMEOUT, CR_ENUMERIC, CR_ESTATE = 0, 1, -1, -2, -3, -4, -5, -6
+THETA_F32, THETA_BF16, THETA_F16 = 0, 1, 2
+DRIVER_AUTO, DRIVER_PERSISTENT, DRIVER_PHASES = 0, 1, 2
+_DTYPES = {"f32": THETA_F32, "fp32": THETA_F32, "float32": THETA_F32, "bf16": THETA_BF16,
+           "bfloat16": THETA_BF16, "f16": THETA_F16, "fp16": THETA_F16, "float16": THETA_F16}
+
+# the C-ABI entry points declared in include/crgpu.h
+exported_symbols = (
+    "cr_options_default", "cr_create", "cr_create_device", "cr_reset", "cr_iterate", "cr_solve",
+    "cr_objective", "cr_kkt_residual", "cr_get_solution", "cr_get_info", "cr_destroy",
+    "cr_status_str", "cr_last_error", "cr_profile",
+)
+PROFILE_PAIR, PROFILE_FOLD, PROFILE_KKT, PROFILE_PERSISTENT = 0, 1, 2, 3
+
+
+class Options(ctypes.Structure):
+    """Mirror of ``cr_options``."""
+    _fields_ = [
+        ("gamma", ctypes.c_double), ("L", ctypes.c_double), ("shift", ctypes.c_double),
+        ("theta_dtype", ctypes.c_int32), ("stochastic_round", ctypes.c_int32),
+        ("kkt_every", ctypes.c_int32), ("momentum", ctypes.c_int32), ("restart", ctypes.c_int32),
+        ("driver", ctypes.c_int32), ("grid", ctypes.c_int32), ("fp16_exponent", ctypes.c_int32),
+        ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("barrier_timeout_ms", ctypes.c_int32),
+        ("test_barrier_extra", ctypes.c_int32), ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
+    ]
+
+
+class CrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"crgpu status {status}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libcrgpu.so (built by ``__graft_entry__.build()`` / ``python -m paper_1407_7220_gb300._build``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(library_path):
+                raise RuntimeError(f"{library_path} is missing: build the CUDA library first "
+                                   "(python -m paper_1407_7220_gb300._build)")
+            L = ctypes.CDLL(library_path)
+            H = ctypes.c_void_p
+            dp = ctypes.POINTER(ctypes.c_double)
+            fp = ctypes.c_void_p
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            L.cr_options_default.argtypes = [ctypes.POINTER(Options)]
+            L.cr_options_default.restype = None
+            L.cr_create.argtypes = [dp, dp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Options),
+                                    ctypes.POINTER(H)]
+            L.cr_create_device.argtypes = [fp, fp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Options),
+                                           ctypes.POINTER(H)]
+            L.cr_reset.argtypes = [H]
+            L.cr_iterate.argtypes = [H, ctypes.c_int64]
+            L.cr_solve.argtypes = [H, ctypes.c_double, ctypes.c_int64, i64p]
+            L.cr_objective.argtypes = [H, dp, dp, dp]
+            L.cr_kkt_residual.argtypes = [H, dp, dp, dp]
+            L.cr_get_solution.argtypes = [H, dp, dp]
+            L.cr_get_info.argtypes = [H, i64p, i64p, dp, dp]
+            L.cr_profile.argtypes = [H, ctypes.c_int32, dp, i64p]
+            L.cr_profile.restype = ctypes.c_int
+            L.cr_destroy.argtypes = [H]
+            L.cr_destroy.restype = None
+            L.cr_status_str.argtypes = [ctypes.c_int]
+            L.cr_status_str.restype = ctypes.c_char_p
+            L.cr_last_error.argtypes = [H]
+            L.cr_last_error.restype = ctypes.c_char_p
+            for name in ("cr_create", "cr_create_device", "cr_reset", "cr_iterate", "cr_solve", "cr_objective",
+                         "cr_kkt_residual", "cr_get_solution", "cr_get_info"):
+                getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib().cr_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "theta_dtype" and isinstance(v, str):
+            v = _DTYPES[v.lower()]
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k!r}")
+        setattr(o, k, v)
+    return o
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Solver:
+    """One problem instance on the GPU (a ``cr_handle``).
+
+    X: (N, n) array, ybar: (N,) array -- host numpy arrays (copied as FP64) or
+    CUDA torch tensors (copied as FP32 via ``cr_create_device``).  Keyword
+    arguments set ``cr_options`` fields (``gamma``, ``theta_dtype`` ('f32',
+    'bf16', 'f16'), ``stochastic_round``, ``kkt_every``, ``momentum``,
+    ``restart``, ``driver``, ``grid``, ``L``, ``shift``, ``stream`` ...).
+    """
+
+    def __init__(self, X, ybar, **opts):
+        self._h = ctypes.c_void_p()
+        L = lib()
+        o = default_options(**opts)
+        self.options = o
+        if hasattr(X, "is_cuda") and X.is_cuda:
+            Xt = X.contiguous().float()
+            yt = ybar.contiguous().float()
+            N, n = int(Xt.shape[0]), int(Xt.shape[1])
+            st = L.cr_create_device(ctypes.c_void_p(Xt.data_ptr()), ctypes.c_void_p(yt.data_ptr()), N, n,
+                                    ctypes.byref(o), ctypes.byref(self._h))
+        else:
+            Xa = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
+            ya = np.ascontiguousarray(np.asarray(ybar, dtype=np.float64))
+            if Xa.ndim != 2 or ya.shape != (Xa.shape[0],):
+                raise ValueError("X must be (N, n) and ybar (N,)")
+            N, n = Xa.shape
+            st = L.cr_create(_dptr(Xa), _dptr(ya), N, n, ctypes.byref(o), ctypes.byref(self._h))
+        if st != CR_OK:
+            raise CrError(st, L.cr_last_error(None).decode())
+        self.N, self.n = int(N), int(n)
+
+    # -- helpers ---------------------------------------------------------
+    def _check(self, st: int, allow=(CR_OK,)):
+        if st not in allow:
+            raise CrError(st, lib().cr_last_error(self._h).decode())
+        return st
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().cr_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- C ABI -----------------------------------------------------------
+    def reset(self):
+        self._check(lib().cr_reset(self._h))
+
+    def iterate(self, k: int):
+        self._check(lib().cr_iterate(self._h, int(k)))
+
+    def solve(self, tol: float, max_iter: int) -> tuple[bool, int]:
+        done = ctypes.c_int64()
+        st = self._check(lib().cr_solve(self._h, float(tol), int(max_iter), ctypes.byref(done)),
+                         (CR_OK, CR_NOT_CONVERGED))
+        return st == CR_OK, int(done.value)
+
+    def objective(self) -> dict:
+        p, d, g = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(lib().cr_objective(self._h, ctypes.byref(p), ctypes.byref(d), ctypes.byref(g)))
+        return {"primal": p.value, "dual": d.value, "gap": g.value}
+
+    def kkt_residual(self) -> dict:
+        k, i, g = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(lib().cr_kkt_residual(self._h, ctypes.byref(k), ctypes.byref(i), ctypes.byref(g)))
+        return {"kkt": k.value, "infeas_norm": i.value, "gap_norm": g.value}
+
+    def solution(self):
+        y = np.empty(self.N)
+        xi = np.empty((self.N, self.n))
+        self._check(lib().cr_get_solution(self._h, _dptr(y), _dptr(xi)))
+        return y, xi
+
+    def info(self) -> dict:
+        it, rs = ctypes.c_int64(), ctypes.c_int64()
+        Lc, s = ctypes.c_double(), ctypes.c_double()
+        self._check(lib().cr_get_info(self._h, ctypes.byref(it), ctypes.byref(rs), ctypes.byref(Lc), ctypes.byref(s)))
+        return {"iters": it.value, "restarts": rs.value, "L": Lc.value, "shift": s.value}
+
+    def profile(self, kind: int) -> tuple[float, int]:
+        """(summed device ms, launches) of one kernel kind since the last read (needs profile=1)."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        self._check(lib().cr_profile(self._h, int(kind), ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value

@@ -1,0 +1,13 @@
+// Instantiation of the solver kernels with the multiplier array stored as float.
+#include "cr_launch.cuh"
+
+namespace crk {
+KernelSet kernels_f32(int NP)
+{
+#define CR_CASE(V) \
+    if (NP == V) return make_set<float, V>();
+    CR_NP_LIST(CR_CASE)
+#undef CR_CASE
+    return KernelSet{nullptr, nullptr, nullptr, 0, 0};
+}
+}  // namespace crk

@@ -1,0 +1,668 @@
+// cr_kernels.cuh -- device code of the GB300 P-APG convex-regression solver.
+//
+// Method: Aybat & Wang, arXiv:1407.7220, P-APG (Fig. 2) on the dual
+// (lambda_dual) of problem (regularize) with every pairwise constraint of
+// problem (original) dualized (K = N).  One iteration l is split into phases:
+//
+//   foldB(l)  Step 1 at theta^(2)_l by linearity of the closed form:
+//             eta(theta^(2)_l) = (1+beta) eta(theta^(1)_{l-1}) - beta eta(theta^(1)_{l-2})
+//             plus Step 2 for the y >= 0 rows (mu) and Steps 3-4 scalars (t, beta).
+//   pair(l)   Step 2 for every pair p = (l1,l2): theta^(2) = cur + beta (cur - prev),
+//             g = (C eta)_p, theta^(1)_l = max(0, theta^(2) - g / L), written over prev;
+//             fused adjoint: row sums, column sums and theta^T X partials of the new array.
+//   foldA(l)  FP64 reduction of the partials into A_1^T theta, A_2^T theta of theta^(1)_l,
+//             the minimizer eta(theta^(1)_l) and the dual value g_gamma(theta^(1)_l).
+//   kkt       KKT residual terms at theta^(1)_l (FP32 screen, FP64 confirmation).
+//
+// Layout (row-major): theta[b] is N x ld, theta[l1*ld + l2] = multiplier of pair (l1,l2);
+// columns N..ld-1 and the diagonal hold 0.  The pair pass tiles the array in stripes of
+// W = 256 columns; CTA c owns the contiguous range [c*U, (c+1)*U) of (stripe, row) units,
+// stripe-major, so each CTA walks down at most a few stripes and keeps its column
+// accumulators in registers.  Eight warps per CTA: 2 across a stripe x 4 row groups;
+// each thread owns 4 adjacent columns (one 16-byte FP32 vector or 8-byte 16-bit vector).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace crk {
+
+constexpr int kThreads = 256;   // 8 warps
+constexpr int kW = 256;         // stripe width (columns)
+constexpr int kWR = 4;          // row groups per CTA
+constexpr int kRowUnroll = 4;   // rows in flight per thread in the pair pass
+
+enum : int {
+    ERR_BARRIER = 1,   // grid barrier wait exceeded its bound
+    ERR_NUMERIC = 2,   // non-finite value in the fold
+};
+
+// Per-iteration scalar state; two slots indexed by iteration parity so that the
+// phase that writes slot (l & 1) never races with readers of slot ((l-1) & 1).
+struct Scal {
+    double t;          // t of Fig. 2 step 3 after this iteration's update
+    double dual;       // g_gamma(theta^(1)) the restart test compares against
+    double beta;       // momentum weight used to form theta^(2)_l
+    long long restarts;
+};
+
+struct DevState {
+    Scal scal[2];
+    unsigned long long bar_count;  // monotone grid-barrier counter (reset before each launch)
+    long long iters_done;          // written by the persistent kernel at exit
+    int error;
+    int converged;
+    int pad[2];
+    double kkt[8];      // last reduced KKT terms: 0 kkt,1 pri,2 comp,3 infeas,4 gap,5 screen
+};
+
+struct Params {
+    // sizes
+    long long N;
+    int n;
+    int NP;             // padded n (template value, for host checks)
+    long long ld;       // row stride of theta (elements)
+    int S;              // stripes = ceil(N / kW)
+    int G;              // CTAs of the grid
+    int slots;          // column-partial slots per CTA
+    long long total;    // S * N units
+    // constants
+    double gamma, inv_gamma, L, invL_d, shift;
+    float invL;
+    float st_scale, st_inv_scale;   // theta storage scale (FP16 only; 1 otherwise)
+    int momentum, restart, sr;
+    unsigned int seed;
+    unsigned long long bar_timeout_ns;   // bound of every grid-barrier wait
+    int bar_extra;                       // test hook: extra arrivals a barrier waits for (0 in use)
+    // arrays
+    void *theta[2];
+    const double *X64;      // N x n
+    const float *X32;       // N x NP (zero padded)
+    const double *h;        // N, ybar + s
+    float *yrow2, *ccol2, *xi2;     // eta(theta^(2)) for the pair pass: y-s, xi.x - (y-s), xi
+    float *yrow1, *ccol1, *xi1;     // same at theta^(1) (KKT screen)
+    double *y1, *xi1_64;            // eta(theta^(1)) in FP64 (y shifted)
+    double *v[2];           // A_1^T theta^(1) of the two latest iterates (N)
+    double *w[2];           // A_2^T theta^(1) (N x n)
+    double *mu[2];          // multipliers of the y >= 0 rows (N)
+    float *rowpart;         // [2S][N]
+    float *colpart;         // [G][slots][NP+1][kW]
+    double *foldpart;       // [G][8]
+    double *kktpart;        // [G][8]
+    DevState *st;
+};
+
+// ---------------------------------------------------------------------------
+// storage types
+// ---------------------------------------------------------------------------
+template <typename TS> struct Store;
+
+__device__ __forceinline__ uint32_t hash3(uint32_t a, uint32_t b, uint32_t c)
+{
+    // counter-based: a multiply-xor mix of the counters followed by the
+    // "lowbias32" integer finalizer (C. Wellons' hash-prospector)
+    uint32_t x = a * 0x9E3779B1u ^ (b * 0x85EBCA77u + 0x165667B1u) ^ (c * 0xC2B2AE3Du + 0x27D4EB2Fu);
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+template <> struct Store<float> {
+    using Vec = float4;
+    __device__ static __forceinline__ void unpack(const Vec &v, float (&o)[4], float)
+    {
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+    // v = th2 - g*invL computed by the caller as fmaf(-g, invL, th2) = RN(exact);
+    // err approximates the rounding residual (exact when th2 and v are within 2x).
+    __device__ static __forceinline__ float round(float th2, float g, float invL, bool sr, uint32_t rnd, float)
+    {
+        float v = fmaf(-g, invL, th2);
+        if (!(v > 0.0f)) return 0.0f;
+        if (sr) {
+            float err = fmaf(-g, invL, th2 - v);
+            if (err != 0.0f) {
+                uint32_t b = __float_as_uint(v);
+                float nb = __uint_as_float(err > 0.0f ? b + 1u : b - 1u);
+                float d = fabsf(nb - v);
+                // move to the neighbour with probability |err| / d
+                if ((float)(rnd >> 8) * d < fabsf(err) * 16777216.0f) v = nb;
+            }
+        }
+        return v;
+    }
+    __device__ static __forceinline__ float encode(float v, float) { return v; }
+    __device__ static __forceinline__ Vec pack(const float (&s)[4]) { return make_float4(s[0], s[1], s[2], s[3]); }
+    __device__ static __forceinline__ float decoded(float s, float) { return s; }
+};
+
+template <> struct Store<__nv_bfloat16> {
+    using Vec = uint2;  // 4 x bf16
+    __device__ static __forceinline__ float b2f(uint32_t bits16) { return __uint_as_float(bits16 << 16); }
+    __device__ static __forceinline__ void unpack(const Vec &v, float (&o)[4], float)
+    {
+        o[0] = b2f(v.x & 0xFFFFu); o[1] = b2f(v.x >> 16);
+        o[2] = b2f(v.y & 0xFFFFu); o[3] = b2f(v.y >> 16);
+    }
+    // returns the value actually stored (as float); bf16 bits kept in the float's top half
+    __device__ static __forceinline__ float round(float th2, float g, float invL, bool sr, uint32_t rnd, float)
+    {
+        float v = fmaf(-g, invL, th2);
+        if (!(v > 0.0f)) return 0.0f;
+        uint32_t b = __float_as_uint(v);
+        if (sr) b += (rnd & 0xFFFFu);                              // stochastic: add uniform 16-bit noise, truncate
+        else b += 0x7FFFu + ((b >> 16) & 1u);                      // round to nearest even
+        b &= 0xFFFF0000u;
+        return __uint_as_float(b);
+    }
+    __device__ static __forceinline__ Vec pack(const float (&s)[4])
+    {
+        Vec v;
+        v.x = (__float_as_uint(s[0]) >> 16) | (__float_as_uint(s[1]) & 0xFFFF0000u);
+        v.y = (__float_as_uint(s[2]) >> 16) | (__float_as_uint(s[3]) & 0xFFFF0000u);
+        return v;
+    }
+    __device__ static __forceinline__ float decoded(float s, float) { return s; }
+};
+
+template <> struct Store<__half> {
+    using Vec = uint2;  // 4 x fp16, value = half * inv_scale
+    __device__ static __forceinline__ float h2f(uint32_t bits16, float inv_scale)
+    {
+        return __half2float(__ushort_as_half((unsigned short)bits16)) * inv_scale;
+    }
+    __device__ static __forceinline__ void unpack(const Vec &v, float (&o)[4], float inv_scale)
+    {
+        o[0] = h2f(v.x & 0xFFFFu, inv_scale); o[1] = h2f(v.x >> 16, inv_scale);
+        o[2] = h2f(v.y & 0xFFFFu, inv_scale); o[3] = h2f(v.y >> 16, inv_scale);
+    }
+    // returns the scaled half value (as float, exactly representable in fp16)
+    __device__ static __forceinline__ float round(float th2, float g, float invL, bool sr, uint32_t rnd, float scale)
+    {
+        float v = fmaf(-g, invL, th2);
+        if (!(v > 0.0f)) return 0.0f;
+        float sv = fminf(v * scale, 65504.0f);
+        __half hz = __float2half_rz(sv);
+        if (sr) {
+            float lo = __half2float(hz);
+            float hi = __half2float(__ushort_as_half((unsigned short)(__half_as_ushort(hz) + 1)));
+            if (sv > lo && (float)(rnd >> 8) * (hi - lo) < (sv - lo) * 16777216.0f) return hi;
+            return lo;
+        }
+        return __half2float(__float2half_rn(sv));
+    }
+    __device__ static __forceinline__ Vec pack(const float (&s)[4])
+    {
+        Vec v;
+        v.x = (uint32_t)__half_as_ushort(__float2half_rn(s[0])) | ((uint32_t)__half_as_ushort(__float2half_rn(s[1])) << 16);
+        v.y = (uint32_t)__half_as_ushort(__float2half_rn(s[2])) | ((uint32_t)__half_as_ushort(__float2half_rn(s[3])) << 16);
+        return v;
+    }
+    __device__ static __forceinline__ float decoded(float s, float inv_scale) { return s * inv_scale; }
+};
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block reduction of K doubles (sum or max per component) into out[] of thread 0;
+// fixed order, hence deterministic.  red: shared scratch of 8*K doubles.
+template <int K>
+__device__ __forceinline__ void block_reduce(double (&v)[K], const bool (&is_max)[K], double *red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < K; ++i) v[i] = is_max[i] ? warp_max(v[i]) : warp_sum(v[i]);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < K; ++i) red[warp * K + i] = v[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            double a = red[i];
+            for (int w = 1; w < kThreads / 32; ++w) a = is_max[i] ? fmax(a, red[w * K + i]) : a + red[w * K + i];
+            v[i] = a;
+        }
+    }
+    __syncthreads();
+}
+
+// Grid-wide barrier for the persistent (cooperative) launch.  Monotone counter:
+// barrier number b completes when the counter reaches (b+1)*G.  The wait is
+// bounded by wall time; on timeout the error word is set and every CTA leaves.
+__device__ __forceinline__ bool grid_barrier(const Params &P, unsigned long long &bar_no)
+{
+    __syncthreads();
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        unsigned long long target = (bar_no + 1ull) * (unsigned long long)P.G + (unsigned long long)P.bar_extra;
+        atomicAdd(&P.st->bar_count, 1ull);
+        unsigned long long t0 = globaltimer();
+        while (true) {
+            unsigned long long c;
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(c) : "l"(&P.st->bar_count) : "memory");
+            if (c >= target) break;
+            if (*((volatile int *)&P.st->error) != 0) { ok = 0; break; }
+            if (globaltimer() - t0 > P.bar_timeout_ns) {
+                atomicCAS(&P.st->error, 0, ERR_BARRIER);
+                ok = 0;
+                break;
+            }
+            __nanosleep(40);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    ++bar_no;
+    return s_ok != 0;
+}
+
+// CTA c's unit range [u0, u1) of the stripe-major (stripe, row) order.
+__device__ __forceinline__ long long unit_begin(const Params &P, long long c)
+{
+    return (long long)(((unsigned long long)c * (unsigned long long)P.total) / (unsigned long long)P.G);
+}
+
+// ---------------------------------------------------------------------------
+// foldB(l): Step 1 at theta^(2)_l (by linearity), mu update, Steps 3-4 scalars
+// ---------------------------------------------------------------------------
+template <int NP>
+__device__ void phase_foldB(const Params &P, long long ell, double *red)
+{
+    const int c = (int)((ell - 1) & 1), p = (int)(ell & 1);
+    __shared__ double s_beta;
+    if (threadIdx.x < 32) {
+        // every CTA reduces the dual-value partials of foldA(l-1) in the same order
+        double a = 0.0, b = 0.0, cc = 0.0;
+        for (int i = threadIdx.x; i < P.G; i += 32) {
+            a += __ldcg(P.foldpart + i * 8 + 0);
+            b += __ldcg(P.foldpart + i * 8 + 1);
+            cc += __ldcg(P.foldpart + i * 8 + 2);
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        cc = warp_sum(cc);
+        if (threadIdx.x == 0) {
+            Scal old;
+            old.t = __ldcg(&P.st->scal[c].t);
+            old.dual = __ldcg(&P.st->scal[c].dual);
+            old.beta = __ldcg(&P.st->scal[c].beta);
+            old.restarts = __ldcg(&P.st->scal[c].restarts);
+            Scal nw = old;
+            double beta = 0.0;
+            if (ell >= 2) {
+                // g_gamma(theta^(1)_{l-1}) = 1/2||u||^2 + gamma/2||xi||^2 - theta^T C eta,
+                // theta^T C eta = u^T y + gamma||xi||^2, u = y - h (Eq. (eq:g_gamma))
+                double dv = 0.5 * a - cc - 0.5 * P.gamma * b;
+                double t = old.t;
+                if (P.restart && dv < old.dual) {
+                    t = 1.0;
+                    nw.restarts = old.restarts + 1;
+                }
+                double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));   // Fig. 2 step 3
+                beta = P.momentum ? (t - 1.0) / tn : 0.0;           // Fig. 2 step 4 weight
+                nw.t = tn;
+                nw.dual = dv;
+            }
+            nw.beta = beta;
+            s_beta = beta;
+            if (blockIdx.x == 0) P.st->scal[p] = nw;
+        }
+    }
+    __syncthreads();
+    const double beta = s_beta, b1 = 1.0 + beta;
+    const long long N = P.N;
+    const int n = P.n;
+    for (long long l = (long long)blockIdx.x * kThreads + threadIdx.x; l < N; l += (long long)P.G * kThreads) {
+        double v2 = b1 * __ldcg(P.v[c] + l) - beta * __ldcg(P.v[p] + l);
+        double mu2 = b1 * __ldcg(P.mu[c] + l) - beta * __ldcg(P.mu[p] + l);
+        double y2 = __ldg(P.h + l) + v2 + mu2;
+        double mun = mu2 - y2 * P.invL_d;     // Step 2 on the y >= 0 rows of C
+        P.mu[p][l] = mun > 0.0 ? mun : 0.0;
+        double ys = y2 - P.shift;
+        double d = 0.0;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            float xf = 0.0f;
+            if (k < n) {
+                double xi = (b1 * __ldcg(P.w[c] + l * n + k) - beta * __ldcg(P.w[p] + l * n + k)) * P.inv_gamma;
+                d += xi * __ldg(P.X64 + l * n + k);
+                xf = (float)xi;
+            }
+            P.xi2[l * NP + k] = xf;
+        }
+        P.yrow2[l] = (float)ys;
+        P.ccol2[l] = (float)(d - ys);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pair(l): Step 2 over all pairs + fused adjoint partial sums
+// ---------------------------------------------------------------------------
+template <typename TS, int NP>
+__device__ void phase_pair(const Params &P, long long ell, float *sm)
+{
+    using St = Store<TS>;
+    using Vec = typename St::Vec;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wc = warp & 1, wr = warp >> 1;
+    const int p = (int)(ell & 1), c = 1 - p;
+    const TS *__restrict__ cur = (const TS *)P.theta[c];
+    TS *__restrict__ nxt = (TS *)P.theta[p];   // holds theta^(1)_{l-2} on entry
+    const float beta = (float)__ldcg(&P.st->scal[p].beta);
+    const float invL = P.invL;
+    const float scl = P.st_scale, iscl = P.st_inv_scale;
+    const bool sr = P.sr != 0;
+    const uint32_t rseed = P.seed ^ (uint32_t)ell * 0x632BE5ABu;
+    const long long N = P.N, ld = P.ld;
+
+    long long u = unit_begin(P, blockIdx.x);
+    const long long uend = unit_begin(P, blockIdx.x + 1);
+    const long long first_stripe = u / N;
+    while (u < uend) {
+        const long long s = u / N;
+        const long long r0 = u - s * N;
+        const long long r1 = min(N, r0 + (uend - u));
+        const long long col0 = s * kW + wc * 128 + lane * 4;
+        const bool vec_ok = col0 < ld;
+        float ccol[4], xi[4][NP];
+        bool colv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            long long cj = col0 + j;
+            colv[j] = cj < N;
+            ccol[j] = colv[j] ? __ldcg(P.ccol2 + cj) : 0.0f;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) xi[j][k] = colv[j] ? __ldcg(P.xi2 + cj * NP + k) : 0.0f;
+        }
+        float acc[4][NP], csum[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            csum[j] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) acc[j][k] = 0.0f;
+        }
+        float *rp = P.rowpart + (s * 2 + wc) * N;
+
+        for (long long rb = r0 + wr; rb < r1; rb += kWR * kRowUnroll) {
+            Vec vc[kRowUnroll], vp[kRowUnroll];
+#pragma unroll
+            for (int q = 0; q < kRowUnroll; ++q) {
+                long long r = rb + (long long)q * kWR;
+                if (r < r1 && vec_ok) {
+                    vc[q] = __ldcg((const Vec *)(cur + r * ld + col0));
+                    vp[q] = __ldcg((const Vec *)(nxt + r * ld + col0));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kRowUnroll; ++q) {
+                long long r = rb + (long long)q * kWR;
+                if (r >= r1) break;   // warp-uniform
+                float xr[NP];
+#pragma unroll
+                for (int k = 0; k < NP; ++k) xr[k] = __ldg(P.X32 + r * NP + k);
+                const float yr = __ldcg(P.yrow2 + r);
+                float tc[4] = {0.f, 0.f, 0.f, 0.f}, tp[4] = {0.f, 0.f, 0.f, 0.f};
+                if (vec_ok) {
+                    St::unpack(vc[q], tc, iscl);
+                    St::unpack(vp[q], tp, iscl);
+                }
+                float outv[4];
+                float rs = 0.0f;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float th2 = fmaf(beta, tc[j] - tp[j], tc[j]);
+                    float g = yr + ccol[j];
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) g = fmaf(-xi[j][k], xr[k], g);
+                    uint32_t rnd = sr ? hash3((uint32_t)r, (uint32_t)(col0 + j), rseed) : 0u;
+                    float sv = St::round(th2, g, invL, sr, rnd, scl);
+                    if (!colv[j] || (col0 + j) == r) sv = 0.0f;
+                    outv[j] = sv;
+                    const float vv = St::decoded(sv, iscl);
+                    rs += vv;
+                    csum[j] += vv;
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) acc[j][k] = fmaf(vv, xr[k], acc[j][k]);
+                }
+                if (vec_ok) *((Vec *)(nxt + r * ld + col0)) = St::pack(outv);
+                rs = warp_sum(rs);
+                if (lane == 0) rp[r] = rs;
+            }
+        }
+        // column partials: reduce the 4 row groups in shared memory, then one slot write
+        const int slot = (int)(s - first_stripe);
+        float *cp = P.colpart + ((long long)blockIdx.x * P.slots + slot) * (NP + 1) * kW;
+        const int cl = wc * 128 + lane * 4;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            sm[(wr * (NP + 1) + 0) * kW + cl + j] = csum[j];
+#pragma unroll
+            for (int k = 0; k < NP; ++k) sm[(wr * (NP + 1) + 1 + k) * kW + cl + j] = acc[j][k];
+        }
+        __syncthreads();
+        for (int e = tid; e < (NP + 1) * kW; e += kThreads) {
+            float a = sm[e];
+#pragma unroll
+            for (int q = 1; q < kWR; ++q) a += sm[q * (NP + 1) * kW + e];
+            cp[e] = a;
+        }
+        __syncthreads();
+        u += (r1 - r0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// foldA(l): reduce partials of theta^(1)_l in FP64; eta(theta^(1)_l); dual terms
+// ---------------------------------------------------------------------------
+template <int NP>
+__device__ void phase_foldA(const Params &P, long long ell, double *red)
+{
+    const int p = (int)(ell & 1);
+    const long long N = P.N;
+    const int n = P.n;
+    double a = 0.0, b = 0.0, cc = 0.0, mviol = 0.0, mcomp = 0.0, sviol = 0.0, smuy = 0.0;
+    for (long long l = (long long)blockIdx.x * kThreads + threadIdx.x; l < N; l += (long long)P.G * kThreads) {
+        double R = 0.0;
+        for (int q = 0; q < 2 * P.S; ++q) R += (double)__ldcg(P.rowpart + (long long)q * N + l);
+        const long long s = l / kW, cl = l - s * kW;
+        // CTAs whose unit range intersects stripe s, ascending
+        long long ua = s * N, ub = s * N + N - 1;
+        long long c0 = (long long)(((unsigned long long)ua * (unsigned long long)P.G) / (unsigned long long)P.total);
+        while (c0 > 0 && unit_begin(P, c0) > ua) --c0;
+        while (c0 + 1 < P.G && unit_begin(P, c0 + 1) <= ua) ++c0;
+        double Cc = 0.0, TX[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) TX[k] = 0.0;
+        for (long long cta = c0; cta < P.G && unit_begin(P, cta) <= ub; ++cta) {
+            if (unit_begin(P, cta + 1) <= unit_begin(P, cta)) continue;  // empty range
+            const long long fs = unit_begin(P, cta) / N;
+            const float *cp = P.colpart + ((cta * P.slots + (s - fs)) * (NP + 1)) * kW;
+            Cc += (double)__ldcg(cp + cl);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) TX[k] += (double)__ldcg(cp + (1 + k) * kW + cl);
+        }
+        const double v = R - Cc;               // (A_1^T theta)_l = row sum - column sum
+        P.v[p][l] = v;
+        const double y = __ldg(P.h + l) + v + __ldcg(P.mu[p] + l);   // Step 1 closed form
+        const double ys = y - P.shift;
+        double d = 0.0, xin = 0.0;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            float xf = 0.0f;
+            if (k < n) {
+                const double xk = __ldg(P.X64 + l * n + k);
+                const double wk = Cc * xk - TX[k];   // (A_2^T theta)_l = Cc_l x_l - (theta^T X)_l
+                P.w[p][l * n + k] = wk;
+                const double xi = wk * P.inv_gamma;
+                P.xi1_64[l * n + k] = xi;
+                d += xi * xk;
+                xin += xi * xi;
+                xf = (float)xi;
+            }
+            P.xi1[l * NP + k] = xf;
+        }
+        P.y1[l] = y;
+        P.yrow1[l] = (float)ys;
+        P.ccol1[l] = (float)(d - ys);
+        const double uu = y - __ldg(P.h + l);
+        a += uu * uu;
+        b += xin;
+        cc += uu * y;
+        const double mu = __ldcg(P.mu[p] + l);
+        mviol = fmax(mviol, -y);
+        mcomp = fmax(mcomp, mu * fabs(y));
+        if (y < 0.0) sviol += y * y;
+        smuy += mu * y;
+        if (!isfinite(y) || !isfinite(d)) atomicCAS(&P.st->error, 0, ERR_NUMERIC);
+    }
+    double vals[7] = {a, b, cc, mviol, mcomp, sviol, smuy};
+    const bool ismax[7] = {false, false, false, true, true, false, false};
+    block_reduce<7>(vals, ismax, red);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int i = 0; i < 7; ++i) P.foldpart[blockIdx.x * 8 + i] = vals[i];
+}
+
+// ---------------------------------------------------------------------------
+// KKT pass at theta^(1)_l: per-pair g = (C eta)_p; FP32 (screen) or FP64
+// ---------------------------------------------------------------------------
+template <typename TS, int NP, bool F64>
+__device__ void phase_kkt(const Params &P, long long ell, double *red)
+{
+    using St = Store<TS>;
+    using Vec = typename St::Vec;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wc = warp & 1, wr = warp >> 1;
+    const int p = (int)(ell & 1);
+    const TS *__restrict__ th = (const TS *)P.theta[p];
+    const float iscl = P.st_inv_scale;
+    const long long N = P.N, ld = P.ld;
+    const int n = P.n;
+    double mviol = 0.0, mcomp = 0.0, sviol = 0.0, sthg = 0.0;
+
+    long long u = unit_begin(P, blockIdx.x);
+    const long long uend = unit_begin(P, blockIdx.x + 1);
+    while (u < uend) {
+        const long long s = u / N;
+        const long long r0 = u - s * N;
+        const long long r1 = min(N, r0 + (uend - u));
+        const long long col0 = s * kW + wc * 128 + lane * 4;
+        const bool vec_ok = col0 < ld;
+        bool colv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) colv[j] = (col0 + j) < N;
+        float tv_viol = 0.0f, tv_comp = 0.0f, tv_s2 = 0.0f, tv_tg = 0.0f;
+        for (long long r = r0 + wr; r < r1; r += kWR) {
+            if (!vec_ok) continue;
+            float tc[4];
+            St::unpack(__ldcg((const Vec *)(th + r * ld + col0)), tc, iscl);
+            if (F64) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const long long l2 = col0 + j;
+                    if (!colv[j] || l2 == r) continue;
+                    double g = __ldcg(P.y1 + r) - __ldcg(P.y1 + l2);
+                    for (int k = 0; k < n; ++k) g -= __ldcg(P.xi1_64 + l2 * n + k) * (__ldg(P.X64 + r * n + k) - __ldg(P.X64 + l2 * n + k));
+                    mviol = fmax(mviol, -g);
+                    mcomp = fmax(mcomp, (double)tc[j] * fabs(g));
+                    if (g < 0.0) sviol += g * g;
+                    sthg += (double)tc[j] * g;
+                }
+            } else {
+                const float yr = __ldcg(P.yrow1 + r);
+                float xr[NP];
+#pragma unroll
+                for (int k = 0; k < NP; ++k) xr[k] = __ldg(P.X32 + r * NP + k);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const long long l2 = col0 + j;
+                    if (!colv[j] || l2 == r) continue;
+                    float g = yr + __ldcg(P.ccol1 + l2);
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) g = fmaf(-__ldcg(P.xi1 + l2 * NP + k), xr[k], g);
+                    tv_viol = fmaxf(tv_viol, -g);
+                    tv_comp = fmaxf(tv_comp, tc[j] * fabsf(g));
+                    if (g < 0.0f) tv_s2 = fmaf(g, g, tv_s2);
+                    tv_tg = fmaf(tc[j], g, tv_tg);
+                }
+            }
+        }
+        if (!F64) {
+            mviol = fmax(mviol, (double)tv_viol);
+            mcomp = fmax(mcomp, (double)tv_comp);
+            sviol += (double)tv_s2;
+            sthg += (double)tv_tg;
+        }
+        u += (r1 - r0);
+    }
+    double vals[4] = {mviol, mcomp, sviol, sthg};
+    const bool ismax[4] = {true, true, false, false};
+    block_reduce<4>(vals, ismax, red);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) P.kktpart[blockIdx.x * 8 + i] = vals[i];
+}
+
+// Combine the KKT partials (pairs) and the fold partials (y >= 0 rows) into the
+// metrics of cr_kkt_residual; every CTA computes the same values.  out: 0 kkt,
+// 1 pri, 2 comp, 3 infeas_norm, 4 gap_norm.
+__device__ __forceinline__ void reduce_kkt(const Params &P, double sigma, double *out)
+{
+    // warp 0 of the calling CTA
+    double mv = 0.0, mc = 0.0, s2 = 0.0, tg = 0.0;
+    for (int i = threadIdx.x; i < P.G; i += 32) {
+        mv = fmax(mv, fmax(__ldcg(P.kktpart + i * 8 + 0), __ldcg(P.foldpart + i * 8 + 3)));
+        mc = fmax(mc, fmax(__ldcg(P.kktpart + i * 8 + 1), __ldcg(P.foldpart + i * 8 + 4)));
+        s2 += __ldcg(P.kktpart + i * 8 + 2) + __ldcg(P.foldpart + i * 8 + 5);
+        tg += __ldcg(P.kktpart + i * 8 + 3) + __ldcg(P.foldpart + i * 8 + 6);
+    }
+    mv = warp_max(mv);
+    mc = warp_max(mc);
+    s2 = warp_sum(s2);
+    tg = warp_sum(tg);
+    const double np = (double)P.N * (double)(P.N - 1);
+    const double pri = mv / sigma, comp = mc / (sigma * sigma);
+    out[0] = fmax(pri, comp);
+    out[1] = pri;
+    out[2] = comp;
+    out[3] = sqrt(s2) / sqrt(np);
+    out[4] = tg / np;
+}
+
+}  // namespace crk

@@ -1,0 +1,159 @@
+// cr_launch.cuh -- __global__ entry points (persistent driver and per-phase kernels)
+// and the table the host uses to reach them for a given (theta dtype, padded n).
+#pragma once
+
+#include "cr_kernels.cuh"
+
+namespace crk {
+
+enum Phase : int { PH_FOLDB = 0, PH_PAIR = 1, PH_FOLDA = 2, PH_KKT32 = 3, PH_KKT64 = 4, PH_DECIDE32 = 5, PH_DECIDE64 = 6 };
+
+// Shared memory of the pair pass: column partials of the 4 row groups.
+template <int NP> constexpr size_t pair_smem_bytes() { return (size_t)kWR * (NP + 1) * kW * sizeof(float); }
+
+// Persistent driver: iterations ell0..ell1 in one cooperative launch.  Phases are
+// separated by bounded grid barriers; every CTA takes the same decisions from the
+// same reduced values.  check_every > 0 enables the convergence test (FP32 screen,
+// FP64 confirmation) every check_every iterations and at ell1.
+template <typename TS, int NP>
+__global__ void __launch_bounds__(kThreads, 1)
+k_persistent(Params P, long long ell0, long long ell1, int check_every, double tol, double sigma)
+{
+    extern __shared__ float4 sm_raw[];
+    float *sm = reinterpret_cast<float *>(sm_raw);
+    __shared__ double red[64];
+    __shared__ double s_m[8];
+    unsigned long long bar = 0;
+
+    phase_foldB<NP>(P, ell0, red);
+    if (!grid_barrier(P, bar)) return;
+    for (long long ell = ell0; ell <= ell1; ++ell) {
+        phase_pair<TS, NP>(P, ell, sm);
+        if (!grid_barrier(P, bar)) return;
+        phase_foldA<NP>(P, ell, red);
+        if (!grid_barrier(P, bar)) return;
+        const bool check = check_every > 0 && ((ell % check_every) == 0 || ell == ell1);
+        if (check) {
+            phase_kkt<TS, NP, false>(P, ell, red);
+            if (!grid_barrier(P, bar)) return;
+            if (threadIdx.x < 32) {
+                double m[5];
+                reduce_kkt(P, sigma, m);
+                if (threadIdx.x == 0) {
+                    for (int i = 0; i < 5; ++i) s_m[i] = m[i];
+                    s_m[5] = m[0];
+                }
+            }
+            __syncthreads();
+            bool stop = s_m[0] <= tol;
+            const double screen = s_m[5];
+            if (stop) {
+                phase_kkt<TS, NP, true>(P, ell, red);
+                if (!grid_barrier(P, bar)) return;
+                if (threadIdx.x < 32) {
+                    double m[5];
+                    reduce_kkt(P, sigma, m);
+                    if (threadIdx.x == 0)
+                        for (int i = 0; i < 5; ++i) s_m[i] = m[i];
+                }
+                __syncthreads();
+                stop = s_m[0] <= tol;
+            }
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                for (int i = 0; i < 5; ++i) P.st->kkt[i] = s_m[i];
+                P.st->kkt[5] = screen;
+                if (stop) {
+                    P.st->converged = 1;
+                    P.st->iters_done = ell;
+                }
+            }
+            if (stop) return;
+        }
+        if (ell < ell1) {
+            phase_foldB<NP>(P, ell + 1, red);
+            if (!grid_barrier(P, bar)) return;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.st->iters_done = ell1;
+}
+
+// One phase of one iteration (the CR_DRIVER_PHASES path and the stand-alone metric
+// calls).  Every kernel is a no-op once the state says converged or failed.
+template <typename TS, int NP>
+__global__ void __launch_bounds__(kThreads, 1)
+k_phase(Params P, int phase, long long ell, double tol, double sigma)
+{
+    extern __shared__ float4 sm_raw[];
+    float *sm = reinterpret_cast<float *>(sm_raw);
+    __shared__ double red[64];
+    const int conv = __ldcg(&P.st->converged), err = __ldcg(&P.st->error);
+    if (err != 0) return;
+    if (conv != 0 && phase != PH_KKT64 && phase != PH_DECIDE64) return;
+    switch (phase) {
+    case PH_FOLDB: phase_foldB<NP>(P, ell, red); break;
+    case PH_PAIR: phase_pair<TS, NP>(P, ell, sm); break;
+    case PH_FOLDA: phase_foldA<NP>(P, ell, red); break;
+    case PH_KKT32: phase_kkt<TS, NP, false>(P, ell, red); break;
+    case PH_KKT64: phase_kkt<TS, NP, true>(P, ell, red); break;
+    case PH_DECIDE32:
+    case PH_DECIDE64:
+        // single CTA: reduce the KKT partials; tol < 0 only records the metrics
+        if (blockIdx.x == 0 && threadIdx.x < 32) {
+            double m[5];
+            reduce_kkt(P, sigma, m);
+            if (threadIdx.x == 0) {
+                if (phase == PH_DECIDE32) {
+                    P.st->kkt[5] = m[0];
+                    // the FP64 pass that follows runs only if the screen passed
+                    P.st->kkt[6] = (tol >= 0.0 && m[0] <= tol) ? 1.0 : 0.0;
+                } else {
+                    for (int i = 0; i < 5; ++i) P.st->kkt[i] = m[i];
+                    if (tol >= 0.0 && m[0] <= tol) {
+                        P.st->converged = 1;
+                        P.st->iters_done = ell;
+                    }
+                }
+            }
+        }
+        break;
+    }
+}
+
+// KKT64 pass that runs only if the preceding FP32 screen passed (phase path).
+template <typename TS, int NP>
+__global__ void __launch_bounds__(kThreads, 1)
+k_kkt64_if_screened(Params P, long long ell)
+{
+    __shared__ double red[64];
+    if (__ldcg(&P.st->error) != 0 || __ldcg(&P.st->kkt[6]) == 0.0) return;
+    phase_kkt<TS, NP, true>(P, ell, red);
+}
+
+struct KernelSet {
+    const void *persistent;
+    const void *phase;
+    const void *kkt64_if;
+    size_t smem;
+    int NP;
+};
+
+template <typename TS, int NP> KernelSet make_set()
+{
+    KernelSet k;
+    k.persistent = (const void *)k_persistent<TS, NP>;
+    k.phase = (const void *)k_phase<TS, NP>;
+    k.kkt64_if = (const void *)k_kkt64_if_screened<TS, NP>;
+    k.smem = pair_smem_bytes<NP>();
+    k.NP = NP;
+    return k;
+}
+
+// padded n values compiled: n -> smallest NP >= n in this list
+#define CR_NP_LIST(X) X(2) X(4) X(5) X(8) X(10) X(16) X(20) X(32)
+constexpr int kMaxN = 32;
+
+KernelSet kernels_f32(int NP);
+KernelSet kernels_bf16(int NP);
+KernelSet kernels_f16(int NP);
+
+}  // namespace crk

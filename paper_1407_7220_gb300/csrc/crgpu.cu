@@ -1,0 +1,745 @@
+// crgpu.cu -- host side of the C ABI declared in include/crgpu.h.
+//
+// Owns the device buffers of one instance, computes the problem constants
+// (shift s, step constant L_g of Eq. (eq:lischitz)) in FP64 on the host, and
+// drives the iteration either as one cooperative persistent launch per call or
+// as one launch per phase.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "cr_launch.cuh"
+#include "crgpu.h"
+
+using crk::DevState;
+using crk::KernelSet;
+using crk::Params;
+
+struct cr_ctx {
+    cr_options opt;
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    long long N = 0;
+    int n = 0;
+    int NP = 0;
+    long long ld = 0;
+    double sigma = 1.0;
+    long long iters = 0;     // iterations completed (host view)
+    bool persistent_ok = false;
+    KernelSet ks{};
+    Params P{};
+    std::vector<void *> allocs;
+    std::string err;
+    bool broken = false;     // a device-side wait timed out; only reset/destroy are valid
+    // profiling (cr_options.profile): events around launches, summed per kind on cr_profile
+    struct Ev {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Ev> evs;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[4] = {0, 0, 0, 0};
+    long long prof_n[4] = {0, 0, 0, 0};
+};
+
+namespace {
+
+const char *cr_status_str_impl(cr_status s)
+{
+    switch (s) {
+    case CR_OK: return "ok";
+    case CR_NOT_CONVERGED: return "not converged (max_iter reached)";
+    case CR_EINVAL: return "invalid argument";
+    case CR_ENOMEM: return "out of memory";
+    case CR_ECUDA: return "CUDA error";
+    case CR_ETIMEOUT: return "bounded device wait timed out";
+    case CR_ENUMERIC: return "non-finite value in the iteration";
+    case CR_ESTATE: return "invalid handle state";
+    }
+    return "unknown status";
+}
+
+cr_status fail(cr_ctx *h, cr_status s, const char *fmt, ...)
+{
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return s;
+}
+
+#define CR_CUDA(h, call)                                                                     \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            if (e_ == cudaErrorMemoryAllocation) return fail(h, CR_ENOMEM, "%s: %s", #call, cudaGetErrorString(e_)); \
+            return fail(h, CR_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));                \
+        }                                                                                    \
+    } while (0)
+
+int padded_n(int n)
+{
+    static const int list[] = {2, 4, 5, 8, 10, 16, 20, 32};
+    for (int v : list)
+        if (n <= v) return v;
+    return 0;
+}
+
+KernelSet kernels_for(int dtype, int NP)
+{
+    switch (dtype) {
+    case CR_THETA_F32: return crk::kernels_f32(NP);
+    case CR_THETA_BF16: return crk::kernels_bf16(NP);
+    case CR_THETA_F16: return crk::kernels_f16(NP);
+    default: return KernelSet{nullptr, nullptr, nullptr, 0, 0};
+    }
+}
+
+size_t theta_elem_size(int dtype) { return dtype == CR_THETA_F32 ? 4 : 2; }
+
+// ---- problem constants (host, FP64) ----------------------------------------
+
+// Observation shift (the paragraph after Eq. (omega_primal) asks only for "a
+// sufficiently large quantity"): s = max(0, -min ybar) + (max ybar - min ybar).
+double default_shift(const std::vector<double> &yb)
+{
+    double lo = yb[0], hi = yb[0];
+    for (double v : yb) {
+        lo = std::min(lo, v);
+        hi = std::max(hi, v);
+    }
+    return std::max(0.0, -lo) + (hi - lo);
+}
+
+// Eigen-decomposition of a symmetric n x n matrix by cyclic Jacobi rotations with
+// accumulated eigenvectors (columns of V).  a is overwritten; eigenvalues on its diagonal.
+void sym_eig(std::vector<double> &a, std::vector<double> &V, int n)
+{
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) (i == j ? diag : off) += a[(size_t)i * n + j] * a[(size_t)i * n + j];
+        if (off <= 1e-32 * std::max(diag, 1e-300)) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = a[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                const double theta = (a[(size_t)q * n + q] - a[(size_t)p * n + p]) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {  // columns p, q
+                    const double kp = a[(size_t)k * n + p], kq = a[(size_t)k * n + q];
+                    a[(size_t)k * n + p] = c * kp - s * kq;
+                    a[(size_t)k * n + q] = s * kp + c * kq;
+                }
+                for (int k = 0; k < n; ++k) {  // rows p, q
+                    const double pk = a[(size_t)p * n + k], qk = a[(size_t)q * n + k];
+                    a[(size_t)p * n + k] = c * pk - s * qk;
+                    a[(size_t)q * n + k] = s * pk + c * qk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double kp = V[(size_t)k * n + p], kq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = c * kp - s * kq;
+                    V[(size_t)k * n + q] = s * kp + c * kq;
+                }
+            }
+    }
+}
+
+// ||A_2||^2 = max_l lambda_max(M_l), M_l = sum_m (x_m - x_l)(x_m - x_l)^T (A_2^T A_2 is block
+// diagonal with blocks M_l).  M_l = N (Sigma + v v^T) with Sigma the population covariance
+// and v = xbar - x_l, so with Sigma = Q diag(lam) Q^T the largest eigenvalue is the largest
+// root of the secular equation 1 = sum_i z_i^2 / (mu - lam_i), z = Q^T v, which lies in
+// [max lam, max lam + ||z||^2]; it is found by bisection.
+double max_block_eig(const std::vector<double> &X, long long N, int n)
+{
+    std::vector<double> mean(n, 0.0), cov((size_t)n * n, 0.0), V;
+    for (long long l = 0; l < N; ++l)
+        for (int k = 0; k < n; ++k) mean[k] += X[(size_t)l * n + k];
+    for (int k = 0; k < n; ++k) mean[k] /= (double)N;
+    for (long long l = 0; l < N; ++l)
+        for (int i = 0; i < n; ++i) {
+            const double di = X[(size_t)l * n + i] - mean[i];
+            for (int j = 0; j < n; ++j) cov[(size_t)i * n + j] += di * (X[(size_t)l * n + j] - mean[j]);
+        }
+    for (double &c : cov) c /= (double)N;
+    sym_eig(cov, V, n);
+    std::vector<double> lam(n), z(n);
+    double lmax = -std::numeric_limits<double>::infinity();
+    for (int i = 0; i < n; ++i) {
+        lam[i] = cov[(size_t)i * n + i];
+        lmax = std::max(lmax, lam[i]);
+    }
+    double best = 0.0;
+    for (long long l = 0; l < N; ++l) {
+        double zz = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < n; ++k) s += V[(size_t)k * n + i] * (mean[k] - X[(size_t)l * n + k]);
+            z[i] = s;
+            zz += s * s;
+        }
+        double lo = lmax, hi = lmax + zz;
+        for (int it = 0; it < 200 && hi > lo; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            double f = 1.0;
+            for (int i = 0; i < n; ++i) f -= z[i] * z[i] / (mid - lam[i]);
+            (f < 0.0 ? lo : hi) = mid;
+        }
+        best = std::max(best, (double)N * hi);
+    }
+    return best;
+}
+
+bool all_finite(const double *a, size_t k)
+{
+    for (size_t i = 0; i < k; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+template <typename T> cr_status dev_alloc(cr_ctx *h, T **p, size_t count)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(h, CR_ENOMEM, "cudaMalloc(%zu bytes): %s", count * sizeof(T), cudaGetErrorString(e));
+    }
+    h->allocs.push_back(q);
+    *p = (T *)q;
+    return CR_OK;
+}
+
+#define CR_TRY(x)                          \
+    do {                                   \
+        cr_status s_ = (x);                \
+        if (s_ != CR_OK) return s_;        \
+    } while (0)
+
+// Work partition of the pair pass: the number of column-partial slots per CTA.
+int max_slots(long long total, long long N, int G)
+{
+    int best = 1;
+    for (long long c = 0; c < G; ++c) {
+        long long u0 = (long long)(((unsigned long long)c * total) / G);
+        long long u1 = (long long)(((unsigned long long)(c + 1) * total) / G);
+        if (u1 <= u0) continue;
+        best = std::max(best, (int)((u1 - 1) / N - u0 / N + 1));
+    }
+    return best;
+}
+
+cudaEvent_t take_event(cr_ctx *h)
+{
+    if (!h->pool.empty()) {
+        cudaEvent_t e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Events bracketing one launch of the given kind (profile option only).
+struct ProfScope {
+    cr_ctx *h;
+    int kind;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(cr_ctx *h_, int kind_) : h(h_), kind(kind_)
+    {
+        if (!h->opt.profile) return;
+        a = take_event(h);
+        b = take_event(h);
+        if (a) cudaEventRecord(a, h->stream);
+    }
+    ~ProfScope()
+    {
+        if (!a || !b) return;
+        cudaEventRecord(b, h->stream);
+        h->evs.push_back({kind, a, b});
+    }
+};
+
+int phase_kind(int phase)
+{
+    if (phase == crk::PH_PAIR) return 0;
+    if (phase == crk::PH_FOLDA || phase == crk::PH_FOLDB) return 1;
+    return 2;
+}
+
+cr_status launch_phase(cr_ctx *h, int phase, long long ell, double tol, int grid = -1)
+{
+    Params P = h->P;
+    void *args[] = {&P, &phase, &ell, &tol, &h->sigma};
+    const int g = grid > 0 ? grid : h->P.G;
+    ProfScope ps(h, phase_kind(phase));
+    CR_CUDA(h, cudaLaunchKernel(h->ks.phase, dim3(g), dim3(crk::kThreads), args, h->ks.smem, h->stream));
+    return CR_OK;
+}
+
+cr_status launch_persistent(cr_ctx *h, long long ell0, long long ell1, int check_every, double tol)
+{
+    CR_CUDA(h, cudaMemsetAsync(&h->P.st->bar_count, 0, sizeof(unsigned long long), h->stream));
+    Params P = h->P;
+    void *args[] = {&P, &ell0, &ell1, &check_every, &tol, &h->sigma};
+    ProfScope ps(h, 3);
+    CR_CUDA(h, cudaLaunchCooperativeKernel(h->ks.persistent, dim3(h->P.G), dim3(crk::kThreads), args, h->ks.smem,
+                                           h->stream));
+    return CR_OK;
+}
+
+// Iterations ell0..ell1 through the per-phase kernels; checks as in the persistent driver.
+cr_status run_phases(cr_ctx *h, long long ell0, long long ell1, int check_every, double tol)
+{
+    for (long long ell = ell0; ell <= ell1; ++ell) {
+        CR_TRY(launch_phase(h, crk::PH_FOLDB, ell, tol));
+        CR_TRY(launch_phase(h, crk::PH_PAIR, ell, tol));
+        CR_TRY(launch_phase(h, crk::PH_FOLDA, ell, tol));
+        if (check_every > 0 && ((ell % check_every) == 0 || ell == ell1)) {
+            CR_TRY(launch_phase(h, crk::PH_KKT32, ell, tol));
+            CR_TRY(launch_phase(h, crk::PH_DECIDE32, ell, tol, 1));
+            Params P = h->P;
+            void *args[] = {&P, &ell};
+            ProfScope ps(h, 2);
+            CR_CUDA(h, cudaLaunchKernel(h->ks.kkt64_if, dim3(h->P.G), dim3(crk::kThreads), args, 0, h->stream));
+            CR_TRY(launch_phase(h, crk::PH_DECIDE64, ell, tol, 1));
+        }
+    }
+    return CR_OK;
+}
+
+cr_status read_state(cr_ctx *h, DevState *st)
+{
+    CR_CUDA(h, cudaMemcpyAsync(st, h->P.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    CR_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (st->error == crk::ERR_BARRIER) {
+        h->broken = true;
+        return fail(h, CR_ETIMEOUT, "a grid barrier wait exceeded its bound");
+    }
+    if (st->error == crk::ERR_NUMERIC) return fail(h, CR_ENUMERIC, "non-finite value in the iteration");
+    return CR_OK;
+}
+
+cr_status init_state(cr_ctx *h)
+{
+    const Params &P = h->P;
+    const size_t th = (size_t)h->N * h->ld * theta_elem_size(h->opt.theta_dtype);
+    for (int b = 0; b < 2; ++b) {
+        CR_CUDA(h, cudaMemsetAsync(P.theta[b], 0, th, h->stream));
+        CR_CUDA(h, cudaMemsetAsync(P.v[b], 0, sizeof(double) * h->N, h->stream));
+        CR_CUDA(h, cudaMemsetAsync(P.w[b], 0, sizeof(double) * h->N * h->n, h->stream));
+        CR_CUDA(h, cudaMemsetAsync(P.mu[b], 0, sizeof(double) * h->N, h->stream));
+    }
+    CR_CUDA(h, cudaMemsetAsync(P.rowpart, 0, sizeof(float) * 2 * (size_t)P.S * h->N, h->stream));
+    CR_CUDA(h, cudaMemsetAsync(P.colpart, 0, sizeof(float) * (size_t)P.G * P.slots * (h->NP + 1) * crk::kW, h->stream));
+    DevState st;
+    std::memset(&st, 0, sizeof st);
+    st.scal[0].t = 1.0;   // t_1 = 1 (Iteration 0 of Fig. 2)
+    st.scal[0].dual = -std::numeric_limits<double>::infinity();
+    st.scal[1] = st.scal[0];
+    CR_CUDA(h, cudaMemcpyAsync(P.st, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
+    // eta(theta^(1)_0 = 0): y = h, xi = 0 (foldA of iteration 0 over zero partials)
+    CR_TRY(launch_phase(h, crk::PH_FOLDA, 0, -1.0));
+    CR_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->iters = 0;
+    h->broken = false;
+    return CR_OK;
+}
+
+cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long N, int n, const cr_options *opt,
+                      cr_handle *out)
+{
+    cr_ctx *h = new (std::nothrow) cr_ctx();
+    if (!h) return CR_ENOMEM;
+    *out = h;
+    if (opt) h->opt = *opt;
+    else cr_options_default(&h->opt);
+    cr_options &o = h->opt;
+    if (!(o.gamma > 0.0) || !std::isfinite(o.gamma)) return fail(h, CR_EINVAL, "gamma must be > 0");
+    if (o.theta_dtype < 0 || o.theta_dtype > 2) return fail(h, CR_EINVAL, "unknown theta_dtype %d", o.theta_dtype);
+    if (o.kkt_every < 1) return fail(h, CR_EINVAL, "kkt_every must be >= 1");
+    h->N = N;
+    h->n = n;
+    h->NP = padded_n(n);
+    h->ks = kernels_for(o.theta_dtype, h->NP);
+    if (!h->ks.phase) return fail(h, CR_EINVAL, "no kernel for n = %d", n);
+
+    CR_CUDA(h, cudaGetDevice(&h->device));
+    cudaDeviceProp prop;
+    CR_CUDA(h, cudaGetDeviceProperties(&prop, h->device));
+    if (prop.major * 10 + prop.minor < 100)
+        return fail(h, CR_ECUDA, "device %s (sm_%d%d) is not a Blackwell part", prop.name, prop.major, prop.minor);
+    h->num_sms = prop.multiProcessorCount;
+    if (o.stream) {
+        h->stream = (cudaStream_t)o.stream;
+    } else {
+        CR_CUDA(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    CR_CUDA(h, cudaFuncSetAttribute(h->ks.persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem));
+    CR_CUDA(h, cudaFuncSetAttribute(h->ks.phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem));
+    int per_sm = 0;
+    CR_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, h->ks.persistent, crk::kThreads, h->ks.smem));
+    int coop = 0;
+    CR_CUDA(h, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
+    const int max_coresident = per_sm * h->num_sms;
+
+    // grid: one CTA per (SM x resident slot) by default; small problems use fewer
+    long long S = (N + crk::kW - 1) / crk::kW;
+    long long total = S * N;
+    int G = o.grid > 0 ? o.grid : std::max(1, max_coresident);
+    const long long min_units = 64;   // keep at least 64 (stripe,row) units per CTA
+    if (o.grid <= 0) G = (int)std::max<long long>(1, std::min<long long>(G, total / min_units));
+    h->persistent_ok = coop && per_sm > 0 && G <= max_coresident;
+    if (o.driver == CR_DRIVER_PERSISTENT && !h->persistent_ok)
+        return fail(h, CR_EINVAL, "persistent driver: grid %d exceeds %d co-resident CTAs", G, max_coresident);
+
+    // host constants
+    double s = o.shift >= 0.0 ? o.shift : default_shift(yb);
+    double lo = yb[0], hi = yb[0];
+    for (double v : yb) {
+        lo = std::min(lo, v);
+        hi = std::max(hi, v);
+    }
+    h->sigma = std::max(1.0, hi - lo);
+    double L = o.L > 0.0 ? o.L : (1.0 + 2.0 * (double)N + max_block_eig(X, N, n)) / o.gamma;
+    o.shift = s;
+    o.L = L;
+
+    Params &P = h->P;
+    P.N = N;
+    P.n = n;
+    P.NP = h->NP;
+    h->ld = ((N + 15) / 16) * 16;
+    P.ld = h->ld;
+    P.S = (int)S;
+    P.G = G;
+    P.total = total;
+    P.slots = max_slots(total, N, G);
+    P.gamma = o.gamma;
+    P.inv_gamma = 1.0 / o.gamma;
+    P.L = L;
+    P.invL_d = 1.0 / L;
+    P.invL = (float)(1.0 / L);
+    P.shift = s;
+    P.st_scale = 1.0f;
+    P.st_inv_scale = 1.0f;
+    if (o.theta_dtype == CR_THETA_F16) {
+        P.st_scale = std::ldexp(1.0f, o.fp16_exponent);
+        P.st_inv_scale = std::ldexp(1.0f, -o.fp16_exponent);
+    }
+    P.momentum = o.momentum;
+    P.restart = o.restart;
+    P.sr = o.stochastic_round;
+    P.seed = (unsigned)(o.seed ^ (o.seed >> 32));
+    P.bar_timeout_ns = (unsigned long long)(o.barrier_timeout_ms > 0 ? o.barrier_timeout_ms : 4000) * 1000000ull;
+    P.bar_extra = o.test_barrier_extra > 0 ? o.test_barrier_extra : 0;
+
+    const size_t es = theta_elem_size(o.theta_dtype);
+    for (int b = 0; b < 2; ++b) {
+        void *t = nullptr;
+        CR_TRY(dev_alloc(h, (char **)&t, (size_t)N * h->ld * es));
+        P.theta[b] = t;
+    }
+    double *X64, *hh;
+    float *X32;
+    CR_TRY(dev_alloc(h, &X64, (size_t)N * n));
+    CR_TRY(dev_alloc(h, &X32, (size_t)N * h->NP));
+    CR_TRY(dev_alloc(h, &hh, (size_t)N));
+    P.X64 = X64;
+    P.X32 = X32;
+    P.h = hh;
+    CR_TRY(dev_alloc(h, &P.yrow2, N));
+    CR_TRY(dev_alloc(h, &P.ccol2, N));
+    CR_TRY(dev_alloc(h, &P.xi2, (size_t)N * h->NP));
+    CR_TRY(dev_alloc(h, &P.yrow1, N));
+    CR_TRY(dev_alloc(h, &P.ccol1, N));
+    CR_TRY(dev_alloc(h, &P.xi1, (size_t)N * h->NP));
+    CR_TRY(dev_alloc(h, &P.y1, N));
+    CR_TRY(dev_alloc(h, &P.xi1_64, (size_t)N * n));
+    for (int b = 0; b < 2; ++b) {
+        CR_TRY(dev_alloc(h, &P.v[b], N));
+        CR_TRY(dev_alloc(h, &P.w[b], (size_t)N * n));
+        CR_TRY(dev_alloc(h, &P.mu[b], N));
+    }
+    CR_TRY(dev_alloc(h, &P.rowpart, 2 * (size_t)S * N));
+    CR_TRY(dev_alloc(h, &P.colpart, (size_t)G * P.slots * (h->NP + 1) * crk::kW));
+    CR_TRY(dev_alloc(h, &P.foldpart, (size_t)G * 8));
+    CR_TRY(dev_alloc(h, &P.kktpart, (size_t)G * 8));
+    CR_TRY(dev_alloc(h, &P.st, 1));
+
+    std::vector<float> x32((size_t)N * h->NP, 0.0f);
+    std::vector<double> hv(N);
+    for (long long l = 0; l < N; ++l) {
+        for (int k = 0; k < n; ++k) x32[(size_t)l * h->NP + k] = (float)X[(size_t)l * n + k];
+        hv[l] = yb[l] + s;
+    }
+    CR_CUDA(h, cudaMemcpyAsync(X64, X.data(), sizeof(double) * N * n, cudaMemcpyHostToDevice, h->stream));
+    CR_CUDA(h, cudaMemcpyAsync(X32, x32.data(), sizeof(float) * x32.size(), cudaMemcpyHostToDevice, h->stream));
+    CR_CUDA(h, cudaMemcpyAsync(hh, hv.data(), sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+    return init_state(h);
+}
+
+cr_status check_inputs(const double *X, const double *ybar, long long N, int n)
+{
+    if (!X || !ybar || n < 1 || n > crk::kMaxN || N < (long long)n + 1 || N > (1ll << 31)) return CR_EINVAL;
+    if (!all_finite(X, (size_t)N * n) || !all_finite(ybar, (size_t)N)) return CR_EINVAL;
+    return CR_OK;
+}
+
+// Creation errors have no handle to live on: they are kept per host thread and
+// returned by cr_last_error(NULL).
+thread_local std::string g_create_err;
+
+cr_status create_error(cr_status s, const char *msg)
+{
+    g_create_err = msg;
+    return s;
+}
+
+cr_status finish_create(cr_status s, cr_handle *out)
+{
+    if (s == CR_OK) {
+        g_create_err.clear();
+        return s;
+    }
+    g_create_err = *out ? (*out)->err : std::string(cr_status_str_impl(s));
+    cr_destroy(*out);
+    *out = nullptr;
+    return s;
+}
+
+cr_status usable(cr_ctx *h)
+{
+    if (!h) return CR_EINVAL;
+    if (h->broken) return fail(h, CR_ESTATE, "handle failed a bounded wait; call cr_reset");
+    return CR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cr_options_default(cr_options *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->gamma = 1e-2;
+    o->L = 0.0;
+    o->shift = -1.0;
+    o->theta_dtype = CR_THETA_F32;
+    o->stochastic_round = 1;
+    o->kkt_every = 10;
+    o->momentum = 1;
+    o->restart = 1;
+    o->driver = CR_DRIVER_AUTO;
+    o->grid = 0;
+    o->fp16_exponent = 8;
+    o->seed = 0x5eedULL;
+    o->stream = nullptr;
+}
+
+cr_status cr_create(const double *X, const double *ybar, int64_t N, int32_t n, const cr_options *opt, cr_handle *out)
+{
+    if (!out) return create_error(CR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (check_inputs(X, ybar, N, n) != CR_OK)
+        return create_error(CR_EINVAL, "need X, ybar finite, 1 <= n <= 32 and N >= n + 1");
+    std::vector<double> Xv(X, X + (size_t)N * n), yv(ybar, ybar + N);
+    return finish_create(create_impl(Xv, yv, N, n, opt, out), out);
+}
+
+cr_status cr_create_device(const float *dX, const float *dybar, int64_t N, int32_t n, const cr_options *opt,
+                           cr_handle *out)
+{
+    if (!out) return create_error(CR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!dX || !dybar || n < 1 || n > crk::kMaxN || N < (int64_t)n + 1)
+        return create_error(CR_EINVAL, "need device X, ybar, 1 <= n <= 32 and N >= n + 1");
+    std::vector<float> xf((size_t)N * n), yf(N);
+    cudaError_t e = cudaMemcpy(xf.data(), dX, sizeof(float) * xf.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(yf.data(), dybar, sizeof(float) * yf.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return create_error(CR_ECUDA, cudaGetErrorString(e));
+    }
+    std::vector<double> Xv(xf.begin(), xf.end()), yv(yf.begin(), yf.end());
+    if (check_inputs(Xv.data(), yv.data(), N, n) != CR_OK) return create_error(CR_EINVAL, "non-finite input");
+    return finish_create(create_impl(Xv, yv, N, n, opt, out), out);
+}
+
+cr_status cr_reset(cr_handle h)
+{
+    if (!h) return CR_EINVAL;
+    return init_state(h);
+}
+
+cr_status cr_iterate(cr_handle h, int64_t k)
+{
+    CR_TRY(usable(h));
+    if (k < 0) return fail(h, CR_EINVAL, "k < 0");
+    if (k == 0) return CR_OK;
+    CR_CUDA(h, cudaMemsetAsync(&h->P.st->converged, 0, sizeof(int), h->stream));
+    const long long ell0 = h->iters + 1, ell1 = h->iters + k;
+    const bool pers = h->opt.driver != CR_DRIVER_PHASES && h->persistent_ok;
+    if (pers) CR_TRY(launch_persistent(h, ell0, ell1, 0, -1.0));
+    else CR_TRY(run_phases(h, ell0, ell1, 0, -1.0));
+    h->iters = ell1;
+    return CR_OK;
+}
+
+cr_status cr_solve(cr_handle h, double tol, int64_t max_iter, int64_t *iters_done)
+{
+    CR_TRY(usable(h));
+    if (iters_done) *iters_done = 0;
+    if (max_iter < 0 || !(tol >= 0.0)) return fail(h, CR_EINVAL, "bad tol/max_iter");
+    CR_CUDA(h, cudaMemsetAsync(&h->P.st->converged, 0, sizeof(int), h->stream));
+    const long long start = h->iters;
+    const bool pers = h->opt.driver != CR_DRIVER_PHASES && h->persistent_ok;
+    long long done = 0;
+    const long long chunk = pers ? 20000 : 200;
+    DevState st;
+    while (done < max_iter) {
+        const long long k = std::min<long long>(chunk, max_iter - done);
+        const long long ell0 = h->iters + 1, ell1 = h->iters + k;
+        if (pers) CR_TRY(launch_persistent(h, ell0, ell1, h->opt.kkt_every, tol));
+        else CR_TRY(run_phases(h, ell0, ell1, h->opt.kkt_every, tol));
+        CR_TRY(read_state(h, &st));
+        if (st.converged) {
+            h->iters = st.iters_done;
+            done = h->iters - start;
+            if (iters_done) *iters_done = done;
+            return CR_OK;
+        }
+        h->iters = ell1;
+        done += k;
+    }
+    if (iters_done) *iters_done = done;
+    return CR_NOT_CONVERGED;
+}
+
+cr_status cr_kkt_residual(cr_handle h, double *kkt, double *infeas_norm, double *gap_norm)
+{
+    CR_TRY(usable(h));
+    CR_CUDA(h, cudaMemsetAsync(&h->P.st->converged, 0, sizeof(int), h->stream));
+    CR_TRY(launch_phase(h, crk::PH_KKT64, h->iters, -1.0));
+    CR_TRY(launch_phase(h, crk::PH_DECIDE64, h->iters, -1.0, 1));
+    DevState st;
+    CR_TRY(read_state(h, &st));
+    if (kkt) *kkt = st.kkt[0];
+    if (infeas_norm) *infeas_norm = st.kkt[3];
+    if (gap_norm) *gap_norm = st.kkt[4];
+    return CR_OK;
+}
+
+cr_status cr_objective(cr_handle h, double *primal, double *dual, double *gap)
+{
+    CR_TRY(usable(h));
+    std::vector<double> fp((size_t)h->P.G * 8);
+    CR_CUDA(h, cudaMemcpyAsync(fp.data(), h->P.foldpart, sizeof(double) * fp.size(), cudaMemcpyDeviceToHost,
+                               h->stream));
+    CR_CUDA(h, cudaStreamSynchronize(h->stream));
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = 0; i < h->P.G; ++i) {
+        a += fp[(size_t)i * 8 + 0];
+        b += fp[(size_t)i * 8 + 1];
+        c += fp[(size_t)i * 8 + 2];
+    }
+    // u = y - h:  primal = 1/2||u||^2 + gamma/2||xi||^2,  theta^T C eta = u^T y + gamma ||xi||^2
+    const double pr = 0.5 * a + 0.5 * h->opt.gamma * b;
+    const double gp = c + h->opt.gamma * b;
+    if (primal) *primal = pr;
+    if (gap) *gap = gp;
+    if (dual) *dual = pr - gp;
+    return CR_OK;
+}
+
+cr_status cr_get_solution(cr_handle h, double *yhat, double *xi)
+{
+    CR_TRY(usable(h));
+    if (yhat) {
+        CR_CUDA(h, cudaMemcpyAsync(yhat, h->P.y1, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->stream));
+    }
+    if (xi) {
+        CR_CUDA(h, cudaMemcpyAsync(xi, h->P.xi1_64, sizeof(double) * h->N * h->n, cudaMemcpyDeviceToHost,
+                                   h->stream));
+    }
+    CR_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (yhat)
+        for (long long l = 0; l < h->N; ++l) yhat[l] -= h->P.shift;
+    return CR_OK;
+}
+
+cr_status cr_get_info(cr_handle h, int64_t *iters, int64_t *restarts, double *L, double *shift)
+{
+    if (!h) return CR_EINVAL;
+    if (iters) *iters = h->iters;
+    if (L) *L = h->P.L;
+    if (shift) *shift = h->P.shift;
+    if (restarts) {
+        DevState st;
+        CR_TRY(read_state(h, &st));
+        *restarts = st.scal[h->iters & 1].restarts;
+    }
+    return CR_OK;
+}
+
+cr_status cr_profile(cr_handle h, int32_t kind, double *ms, int64_t *launches)
+{
+    if (!h || kind < 0 || kind > 3) return CR_EINVAL;
+    CR_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (auto &e : h->evs) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, e.a, e.b) == cudaSuccess) {
+            h->prof_ms[e.kind] += t;
+            h->prof_n[e.kind] += 1;
+        }
+        h->pool.push_back(e.a);
+        h->pool.push_back(e.b);
+    }
+    h->evs.clear();
+    if (ms) *ms = h->prof_ms[kind];
+    if (launches) *launches = h->prof_n[kind];
+    h->prof_ms[kind] = 0.0;
+    h->prof_n[kind] = 0;
+    return CR_OK;
+}
+
+void cr_destroy(cr_handle h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (auto &e : h->evs) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+    for (void *p : h->allocs) cudaFree(p);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+const char *cr_status_str(cr_status s) { return cr_status_str_impl(s); }
+
+const char *cr_last_error(cr_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+}  // extern "C"
