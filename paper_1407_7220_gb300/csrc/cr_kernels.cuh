@@ -22,6 +22,7 @@
 // each thread owns 4 adjacent columns (one 16-byte FP32 vector or 8-byte 16-bit vector).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -29,14 +30,21 @@
 
 namespace crk {
 
-constexpr int kThreads = 256;   // 8 warps
+constexpr int kCons = 256;      // consumer threads (8 warps) of the pair pass
+constexpr int kThreads = 288;   // + 1 producer warp
 constexpr int kW = 256;         // stripe width (columns)
-constexpr int kWR = 4;          // row groups per CTA
-constexpr int kRowUnroll = 4;   // rows in flight per thread in the pair pass
+constexpr int kWR = 4;          // row groups of consumer warps (2 warps per row)
+constexpr int kRS = 8;          // rows per pipeline stage
+constexpr int kMaxStages = 8;
+
+template <int NP> struct RecLayout {
+    static constexpr int REC = ((NP + 1 + 3) / 4) * 4;   // floats per row record (16-byte multiple)
+};
 
 enum : int {
     ERR_BARRIER = 1,   // grid barrier wait exceeded its bound
     ERR_NUMERIC = 2,   // non-finite value in the fold
+    ERR_PIPE = 3,      // a pipeline (mbarrier) wait exceeded its bound
 };
 
 // Per-iteration scalar state; two slots indexed by iteration parity so that the
@@ -59,6 +67,7 @@ struct DevState {
 };
 
 struct Params {
+    CUtensorMap tmap[2];    // TMA descriptors of theta[0], theta[1]: N x N, box kRS x kW
     // sizes
     long long N;
     int n;
@@ -79,9 +88,9 @@ struct Params {
     // arrays
     void *theta[2];
     const double *X64;      // N x n
-    const float *X32;       // N x NP (zero padded)
+    float *rowrec;          // N x REC row records {y(theta^(2)) - s, x_1..x_n, 0...} (FP32)
     const double *h;        // N, ybar + s
-    float *yrow2, *ccol2, *xi2;     // eta(theta^(2)) for the pair pass: y-s, xi.x - (y-s), xi
+    float *ccol2, *xi2;     // column data at theta^(2): xi.x - (y - s), xi (N x NP)
     float *yrow1, *ccol1, *xi1;     // same at theta^(1) (KKT screen)
     double *y1, *xi1_64;            // eta(theta^(1)) in FP64 (y shifted)
     double *v[2];           // A_1^T theta^(1) of the two latest iterates (N)
@@ -216,6 +225,56 @@ __device__ __forceinline__ unsigned long long globaltimer()
     return t;
 }
 
+// --- PTX wrappers: mbarrier, TMA, proxy fence, named barrier ---
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// generic-proxy writes (earlier phases) ordered before async-proxy (TMA) reads
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+__device__ __forceinline__ void named_barrier_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll
@@ -297,6 +356,22 @@ __device__ __forceinline__ long long unit_begin(const Params &P, long long c)
     return (long long)(((unsigned long long)c * (unsigned long long)P.total) / (unsigned long long)P.G);
 }
 
+// Bounded mbarrier phase wait: gives up (and sets the error word) after the
+// barrier bound, or at once when another CTA already reported an error.
+__device__ __forceinline__ bool mbar_wait(const Params &P, uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*((volatile int *)&P.st->error) != 0) return false;
+        if (globaltimer() - t0 > P.bar_timeout_ns) {
+            atomicCAS(&P.st->error, 0, ERR_PIPE);
+            return false;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // foldB(l): Step 1 at theta^(2)_l (by linearity), mu update, Steps 3-4 scalars
 // ---------------------------------------------------------------------------
@@ -365,126 +440,216 @@ __device__ void phase_foldB(const Params &P, long long ell, double *red)
             }
             P.xi2[l * NP + k] = xf;
         }
-        P.yrow2[l] = (float)ys;
+        P.rowrec[l * RecLayout<NP>::REC] = (float)ys;
         P.ccol2[l] = (float)(d - ys);
     }
 }
 
 // ---------------------------------------------------------------------------
 // pair(l): Step 2 over all pairs + fused adjoint partial sums
+//
+// Warp-specialized pipeline per CTA: warp 8 (one lane) is the producer -- for every
+// stage of kRS rows of the current stripe it issues two tiled TMA loads
+// (cp.async.bulk.tensor.2d) of the theta^(1)_{l-1} and theta^(1)_{l-2} tiles
+// [kRS x 256] and one bulk copy of the kRS row records (y_row, x), completing on the
+// stage's "full" mbarrier.  Warps 0-7 consume: each takes 2 rows x 128 columns of the
+// stage from shared memory, writes theta^(1)_l straight to global memory (16-byte or
+// 8-byte vector stores) and arrives on the stage's "empty" mbarrier.  Out-of-range
+// rows/columns of a tile are zero-filled by the TMA unit.
 // ---------------------------------------------------------------------------
+
+template <typename TS, int NP> struct PairSmem {
+    static constexpr int REC = RecLayout<NP>::REC;
+    static constexpr int kStages = sizeof(TS) == 4 ? 5 : 8;
+    static constexpr size_t tile_bytes = (size_t)kRS * kW * sizeof(TS);
+    static constexpr size_t rec_bytes = (size_t)kRS * REC * sizeof(float);
+    static constexpr size_t stage_bytes = 2 * tile_bytes + rec_bytes;
+    static constexpr size_t flush_bytes = (size_t)kWR * (NP + 1) * kW * sizeof(float);
+    static constexpr size_t bytes = kStages * stage_bytes + flush_bytes + 128;   // + base alignment slack
+    static_assert(tile_bytes % 128 == 0 && rec_bytes % 128 == 0, "stage buffers must stay 128-byte aligned");
+};
+
+// One row of one warp: 4 columns per lane.  MASK handles the diagonal (l1 == l2)
+// and columns >= N; rows without either take the unmasked instantiation.
+template <typename TS, int NP, bool MASK>
+__device__ __forceinline__ float pair_row(const float (&tc)[4], const float (&tp)[4], const float (&xr)[NP], float yr,
+                                          const float (&ccol)[4], const float (&xi)[4][NP], float (&acc)[4][NP],
+                                          float (&csum)[4], float beta, float invL, bool sr, uint32_t h, float scl,
+                                          float iscl, long long col0, long long row, long long N, float (&outv)[4])
+{
+    using St = Store<TS>;
+    const uint32_t h2 = (h ^ (h >> 15)) * 0x2C1B3C6Du;
+    const uint32_t rnd[4] = {h & 0xFFFFu, h >> 16, h2 & 0xFFFFu, h2 >> 16};
+    float rs = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float th2 = fmaf(beta, tc[j] - tp[j], tc[j]);     // theta^(2) = theta^(1) + beta (theta^(1) - prev)
+        float g = yr + ccol[j];                                 // (C eta)_p = y_l1 - y_l2 + xi_l2.x_l2 - xi_l2.x_l1
+#pragma unroll
+        for (int k = 0; k < NP; ++k) g = fmaf(-xi[j][k], xr[k], g);
+        float sv = St::round(th2, g, invL, sr, rnd[j], scl);    // Pi_{theta >= 0}(theta^(2) - g / L)
+        if (MASK) {
+            if (col0 + j >= N || col0 + j == row) sv = 0.0f;
+        }
+        outv[j] = sv;
+        const float vv = St::decoded(sv, iscl);
+        rs += vv;                                               // row sum      (A_1^T, + part)
+        csum[j] += vv;                                          // column sum   (A_1^T, - part)
+#pragma unroll
+        for (int k = 0; k < NP; ++k) acc[j][k] = fmaf(vv, xr[k], acc[j][k]);   // theta^T X (A_2^T)
+    }
+    return rs;
+}
+
 template <typename TS, int NP>
-__device__ void phase_pair(const Params &P, long long ell, float *sm)
+__device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, uint64_t *full, uint64_t *empty,
+                           unsigned long long &kstage)
 {
     using St = Store<TS>;
     using Vec = typename St::Vec;
+    using L = PairSmem<TS, NP>;
+    constexpr int REC = L::REC;
+    constexpr int S = L::kStages;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wc = warp & 1, wr = warp >> 1;
     const int p = (int)(ell & 1), c = 1 - p;
-    const TS *__restrict__ cur = (const TS *)P.theta[c];
-    TS *__restrict__ nxt = (TS *)P.theta[p];   // holds theta^(1)_{l-2} on entry
-    const float beta = (float)__ldcg(&P.st->scal[p].beta);
-    const float invL = P.invL;
-    const float scl = P.st_scale, iscl = P.st_inv_scale;
-    const bool sr = P.sr != 0;
-    const uint32_t rseed = P.seed ^ (uint32_t)ell * 0x632BE5ABu;
     const long long N = P.N, ld = P.ld;
-
-    long long u = unit_begin(P, blockIdx.x);
+    const long long ubeg = unit_begin(P, blockIdx.x);
     const long long uend = unit_begin(P, blockIdx.x + 1);
-    const long long first_stripe = u / N;
-    while (u < uend) {
-        const long long s = u / N;
-        const long long r0 = u - s * N;
-        const long long r1 = min(N, r0 + (uend - u));
-        const long long col0 = s * kW + wc * 128 + lane * 4;
-        const bool vec_ok = col0 < ld;
-        float ccol[4], xi[4][NP];
-        bool colv[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            long long cj = col0 + j;
-            colv[j] = cj < N;
-            ccol[j] = colv[j] ? __ldcg(P.ccol2 + cj) : 0.0f;
-#pragma unroll
-            for (int k = 0; k < NP; ++k) xi[j][k] = colv[j] ? __ldcg(P.xi2 + cj * NP + k) : 0.0f;
-        }
-        float acc[4][NP], csum[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            csum[j] = 0.0f;
-#pragma unroll
-            for (int k = 0; k < NP; ++k) acc[j][k] = 0.0f;
-        }
-        float *rp = P.rowpart + (s * 2 + wc) * N;
+    unsigned char *stage0 = smem;
+    float *flush = reinterpret_cast<float *>(smem + S * L::stage_bytes);
 
-        for (long long rb = r0 + wr; rb < r1; rb += kWR * kRowUnroll) {
-            Vec vc[kRowUnroll], vp[kRowUnroll];
-#pragma unroll
-            for (int q = 0; q < kRowUnroll; ++q) {
-                long long r = rb + (long long)q * kWR;
-                if (r < r1 && vec_ok) {
-                    vc[q] = __ldcg((const Vec *)(cur + r * ld + col0));
-                    vp[q] = __ldcg((const Vec *)(nxt + r * ld + col0));
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < kRowUnroll; ++q) {
-                long long r = rb + (long long)q * kWR;
-                if (r >= r1) break;   // warp-uniform
-                float xr[NP];
-#pragma unroll
-                for (int k = 0; k < NP; ++k) xr[k] = __ldg(P.X32 + r * NP + k);
-                const float yr = __ldcg(P.yrow2 + r);
-                float tc[4] = {0.f, 0.f, 0.f, 0.f}, tp[4] = {0.f, 0.f, 0.f, 0.f};
-                if (vec_ok) {
-                    St::unpack(vc[q], tc, iscl);
-                    St::unpack(vp[q], tp, iscl);
-                }
-                float outv[4];
-                float rs = 0.0f;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float th2 = fmaf(beta, tc[j] - tp[j], tc[j]);
-                    float g = yr + ccol[j];
-#pragma unroll
-                    for (int k = 0; k < NP; ++k) g = fmaf(-xi[j][k], xr[k], g);
-                    uint32_t rnd = sr ? hash3((uint32_t)r, (uint32_t)(col0 + j), rseed) : 0u;
-                    float sv = St::round(th2, g, invL, sr, rnd, scl);
-                    if (!colv[j] || (col0 + j) == r) sv = 0.0f;
-                    outv[j] = sv;
-                    const float vv = St::decoded(sv, iscl);
-                    rs += vv;
-                    csum[j] += vv;
-#pragma unroll
-                    for (int k = 0; k < NP; ++k) acc[j][k] = fmaf(vv, xr[k], acc[j][k]);
-                }
-                if (vec_ok) *((Vec *)(nxt + r * ld + col0)) = St::pack(outv);
-                rs = warp_sum(rs);
-                if (lane == 0) rp[r] = rs;
-            }
-        }
-        // column partials: reduce the 4 row groups in shared memory, then one slot write
-        const int slot = (int)(s - first_stripe);
-        float *cp = P.colpart + ((long long)blockIdx.x * P.slots + slot) * (NP + 1) * kW;
-        const int cl = wc * 128 + lane * 4;
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            sm[(wr * (NP + 1) + 0) * kW + cl + j] = csum[j];
-#pragma unroll
-            for (int k = 0; k < NP; ++k) sm[(wr * (NP + 1) + 1 + k) * kW + cl + j] = acc[j][k];
-        }
-        __syncthreads();
-        for (int e = tid; e < (NP + 1) * kW; e += kThreads) {
-            float a = sm[e];
-#pragma unroll
-            for (int q = 1; q < kWR; ++q) a += sm[q * (NP + 1) * kW + e];
-            cp[e] = a;
-        }
-        __syncthreads();
-        u += (r1 - r0);
+    // number of stages of this pass (identical in every thread)
+    unsigned long long nst = 0;
+    for (long long u = ubeg; u < uend;) {
+        const long long s = u / N, r0 = u - s * N, r1 = min(N, r0 + (uend - u));
+        nst += (unsigned long long)((r1 - r0 + kRS - 1) / kRS);
+        u += r1 - r0;
     }
+
+    if (warp == kCons / 32) {
+        // ---------------- producer ----------------
+        if (lane == 0) {
+            fence_proxy_async();
+            unsigned long long k = kstage;
+            bool ok = true;
+            for (long long u = ubeg; u < uend && ok;) {
+                const long long s = u / N, r0 = u - s * N, r1 = min(N, r0 + (uend - u));
+                for (long long r = r0; r < r1; r += kRS, ++k) {
+                    const int slot = (int)(k % S);
+                    const unsigned long long round = k / S;
+                    if (round > 0 && !mbar_wait(P, &empty[slot], (uint32_t)((round - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    const int nrows = (int)min((long long)kRS, r1 - r);
+                    unsigned char *st = stage0 + slot * L::stage_bytes;
+                    mbar_arrive_expect_tx(&full[slot], (uint32_t)(2 * L::tile_bytes + (size_t)nrows * REC * 4));
+                    tma_load_2d(st, &P.tmap[c], (int)(s * kW), (int)r, &full[slot]);
+                    tma_load_2d(st + L::tile_bytes, &P.tmap[p], (int)(s * kW), (int)r, &full[slot]);
+                    bulk_load(st + 2 * L::tile_bytes, P.rowrec + r * REC, (uint32_t)(nrows * REC * 4), &full[slot]);
+                }
+                u += r1 - r0;
+            }
+        }
+    } else {
+        // ---------------- consumers ----------------
+        const int wc = warp & 1, rg = warp >> 1;
+        const float beta = (float)__ldcg(&P.st->scal[p].beta);
+        const float invL = P.invL;
+        const float scl = P.st_scale, iscl = P.st_inv_scale;
+        const bool sr = P.sr != 0;
+        const uint32_t rseed = P.seed ^ (uint32_t)ell * 0x632BE5ABu;
+        TS *__restrict__ nxt = (TS *)P.theta[p];   // theta^(1)_{l-2} on entry, theta^(1)_l on exit
+        const long long first_stripe = ubeg / N;
+        unsigned long long k = kstage;
+        bool ok = true;
+        for (long long u = ubeg; u < uend;) {
+            const long long s = u / N, r0 = u - s * N, r1 = min(N, r0 + (uend - u));
+            const long long colw = s * kW + wc * 128;       // first column of this warp
+            const long long col0 = colw + lane * 4;
+            const bool vec_ok = col0 < ld;
+            const bool ragged = (s * kW + kW) > N;
+            float ccol[4], xi[4][NP];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const long long cj = col0 + j;
+                const bool v = cj < N;
+                ccol[j] = v ? __ldcg(P.ccol2 + cj) : 0.0f;
+#pragma unroll
+                for (int q = 0; q < NP; ++q) xi[j][q] = v ? __ldcg(P.xi2 + cj * NP + q) : 0.0f;
+            }
+            float acc[4][NP], csum[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                csum[j] = 0.0f;
+#pragma unroll
+                for (int q = 0; q < NP; ++q) acc[j][q] = 0.0f;
+            }
+            float *rp = P.rowpart + (s * 2 + wc) * N;
+            for (long long r = r0; r < r1; r += kRS, ++k) {
+                const int slot = (int)(k % S);
+                if (ok && !mbar_wait(P, &full[slot], (uint32_t)((k / S) & 1))) ok = false;
+                if (ok) {
+                    const unsigned char *st = stage0 + slot * L::stage_bytes;
+                    const TS *tcur = reinterpret_cast<const TS *>(st);
+                    const TS *tprv = reinterpret_cast<const TS *>(st + L::tile_bytes);
+                    const float *rec = reinterpret_cast<const float *>(st + 2 * L::tile_bytes);
+#pragma unroll
+                    for (int i = 0; i < kRS / kWR; ++i) {
+                        const int rl = rg + i * kWR;
+                        const long long rr = r + rl;
+                        if (rr >= r1) break;   // warp-uniform
+                        float rv[REC];
+#pragma unroll
+                        for (int q = 0; q < REC; q += 4) {
+                            const float4 t4 = *reinterpret_cast<const float4 *>(rec + rl * REC + q);
+                            rv[q] = t4.x; rv[q + 1] = t4.y; rv[q + 2] = t4.z; rv[q + 3] = t4.w;
+                        }
+                        float xr[NP];
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) xr[q] = rv[1 + q];
+                        float tc[4], tp[4], outv[4];
+                        St::unpack(*reinterpret_cast<const Vec *>(tcur + rl * kW + wc * 128 + lane * 4), tc, iscl);
+                        St::unpack(*reinterpret_cast<const Vec *>(tprv + rl * kW + wc * 128 + lane * 4), tp, iscl);
+                        const uint32_t h = sr ? hash3((uint32_t)rr, (uint32_t)(col0 >> 2), rseed) : 0u;
+                        float rs;
+                        if (ragged || (rr >= colw && rr < colw + 128))
+                            rs = pair_row<TS, NP, true>(tc, tp, xr, rv[0], ccol, xi, acc, csum, beta, invL, sr, h, scl,
+                                                        iscl, col0, rr, N, outv);
+                        else
+                            rs = pair_row<TS, NP, false>(tc, tp, xr, rv[0], ccol, xi, acc, csum, beta, invL, sr, h,
+                                                         scl, iscl, col0, rr, N, outv);
+                        if (vec_ok) *reinterpret_cast<Vec *>(nxt + rr * ld + col0) = St::pack(outv);
+                        rs = warp_sum(rs);
+                        if (lane == 0) rp[rr] = rs;
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+            }
+            // column partials of this segment: reduce the 4 row groups in shared memory
+            const int slotc = (int)(s - first_stripe);
+            float *cp = P.colpart + ((long long)blockIdx.x * P.slots + slotc) * (NP + 1) * kW;
+            const int cl = wc * 128 + lane * 4;
+            named_barrier_sync(1, kCons);
+            *reinterpret_cast<float4 *>(flush + (rg * (NP + 1)) * kW + cl) = make_float4(csum[0], csum[1], csum[2], csum[3]);
+#pragma unroll
+            for (int q = 0; q < NP; ++q)
+                *reinterpret_cast<float4 *>(flush + (rg * (NP + 1) + 1 + q) * kW + cl) =
+                    make_float4(acc[0][q], acc[1][q], acc[2][q], acc[3][q]);
+            named_barrier_sync(1, kCons);
+            for (int e = tid; e < (NP + 1) * kW; e += kCons) {
+                float a = flush[e];
+#pragma unroll
+                for (int q = 1; q < kWR; ++q) a += flush[q * (NP + 1) * kW + e];
+                cp[e] = a;
+            }
+            named_barrier_sync(1, kCons);
+            u += r1 - r0;
+        }
+    }
+    kstage += nst;
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -575,10 +740,11 @@ __device__ void phase_kkt(const Params &P, long long ell, double *red)
     const long long N = P.N, ld = P.ld;
     const int n = P.n;
     double mviol = 0.0, mcomp = 0.0, sviol = 0.0, sthg = 0.0;
+    constexpr int REC = RecLayout<NP>::REC;
 
     long long u = unit_begin(P, blockIdx.x);
     const long long uend = unit_begin(P, blockIdx.x + 1);
-    while (u < uend) {
+    while (warp < kCons / 32 && u < uend) {
         const long long s = u / N;
         const long long r0 = u - s * N;
         const long long r1 = min(N, r0 + (uend - u));
@@ -608,7 +774,7 @@ __device__ void phase_kkt(const Params &P, long long ell, double *red)
                 const float yr = __ldcg(P.yrow1 + r);
                 float xr[NP];
 #pragma unroll
-                for (int k = 0; k < NP; ++k) xr[k] = __ldg(P.X32 + r * NP + k);
+                for (int k = 0; k < NP; ++k) xr[k] = __ldcg(P.rowrec + r * REC + 1 + k);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const long long l2 = col0 + j;

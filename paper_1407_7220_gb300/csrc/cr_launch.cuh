@@ -8,8 +8,27 @@ namespace crk {
 
 enum Phase : int { PH_FOLDB = 0, PH_PAIR = 1, PH_FOLDA = 2, PH_KKT32 = 3, PH_KKT64 = 4, PH_DECIDE32 = 5, PH_DECIDE64 = 6 };
 
-// Shared memory of the pair pass: column partials of the 4 row groups.
-template <int NP> constexpr size_t pair_smem_bytes() { return (size_t)kWR * (NP + 1) * kW * sizeof(float); }
+// Dynamic shared memory of the pair pass (pipeline stages + column-partial reduction).
+template <typename TS, int NP> constexpr size_t pair_smem_bytes() { return PairSmem<TS, NP>::bytes; }
+
+// 128-byte aligned base of the dynamic shared memory (TMA destinations).
+__device__ __forceinline__ unsigned char *aligned_smem(unsigned char *raw)
+{
+    const uint32_t a = smem_u32(raw);
+    return raw + ((128u - (a & 127u)) & 127u);
+}
+
+__device__ __forceinline__ void init_pipeline(uint64_t *full, uint64_t *empty)
+{
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kMaxStages; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kCons / 32);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
 
 // Persistent driver: iterations ell0..ell1 in one cooperative launch.  Phases are
 // separated by bounded grid barriers; every CTA takes the same decisions from the
@@ -17,18 +36,21 @@ template <int NP> constexpr size_t pair_smem_bytes() { return (size_t)kWR * (NP 
 // FP64 confirmation) every check_every iterations and at ell1.
 template <typename TS, int NP>
 __global__ void __launch_bounds__(kThreads, 1)
-k_persistent(Params P, long long ell0, long long ell1, int check_every, double tol, double sigma)
+k_persistent(const __grid_constant__ Params P, long long ell0, long long ell1, int check_every, double tol,
+             double sigma)
 {
-    extern __shared__ float4 sm_raw[];
-    float *sm = reinterpret_cast<float *>(sm_raw);
-    __shared__ double red[64];
+    extern __shared__ unsigned char sm_raw[];
+    unsigned char *sm = aligned_smem(sm_raw);
+    __shared__ double red[72];
     __shared__ double s_m[8];
-    unsigned long long bar = 0;
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
+    unsigned long long bar = 0, kstage = 0;
+    init_pipeline(full, empty);
 
     phase_foldB<NP>(P, ell0, red);
     if (!grid_barrier(P, bar)) return;
     for (long long ell = ell0; ell <= ell1; ++ell) {
-        phase_pair<TS, NP>(P, ell, sm);
+        phase_pair<TS, NP>(P, ell, sm, full, empty, kstage);
         if (!grid_barrier(P, bar)) return;
         phase_foldA<NP>(P, ell, red);
         if (!grid_barrier(P, bar)) return;
@@ -81,17 +103,22 @@ k_persistent(Params P, long long ell0, long long ell1, int check_every, double t
 // calls).  Every kernel is a no-op once the state says converged or failed.
 template <typename TS, int NP>
 __global__ void __launch_bounds__(kThreads, 1)
-k_phase(Params P, int phase, long long ell, double tol, double sigma)
+k_phase(const __grid_constant__ Params P, int phase, long long ell, double tol, double sigma)
 {
-    extern __shared__ float4 sm_raw[];
-    float *sm = reinterpret_cast<float *>(sm_raw);
-    __shared__ double red[64];
+    extern __shared__ unsigned char sm_raw[];
+    __shared__ double red[72];
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
     const int conv = __ldcg(&P.st->converged), err = __ldcg(&P.st->error);
     if (err != 0) return;
     if (conv != 0 && phase != PH_KKT64 && phase != PH_DECIDE64) return;
     switch (phase) {
     case PH_FOLDB: phase_foldB<NP>(P, ell, red); break;
-    case PH_PAIR: phase_pair<TS, NP>(P, ell, sm); break;
+    case PH_PAIR: {
+        unsigned long long kstage = 0;
+        init_pipeline(full, empty);
+        phase_pair<TS, NP>(P, ell, aligned_smem(sm_raw), full, empty, kstage);
+        break;
+    }
     case PH_FOLDA: phase_foldA<NP>(P, ell, red); break;
     case PH_KKT32: phase_kkt<TS, NP, false>(P, ell, red); break;
     case PH_KKT64: phase_kkt<TS, NP, true>(P, ell, red); break;
@@ -122,9 +149,9 @@ k_phase(Params P, int phase, long long ell, double tol, double sigma)
 // KKT64 pass that runs only if the preceding FP32 screen passed (phase path).
 template <typename TS, int NP>
 __global__ void __launch_bounds__(kThreads, 1)
-k_kkt64_if_screened(Params P, long long ell)
+k_kkt64_if_screened(const __grid_constant__ Params P, long long ell)
 {
-    __shared__ double red[64];
+    __shared__ double red[72];
     if (__ldcg(&P.st->error) != 0 || __ldcg(&P.st->kkt[6]) == 0.0) return;
     phase_kkt<TS, NP, true>(P, ell, red);
 }
@@ -143,7 +170,7 @@ template <typename TS, int NP> KernelSet make_set()
     k.persistent = (const void *)k_persistent<TS, NP>;
     k.phase = (const void *)k_phase<TS, NP>;
     k.kkt64_if = (const void *)k_kkt64_if_screened<TS, NP>;
-    k.smem = pair_smem_bytes<NP>();
+    k.smem = pair_smem_bytes<TS, NP>();
     k.NP = NP;
     return k;
 }

@@ -4,6 +4,8 @@
 // (shift s, step constant L_g of Eq. (eq:lischitz)) in FP64 on the host, and
 // drives the iteration either as one cooperative persistent launch per call or
 // as one launch per phase.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -110,6 +112,23 @@ KernelSet kernels_for(int dtype, int NP)
 }
 
 size_t theta_elem_size(int dtype) { return dtype == CR_THETA_F32 ? 4 : 2; }
+
+int rec_floats(int NP) { return ((NP + 1 + 3) / 4) * 4; }
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link-time libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
 
 // ---- problem constants (host, FP64) ----------------------------------------
 
@@ -460,15 +479,30 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
         CR_TRY(dev_alloc(h, (char **)&t, (size_t)N * h->ld * es));
         P.theta[b] = t;
     }
+    // TMA descriptors of the two multiplier arrays: N x N elements, row pitch ld, box kRS x kW;
+    // out-of-range rows/columns read as zero
+    auto encode = tensor_map_encoder();
+    if (!encode) return fail(h, CR_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const CUtensorMapDataType tdt = o.theta_dtype == CR_THETA_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                    : o.theta_dtype == CR_THETA_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    for (int b = 0; b < 2; ++b) {
+        cuuint64_t gdim[2] = {(cuuint64_t)N, (cuuint64_t)N};
+        cuuint64_t gstride[1] = {(cuuint64_t)h->ld * es};
+        cuuint32_t box[2] = {(cuuint32_t)crk::kW, (cuuint32_t)crk::kRS};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = encode(&P.tmap[b], tdt, 2, P.theta[b], gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(h, CR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
+    const int REC = rec_floats(h->NP);
     double *X64, *hh;
-    float *X32;
     CR_TRY(dev_alloc(h, &X64, (size_t)N * n));
-    CR_TRY(dev_alloc(h, &X32, (size_t)N * h->NP));
+    CR_TRY(dev_alloc(h, &P.rowrec, (size_t)N * REC));
     CR_TRY(dev_alloc(h, &hh, (size_t)N));
     P.X64 = X64;
-    P.X32 = X32;
     P.h = hh;
-    CR_TRY(dev_alloc(h, &P.yrow2, N));
     CR_TRY(dev_alloc(h, &P.ccol2, N));
     CR_TRY(dev_alloc(h, &P.xi2, (size_t)N * h->NP));
     CR_TRY(dev_alloc(h, &P.yrow1, N));
@@ -487,14 +521,15 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     CR_TRY(dev_alloc(h, &P.kktpart, (size_t)G * 8));
     CR_TRY(dev_alloc(h, &P.st, 1));
 
-    std::vector<float> x32((size_t)N * h->NP, 0.0f);
+    // row records {y - s (set by every fold), x_1..x_n, 0 ...}
+    std::vector<float> rec((size_t)N * REC, 0.0f);
     std::vector<double> hv(N);
     for (long long l = 0; l < N; ++l) {
-        for (int k = 0; k < n; ++k) x32[(size_t)l * h->NP + k] = (float)X[(size_t)l * n + k];
+        for (int k = 0; k < n; ++k) rec[(size_t)l * REC + 1 + k] = (float)X[(size_t)l * n + k];
         hv[l] = yb[l] + s;
     }
     CR_CUDA(h, cudaMemcpyAsync(X64, X.data(), sizeof(double) * N * n, cudaMemcpyHostToDevice, h->stream));
-    CR_CUDA(h, cudaMemcpyAsync(X32, x32.data(), sizeof(float) * x32.size(), cudaMemcpyHostToDevice, h->stream));
+    CR_CUDA(h, cudaMemcpyAsync(P.rowrec, rec.data(), sizeof(float) * rec.size(), cudaMemcpyHostToDevice, h->stream));
     CR_CUDA(h, cudaMemcpyAsync(hh, hv.data(), sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
     return init_state(h);
 }
