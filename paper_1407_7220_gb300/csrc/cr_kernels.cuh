@@ -30,8 +30,8 @@
 
 namespace crk {
 
-constexpr int kCons = 256;      // consumer threads (8 warps) of the pair pass
-constexpr int kThreads = 288;   // + 1 producer warp
+constexpr int kThreads = 256;   // 8 warps per CTA
+constexpr int kCons = kThreads; // every warp consumes pair-pass stages; lane 0 of warp 0 also produces them
 constexpr int kW = 256;         // stripe width (columns)
 constexpr int kWR = 4;          // row groups of consumer warps (2 warps per row)
 constexpr int kRS = 8;          // rows per pipeline stage
@@ -127,23 +127,24 @@ template <> struct Store<float> {
     {
         o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
     }
-    // v = th2 - g*invL computed by the caller as fmaf(-g, invL, th2) = RN(exact);
-    // err approximates the rounding residual (exact when th2 and v are within 2x).
-    __device__ static __forceinline__ float round(float th2, float g, float invL, bool sr, uint32_t rnd, float)
+    // Projected update max(0, th2 - g/L) rounded to the stored type.  v = RN(th2 - g*invL);
+    // with SR the rounding residual e (exact while th2 and v are within 2x) decides the
+    // unbiased step to a neighbour: k = floor(e/ulp(v) + u), u uniform in [0,1) from 16 bits.
+    template <bool SR>
+    __device__ static __forceinline__ float round(float th2, float g, float invL, uint32_t rnd16, float)
     {
-        float v = fmaf(-g, invL, th2);
-        if (!(v > 0.0f)) return 0.0f;
-        if (sr) {
-            float err = fmaf(-g, invL, th2 - v);
-            if (err != 0.0f) {
-                uint32_t b = __float_as_uint(v);
-                float nb = __uint_as_float(err > 0.0f ? b + 1u : b - 1u);
-                float d = fabsf(nb - v);
-                // move to the neighbour with probability |err| / d
-                if ((float)(rnd >> 8) * d < fabsf(err) * 16777216.0f) v = nb;
-            }
+        const float v = fmaf(-g, invL, th2);
+        float r = v;
+        if (SR) {
+            const float e = fmaf(-g, invL, th2 - v);
+            const uint32_t b = __float_as_uint(v);
+            const uint32_t ef = max(b & 0x7F800000u, 23u << 23);
+            const float inv_ulp = __uint_as_float(0x8A800000u - ef);          // 2^(23 - exponent(v))
+            const float u1 = __uint_as_float(0x3F800000u | (rnd16 << 7));     // 1 + u
+            const int kk = __float2int_rd(fmaf(e, inv_ulp, u1));             // floor(e/ulp + u) + 1
+            r = __uint_as_float(b + (uint32_t)kk - 1u);
         }
-        return v;
+        return v > 0.0f ? r : 0.0f;
     }
     __device__ static __forceinline__ float encode(float v, float) { return v; }
     __device__ static __forceinline__ Vec pack(const float (&s)[4]) { return make_float4(s[0], s[1], s[2], s[3]); }
@@ -159,15 +160,15 @@ template <> struct Store<__nv_bfloat16> {
         o[2] = b2f(v.y & 0xFFFFu); o[3] = b2f(v.y >> 16);
     }
     // returns the value actually stored (as float); bf16 bits kept in the float's top half
-    __device__ static __forceinline__ float round(float th2, float g, float invL, bool sr, uint32_t rnd, float)
+    template <bool SR>
+    __device__ static __forceinline__ float round(float th2, float g, float invL, uint32_t rnd16, float)
     {
-        float v = fmaf(-g, invL, th2);
-        if (!(v > 0.0f)) return 0.0f;
+        const float v = fmaf(-g, invL, th2);
         uint32_t b = __float_as_uint(v);
-        if (sr) b += (rnd & 0xFFFFu);                              // stochastic: add uniform 16-bit noise, truncate
+        if (SR) b += rnd16;                                        // stochastic: add uniform 16-bit noise, truncate
         else b += 0x7FFFu + ((b >> 16) & 1u);                      // round to nearest even
         b &= 0xFFFF0000u;
-        return __uint_as_float(b);
+        return v > 0.0f ? __uint_as_float(b) : 0.0f;
     }
     __device__ static __forceinline__ Vec pack(const float (&s)[4])
     {
@@ -191,19 +192,21 @@ template <> struct Store<__half> {
         o[2] = h2f(v.y & 0xFFFFu, inv_scale); o[3] = h2f(v.y >> 16, inv_scale);
     }
     // returns the scaled half value (as float, exactly representable in fp16)
-    __device__ static __forceinline__ float round(float th2, float g, float invL, bool sr, uint32_t rnd, float scale)
+    template <bool SR>
+    __device__ static __forceinline__ float round(float th2, float g, float invL, uint32_t rnd16, float scale)
     {
-        float v = fmaf(-g, invL, th2);
-        if (!(v > 0.0f)) return 0.0f;
-        float sv = fminf(v * scale, 65504.0f);
-        __half hz = __float2half_rz(sv);
-        if (sr) {
-            float lo = __half2float(hz);
-            float hi = __half2float(__ushort_as_half((unsigned short)(__half_as_ushort(hz) + 1)));
-            if (sv > lo && (float)(rnd >> 8) * (hi - lo) < (sv - lo) * 16777216.0f) return hi;
-            return lo;
+        const float v = fmaf(-g, invL, th2);
+        const float sv = fminf(fmaxf(v, 0.0f) * scale, 65504.0f);
+        float r;
+        if (SR) {
+            const __half hz = __float2half_rz(sv);
+            const float lo = __half2float(hz);
+            const float hi = __half2float(__ushort_as_half((unsigned short)(__half_as_ushort(hz) + 1)));
+            r = ((float)rnd16 * (hi - lo) < (sv - lo) * 65536.0f) ? hi : lo;
+        } else {
+            r = __half2float(__float2half_rn(sv));
         }
-        return __half2float(__float2half_rn(sv));
+        return v > 0.0f ? r : 0.0f;
     }
     __device__ static __forceinline__ Vec pack(const float (&s)[4])
     {
@@ -469,36 +472,151 @@ template <typename TS, int NP> struct PairSmem {
     static_assert(tile_bytes % 128 == 0 && rec_bytes % 128 == 0, "stage buffers must stay 128-byte aligned");
 };
 
-// One row of one warp: 4 columns per lane.  MASK handles the diagonal (l1 == l2)
-// and columns >= N; rows without either take the unmasked instantiation.
-template <typename TS, int NP, bool MASK>
-__device__ __forceinline__ float pair_row(const float (&tc)[4], const float (&tp)[4], const float (&xr)[NP], float yr,
-                                          const float (&ccol)[4], const float (&xi)[4][NP], float (&acc)[4][NP],
-                                          float (&csum)[4], float beta, float invL, bool sr, uint32_t h, float scl,
-                                          float iscl, long long col0, long long row, long long N, float (&outv)[4])
+// The two rows (rg, rg + 4) of one pipeline stage for one consumer warp, 4 columns per
+// lane.  MASK handles the diagonal (l1 == l2), columns >= N and rows past the segment;
+// stages without any of these take the unmasked instantiation.  SR: stochastic rounding.
+template <typename TS, int NP, bool MASK, bool SR>
+__device__ __forceinline__ void pair_stage_rows(const TS *tcur, const TS *tprv, const float *rec, int rg, int cofs,
+                                                long long r, long long r1, long long col0, long long N, long long ld,
+                                                const float (&ccol)[4], const float (&xi)[4][NP], float (&acc)[4][NP],
+                                                float (&csum)[4], float beta, float invL, uint32_t rseed, float scl,
+                                                float iscl, TS *__restrict__ nxt, bool vec_ok, float &rs0, float &rs1)
 {
     using St = Store<TS>;
-    const uint32_t h2 = (h ^ (h >> 15)) * 0x2C1B3C6Du;
-    const uint32_t rnd[4] = {h & 0xFFFFu, h >> 16, h2 & 0xFFFFu, h2 >> 16};
-    float rs = 0.0f;
+    using Vec = typename St::Vec;
+    constexpr int REC = RecLayout<NP>::REC;
+    float rsv[2];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float th2 = fmaf(beta, tc[j] - tp[j], tc[j]);     // theta^(2) = theta^(1) + beta (theta^(1) - prev)
-        float g = yr + ccol[j];                                 // (C eta)_p = y_l1 - y_l2 + xi_l2.x_l2 - xi_l2.x_l1
+    for (int i = 0; i < 2; ++i) {
+        const int rl = rg + i * kWR;
+        const long long rr = r + rl;
+        const bool valid = !MASK || rr < r1;
+        float rv[REC];
 #pragma unroll
-        for (int k = 0; k < NP; ++k) g = fmaf(-xi[j][k], xr[k], g);
-        float sv = St::round(th2, g, invL, sr, rnd[j], scl);    // Pi_{theta >= 0}(theta^(2) - g / L)
-        if (MASK) {
-            if (col0 + j >= N || col0 + j == row) sv = 0.0f;
+        for (int q = 0; q < REC; q += 4) {
+            const float4 t4 = *reinterpret_cast<const float4 *>(rec + rl * REC + q);
+            rv[q] = t4.x; rv[q + 1] = t4.y; rv[q + 2] = t4.z; rv[q + 3] = t4.w;
         }
-        outv[j] = sv;
-        const float vv = St::decoded(sv, iscl);
-        rs += vv;                                               // row sum      (A_1^T, + part)
-        csum[j] += vv;                                          // column sum   (A_1^T, - part)
+        float tc[4], tp[4], outv[4];
+        St::unpack(*reinterpret_cast<const Vec *>(tcur + rl * kW + cofs), tc, iscl);
+        St::unpack(*reinterpret_cast<const Vec *>(tprv + rl * kW + cofs), tp, iscl);
+        uint32_t h = 0, h2 = 0;
+        if (SR) {
+            h = hash3((uint32_t)rr, (uint32_t)(col0 >> 2), rseed);
+            h2 = (h ^ (h >> 15)) * 0x2C1B3C6Du;
+        }
+        const uint32_t rnd[4] = {h & 0xFFFFu, h >> 16, h2 & 0xFFFFu, h2 >> 16};
+        float rs = 0.0f;
 #pragma unroll
-        for (int k = 0; k < NP; ++k) acc[j][k] = fmaf(vv, xr[k], acc[j][k]);   // theta^T X (A_2^T)
+        for (int j = 0; j < 4; ++j) {
+            const float th2 = fmaf(beta, tc[j] - tp[j], tc[j]);  // theta^(2) = theta^(1) + beta (theta^(1) - prev)
+            // (C eta)_p = y_l1 - y_l2 + xi_l2.x_l2 - xi_l2.x_l1, summed in two chains
+            float g0 = rv[0] + ccol[j], g1 = 0.0f;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                if (k & 1) g1 = fmaf(-xi[j][k], rv[1 + k], g1);
+                else g0 = fmaf(-xi[j][k], rv[1 + k], g0);
+            }
+            float sv = St::template round<SR>(th2, g0 + g1, invL, rnd[j], scl);   // Pi_{>=0}(theta^(2) - g/L)
+            if (MASK) {
+                if (!valid || col0 + j >= N || col0 + j == rr) sv = 0.0f;
+            }
+            outv[j] = sv;
+            const float vv = St::decoded(sv, iscl);
+            rs += vv;                                                // row sum    (A_1^T, + part)
+            csum[j] += vv;                                           // column sum (A_1^T, - part)
+#pragma unroll
+            for (int k = 0; k < NP; ++k) acc[j][k] = fmaf(vv, rv[1 + k], acc[j][k]);   // theta^T X (A_2^T)
+        }
+        if (vec_ok && valid) *reinterpret_cast<Vec *>(nxt + rr * ld + col0) = St::pack(outv);
+        rsv[i] = rs;
     }
-    return rs;
+    rs0 = rsv[0];
+    rs1 = rsv[1];
+}
+
+// Row sums of a batch of up to 4 stages (8 rows per warp) reduced across the warp with a
+// transposing butterfly: 9 shuffles leave the full sum of batch entry
+// e = 4*bit4 + 2*bit3 + bit2 (of the lane id) in every lane.  Entry e is row
+// r_last - kRS*(3 - e/2) + rg + kWR*(e & 1); only the nb most recent stages are written.
+__device__ __forceinline__ void flush_row_sums(float (&v)[8], int nb, long long r_last, int rg, long long r1,
+                                               float *rp, int lane)
+{
+    const unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool hi = lane & 16;
+        const float send = hi ? v[i] : v[i + 4], keep = hi ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(full, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool hi = lane & 8;
+        const float send = hi ? v[i] : v[i + 2], keep = hi ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(full, send, 8);
+    }
+    {
+        const bool hi = lane & 4;
+        const float send = hi ? v[0] : v[1], keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(full, send, 4);
+    }
+    v[0] += __shfl_xor_sync(full, v[0], 2);
+    v[0] += __shfl_xor_sync(full, v[0], 1);
+    if ((lane & 3) == 0) {
+        const int e = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        const int sp = e >> 1;
+        const long long row = r_last - (long long)kRS * (3 - sp) + rg + kWR * (e & 1);
+        if (sp >= 4 - nb && row < r1) rp[row] = v[0];
+    }
+}
+
+// Producer cursor: walks the CTA's stages (kRS rows of one stripe) in consumption order.
+struct StageCursor {
+    long long u, uend, s, r0, r1, r;
+    __device__ __forceinline__ void begin(long long u0, long long ue, long long N)
+    {
+        u = u0;
+        uend = ue;
+        r = -1;
+        next_segment(N);
+    }
+    __device__ __forceinline__ void next_segment(long long N)
+    {
+        if (u >= uend) return;
+        s = u / N;
+        r0 = u - s * N;
+        r1 = min(N, r0 + (uend - u));
+        r = r0;
+    }
+    __device__ __forceinline__ void advance(long long N)
+    {
+        r += kRS;
+        if (r >= r1) {
+            u += r1 - r0;
+            next_segment(N);
+        }
+    }
+};
+
+// Issue stage number k (global count) into its ring slot: wait until the slot's previous
+// occupant (stage k - S) was released by all 8 warps, then two tiled TMA loads and one
+// bulk copy complete on the slot's "full" barrier.
+template <typename TS, int NP>
+__device__ __forceinline__ bool produce_stage(const Params &P, unsigned char *stage0, uint64_t *full, uint64_t *empty,
+                                              unsigned long long k, const StageCursor &cur, int c, int p)
+{
+    using L = PairSmem<TS, NP>;
+    constexpr int S = L::kStages;
+    const int slot = (int)(k % S);
+    const unsigned long long round = k / S;
+    if (round > 0 && !mbar_wait(P, &empty[slot], (uint32_t)((round - 1) & 1))) return false;
+    const int nrows = (int)min((long long)kRS, cur.r1 - cur.r);
+    unsigned char *st = stage0 + slot * L::stage_bytes;
+    mbar_arrive_expect_tx(&full[slot], (uint32_t)(2 * L::tile_bytes + (size_t)nrows * L::REC * 4));
+    tma_load_2d(st, &P.tmap[c], (int)(cur.s * kW), (int)cur.r, &full[slot]);
+    tma_load_2d(st + L::tile_bytes, &P.tmap[p], (int)(cur.s * kW), (int)cur.r, &full[slot]);
+    bulk_load(st + 2 * L::tile_bytes, P.rowrec + cur.r * L::REC, (uint32_t)(nrows * L::REC * 4), &full[slot]);
+    return true;
 }
 
 template <typename TS, int NP>
@@ -506,9 +624,7 @@ __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, 
                            unsigned long long &kstage)
 {
     using St = Store<TS>;
-    using Vec = typename St::Vec;
     using L = PairSmem<TS, NP>;
-    constexpr int REC = L::REC;
     constexpr int S = L::kStages;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int p = (int)(ell & 1), c = 1 - p;
@@ -525,128 +641,131 @@ __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, 
         nst += (unsigned long long)((r1 - r0 + kRS - 1) / kRS);
         u += r1 - r0;
     }
+    const unsigned long long kend = kstage + nst;
 
-    if (warp == kCons / 32) {
-        // ---------------- producer ----------------
-        if (lane == 0) {
-            fence_proxy_async();
-            unsigned long long k = kstage;
-            bool ok = true;
-            for (long long u = ubeg; u < uend && ok;) {
-                const long long s = u / N, r0 = u - s * N, r1 = min(N, r0 + (uend - u));
-                for (long long r = r0; r < r1; r += kRS, ++k) {
-                    const int slot = (int)(k % S);
-                    const unsigned long long round = k / S;
-                    if (round > 0 && !mbar_wait(P, &empty[slot], (uint32_t)((round - 1) & 1))) {
-                        ok = false;
-                        break;
-                    }
-                    const int nrows = (int)min((long long)kRS, r1 - r);
-                    unsigned char *st = stage0 + slot * L::stage_bytes;
-                    mbar_arrive_expect_tx(&full[slot], (uint32_t)(2 * L::tile_bytes + (size_t)nrows * REC * 4));
-                    tma_load_2d(st, &P.tmap[c], (int)(s * kW), (int)r, &full[slot]);
-                    tma_load_2d(st + L::tile_bytes, &P.tmap[p], (int)(s * kW), (int)r, &full[slot]);
-                    bulk_load(st + 2 * L::tile_bytes, P.rowrec + r * REC, (uint32_t)(nrows * REC * 4), &full[slot]);
+    // producer (lane 0 of warp 0): prefill the ring
+    const bool producer = (tid == 0);
+    StageCursor pc;
+    unsigned long long kprod = kstage;
+    bool pok = true;
+    if (producer) {
+        fence_proxy_async();
+        pc.begin(ubeg, uend, N);
+        for (; kprod < kend && kprod < kstage + S && pok; ++kprod) {
+            pok = produce_stage<TS, NP>(P, stage0, full, empty, kprod, pc, c, p);
+            pc.advance(N);
+        }
+    }
+    __syncwarp();
+
+    const int wc = warp & 1, rg = warp >> 1;
+    const float beta = (float)__ldcg(&P.st->scal[p].beta);
+    const float invL = P.invL;
+    const float scl = P.st_scale, iscl = P.st_inv_scale;
+    const bool sr = P.sr != 0;
+    const uint32_t rseed = P.seed ^ (uint32_t)ell * 0x632BE5ABu;
+    TS *__restrict__ nxt = (TS *)P.theta[p];   // theta^(1)_{l-2} on entry, theta^(1)_l on exit
+    const long long first_stripe = ubeg / N;
+    unsigned long long k = kstage;
+    bool ok = true;
+    for (long long u = ubeg; u < uend;) {
+        const long long s = u / N, r0 = u - s * N, r1 = min(N, r0 + (uend - u));
+        const long long colw = s * kW + wc * 128;       // first column of this warp
+        const long long col0 = colw + lane * 4;
+        const bool vec_ok = col0 < ld;
+        const bool ragged = (s * kW + kW) > N;
+        float ccol[4], xi[4][NP];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long long cj = col0 + j;
+            const bool v = cj < N;
+            ccol[j] = v ? __ldcg(P.ccol2 + cj) : 0.0f;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) xi[j][q] = v ? __ldcg(P.xi2 + cj * NP + q) : 0.0f;
+        }
+        float acc[4][NP], csum[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            csum[j] = 0.0f;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) acc[j][q] = 0.0f;
+        }
+        float *rp = P.rowpart + (s * 2 + wc) * N;
+        const int cofs = wc * 128 + lane * 4;
+        float rsb[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) rsb[q] = 0.0f;
+        int nb = 0;
+        for (long long r = r0; r < r1; r += kRS, ++k) {
+            const int slot = (int)(k % S);
+            if (ok && !mbar_wait(P, &full[slot], (uint32_t)((k / S) & 1))) ok = false;
+            float ra = 0.0f, rb = 0.0f;
+            if (ok) {
+                const unsigned char *st = stage0 + slot * L::stage_bytes;
+                const TS *tcur = reinterpret_cast<const TS *>(st);
+                const TS *tprv = reinterpret_cast<const TS *>(st + L::tile_bytes);
+                const float *rec = reinterpret_cast<const float *>(st + 2 * L::tile_bytes);
+                const bool fast = !ragged && (r + kRS <= r1) && !(r < colw + 128 && colw < r + kRS);
+                if (sr) {
+                    if (fast)
+                        pair_stage_rows<TS, NP, false, true>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, xi,
+                                                             acc, csum, beta, invL, rseed, scl, iscl, nxt, vec_ok,
+                                                             ra, rb);
+                    else
+                        pair_stage_rows<TS, NP, true, true>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, xi,
+                                                            acc, csum, beta, invL, rseed, scl, iscl, nxt, vec_ok,
+                                                            ra, rb);
+                } else {
+                    if (fast)
+                        pair_stage_rows<TS, NP, false, false>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol,
+                                                              xi, acc, csum, beta, invL, rseed, scl, iscl, nxt,
+                                                              vec_ok, ra, rb);
+                    else
+                        pair_stage_rows<TS, NP, true, false>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol,
+                                                             xi, acc, csum, beta, invL, rseed, scl, iscl, nxt,
+                                                             vec_ok, ra, rb);
                 }
-                u += r1 - r0;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+            if (producer && pok && kprod < kend) {   // refill this slot with stage k + S
+                pok = produce_stage<TS, NP>(P, stage0, full, empty, kprod, pc, c, p);
+                pc.advance(N);
+                ++kprod;
+            }
+            __syncwarp();   // reconverge warp 0 after the producer lane
+            // shift the row-sum batch (most recent stage in entries 6, 7)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) rsb[q] = rsb[q + 2];
+            rsb[6] = ra;
+            rsb[7] = rb;
+            ++nb;
+            if (nb == 4 || r + kRS >= r1) {
+                flush_row_sums(rsb, nb, r, rg, r1, rp, lane);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) rsb[q] = 0.0f;
+                nb = 0;
             }
         }
-    } else {
-        // ---------------- consumers ----------------
-        const int wc = warp & 1, rg = warp >> 1;
-        const float beta = (float)__ldcg(&P.st->scal[p].beta);
-        const float invL = P.invL;
-        const float scl = P.st_scale, iscl = P.st_inv_scale;
-        const bool sr = P.sr != 0;
-        const uint32_t rseed = P.seed ^ (uint32_t)ell * 0x632BE5ABu;
-        TS *__restrict__ nxt = (TS *)P.theta[p];   // theta^(1)_{l-2} on entry, theta^(1)_l on exit
-        const long long first_stripe = ubeg / N;
-        unsigned long long k = kstage;
-        bool ok = true;
-        for (long long u = ubeg; u < uend;) {
-            const long long s = u / N, r0 = u - s * N, r1 = min(N, r0 + (uend - u));
-            const long long colw = s * kW + wc * 128;       // first column of this warp
-            const long long col0 = colw + lane * 4;
-            const bool vec_ok = col0 < ld;
-            const bool ragged = (s * kW + kW) > N;
-            float ccol[4], xi[4][NP];
+        // column partials of this segment: reduce the 4 row groups in shared memory
+        const int slotc = (int)(s - first_stripe);
+        float *cp = P.colpart + ((long long)blockIdx.x * P.slots + slotc) * (NP + 1) * kW;
+        const int cl = wc * 128 + lane * 4;
+        named_barrier_sync(1, kCons);
+        *reinterpret_cast<float4 *>(flush + (rg * (NP + 1)) * kW + cl) = make_float4(csum[0], csum[1], csum[2], csum[3]);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const long long cj = col0 + j;
-                const bool v = cj < N;
-                ccol[j] = v ? __ldcg(P.ccol2 + cj) : 0.0f;
+        for (int q = 0; q < NP; ++q)
+            *reinterpret_cast<float4 *>(flush + (rg * (NP + 1) + 1 + q) * kW + cl) =
+                make_float4(acc[0][q], acc[1][q], acc[2][q], acc[3][q]);
+        named_barrier_sync(1, kCons);
+        for (int e = tid; e < (NP + 1) * kW; e += kCons) {
+            float a = flush[e];
 #pragma unroll
-                for (int q = 0; q < NP; ++q) xi[j][q] = v ? __ldcg(P.xi2 + cj * NP + q) : 0.0f;
-            }
-            float acc[4][NP], csum[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                csum[j] = 0.0f;
-#pragma unroll
-                for (int q = 0; q < NP; ++q) acc[j][q] = 0.0f;
-            }
-            float *rp = P.rowpart + (s * 2 + wc) * N;
-            for (long long r = r0; r < r1; r += kRS, ++k) {
-                const int slot = (int)(k % S);
-                if (ok && !mbar_wait(P, &full[slot], (uint32_t)((k / S) & 1))) ok = false;
-                if (ok) {
-                    const unsigned char *st = stage0 + slot * L::stage_bytes;
-                    const TS *tcur = reinterpret_cast<const TS *>(st);
-                    const TS *tprv = reinterpret_cast<const TS *>(st + L::tile_bytes);
-                    const float *rec = reinterpret_cast<const float *>(st + 2 * L::tile_bytes);
-#pragma unroll
-                    for (int i = 0; i < kRS / kWR; ++i) {
-                        const int rl = rg + i * kWR;
-                        const long long rr = r + rl;
-                        if (rr >= r1) break;   // warp-uniform
-                        float rv[REC];
-#pragma unroll
-                        for (int q = 0; q < REC; q += 4) {
-                            const float4 t4 = *reinterpret_cast<const float4 *>(rec + rl * REC + q);
-                            rv[q] = t4.x; rv[q + 1] = t4.y; rv[q + 2] = t4.z; rv[q + 3] = t4.w;
-                        }
-                        float xr[NP];
-#pragma unroll
-                        for (int q = 0; q < NP; ++q) xr[q] = rv[1 + q];
-                        float tc[4], tp[4], outv[4];
-                        St::unpack(*reinterpret_cast<const Vec *>(tcur + rl * kW + wc * 128 + lane * 4), tc, iscl);
-                        St::unpack(*reinterpret_cast<const Vec *>(tprv + rl * kW + wc * 128 + lane * 4), tp, iscl);
-                        const uint32_t h = sr ? hash3((uint32_t)rr, (uint32_t)(col0 >> 2), rseed) : 0u;
-                        float rs;
-                        if (ragged || (rr >= colw && rr < colw + 128))
-                            rs = pair_row<TS, NP, true>(tc, tp, xr, rv[0], ccol, xi, acc, csum, beta, invL, sr, h, scl,
-                                                        iscl, col0, rr, N, outv);
-                        else
-                            rs = pair_row<TS, NP, false>(tc, tp, xr, rv[0], ccol, xi, acc, csum, beta, invL, sr, h,
-                                                         scl, iscl, col0, rr, N, outv);
-                        if (vec_ok) *reinterpret_cast<Vec *>(nxt + rr * ld + col0) = St::pack(outv);
-                        rs = warp_sum(rs);
-                        if (lane == 0) rp[rr] = rs;
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[slot]);
-            }
-            // column partials of this segment: reduce the 4 row groups in shared memory
-            const int slotc = (int)(s - first_stripe);
-            float *cp = P.colpart + ((long long)blockIdx.x * P.slots + slotc) * (NP + 1) * kW;
-            const int cl = wc * 128 + lane * 4;
-            named_barrier_sync(1, kCons);
-            *reinterpret_cast<float4 *>(flush + (rg * (NP + 1)) * kW + cl) = make_float4(csum[0], csum[1], csum[2], csum[3]);
-#pragma unroll
-            for (int q = 0; q < NP; ++q)
-                *reinterpret_cast<float4 *>(flush + (rg * (NP + 1) + 1 + q) * kW + cl) =
-                    make_float4(acc[0][q], acc[1][q], acc[2][q], acc[3][q]);
-            named_barrier_sync(1, kCons);
-            for (int e = tid; e < (NP + 1) * kW; e += kCons) {
-                float a = flush[e];
-#pragma unroll
-                for (int q = 1; q < kWR; ++q) a += flush[q * (NP + 1) * kW + e];
-                cp[e] = a;
-            }
-            named_barrier_sync(1, kCons);
-            u += r1 - r0;
+            for (int q = 1; q < kWR; ++q) a += flush[q * (NP + 1) * kW + e];
+            cp[e] = a;
         }
+        named_barrier_sync(1, kCons);
+        u += r1 - r0;
     }
     kstage += nst;
     __syncthreads();
