@@ -146,6 +146,40 @@ cr_status cr_get_info(cr_handle h, int64_t *iters, int64_t *restarts, double *L,
  * Blocks; resets the counters. */
 cr_status cr_profile(cr_handle h, int32_t kind, double *ms, int64_t *launches);
 
+/* Device addresses of the handle's current iterate, without copying: theta^(1)_l (N rows of
+ * ld elements, row-major, in the handle's theta_dtype), X (N x n FP64), y (N FP64, the fitted
+ * values plus the shift s), xi (N x n FP64), mu (N FP64, multipliers of the y >= 0 rows) and
+ * the data scale sigma used by the KKT residual.  The buffers stay owned by the handle; the
+ * addresses are valid until the next call that iterates, resets or destroys it.  Any output
+ * pointer may be NULL. */
+cr_status cr_get_device_state(cr_handle h, const void **dtheta, int64_t *ld, const double **dX, const double **dy,
+                              const double **dxi, const double **dmu, double *sigma);
+
+/* KKT residual without any allocation, for callers that cannot allocate device memory when
+ * they check convergence: processes that reserve their whole device-memory budget up front
+ * and forbid later allocation, and loops that must avoid cudaMalloc/cudaFree because those
+ * calls can synchronize the device.  The paper has no counterpart; this is a service of this
+ * library.
+ *
+ * Computes the same five FP64 values as cr_kkt_residual (kkt, pri, comp, infeas_norm,
+ * gap_norm, in that order) for a caller-described dual point: theta (device, FP32, N rows of
+ * ld >= N elements, row-major; the diagonal is ignored), X (device, N x n FP64), y (device, N
+ * FP64, the minimizer's y including the shift), xi (device, N x n FP64), mu (device, N FP64,
+ * or NULL for zero) and sigma > 0; the five results are written to dout (device, 5 doubles).
+ * Work is enqueued on `stream` (cudaStream_t, NULL = legacy default stream) and the call
+ * returns without waiting.
+ *
+ * Scratch: a fixed array of 65,536 x 4 doubles (2 MiB) inside the library, held by every
+ * device that loads the library until the process exits.  N > 65,536 is rejected with
+ * CR_EINVAL (message in cr_last_error(NULL)).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the array, so calls that overlap on the
+ * GPU (for example on two streams at once) race and must be ordered by the caller.  The
+ * call allocates nothing: no cudaMalloc, cudaFree or allocating library routine. */
+cr_status cr_kkt_residual_noalloc(int64_t N, int32_t n, const float *dtheta, int64_t ld, const double *dX,
+                                  const double *dy, const double *dxi, const double *dmu, double sigma, void *stream,
+                                  double *dout);
+
 /* Releases every resource of the handle (NULL is a no-op). */
 void cr_destroy(cr_handle h);
 

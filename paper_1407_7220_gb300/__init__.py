@@ -38,7 +38,7 @@ _DTYPES = {"f32": THETA_F32, "fp32": THETA_F32, "float32": THETA_F32, "bf16": TH
 exported_symbols = (
     "cr_options_default", "cr_create", "cr_create_device", "cr_reset", "cr_iterate", "cr_solve",
     "cr_objective", "cr_kkt_residual", "cr_get_solution", "cr_get_info", "cr_destroy",
-    "cr_status_str", "cr_last_error", "cr_profile",
+    "cr_status_str", "cr_last_error", "cr_profile", "cr_get_device_state", "cr_kkt_residual_noalloc",
 )
 PROFILE_PAIR, PROFILE_FOLD, PROFILE_KKT, PROFILE_PERSISTENT = 0, 1, 2, 3
 
@@ -91,6 +91,12 @@ def lib():
             L.cr_kkt_residual.argtypes = [H, dp, dp, dp]
             L.cr_get_solution.argtypes = [H, dp, dp]
             L.cr_get_info.argtypes = [H, i64p, i64p, dp, dp]
+            vpp = ctypes.POINTER(ctypes.c_void_p)
+            L.cr_get_device_state.argtypes = [H, vpp, i64p, vpp, vpp, vpp, vpp, dp]
+            L.cr_get_device_state.restype = ctypes.c_int
+            L.cr_kkt_residual_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int32, fp, ctypes.c_int64, fp, fp, fp, fp,
+                                                  ctypes.c_double, fp, fp]
+            L.cr_kkt_residual_noalloc.restype = ctypes.c_int
             L.cr_profile.argtypes = [H, ctypes.c_int32, dp, i64p]
             L.cr_profile.restype = ctypes.c_int
             L.cr_destroy.argtypes = [H]
@@ -221,3 +227,12 @@ class Solver:
         ms, n = ctypes.c_double(), ctypes.c_int64()
         self._check(lib().cr_profile(self._h, int(kind), ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+    def device_state(self) -> dict:
+        """Device addresses of the current iterate (see cr_get_device_state); no copy."""
+        th, X, y, xi, mu = (ctypes.c_void_p() for _ in range(5))
+        ld, sg = ctypes.c_int64(), ctypes.c_double()
+        self._check(lib().cr_get_device_state(self._h, ctypes.byref(th), ctypes.byref(ld), ctypes.byref(X),
+                                              ctypes.byref(y), ctypes.byref(xi), ctypes.byref(mu), ctypes.byref(sg)))
+        return {"theta": th.value, "ld": ld.value, "X": X.value, "y": y.value, "xi": xi.value, "mu": mu.value,
+                "sigma": sg.value}

@@ -572,6 +572,10 @@ cr_status usable(cr_ctx *h)
 
 }  // namespace
 
+namespace crk {
+void set_thread_error(const std::string &m) { g_create_err = m; }
+}  // namespace crk
+
 extern "C" {
 
 void cr_options_default(cr_options *o)
@@ -756,6 +760,21 @@ cr_status cr_profile(cr_handle h, int32_t kind, double *ms, int64_t *launches)
     if (launches) *launches = h->prof_n[kind];
     h->prof_ms[kind] = 0.0;
     h->prof_n[kind] = 0;
+    return CR_OK;
+}
+
+cr_status cr_get_device_state(cr_handle h, const void **dtheta, int64_t *ld, const double **dX, const double **dy,
+                              const double **dxi, const double **dmu, double *sigma)
+{
+    if (!h) return CR_EINVAL;
+    const int b = (int)(h->iters & 1);   // theta^(1)_l lives in buffer l & 1
+    if (dtheta) *dtheta = h->P.theta[b];
+    if (ld) *ld = h->ld;
+    if (dX) *dX = h->P.X64;
+    if (dy) *dy = h->P.y1;
+    if (dxi) *dxi = h->P.xi1_64;
+    if (dmu) *dmu = h->P.mu[b];
+    if (sigma) *sigma = h->sigma;
     return CR_OK;
 }
 
