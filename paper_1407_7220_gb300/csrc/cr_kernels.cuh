@@ -35,7 +35,8 @@ constexpr int kCons = kThreads; // every warp consumes pair-pass stages; lane 0 
 constexpr int kW = 256;         // stripe width (columns)
 constexpr int kWR = 4;          // row groups of consumer warps (2 warps per row)
 constexpr int kRS = 8;          // rows per pipeline stage
-constexpr int kMaxStages = 8;
+constexpr int kMaxStages = 16;
+constexpr size_t kSmemBudget = 227 * 1024 - 2048;   // dynamic shared memory per CTA (static arrays excluded)
 
 template <int NP> struct RecLayout {
     static constexpr int REC = ((NP + 1 + 3) / 4) * 4;   // floats per row record (16-byte multiple)
@@ -96,7 +97,8 @@ struct Params {
     double *v[2];           // A_1^T theta^(1) of the two latest iterates (N)
     double *w[2];           // A_2^T theta^(1) (N x n)
     double *mu[2];          // multipliers of the y >= 0 rows (N)
-    float *rowpart;         // [2S][N]
+    float *rowpart;         // [N][Q]: row sums per (stripe, column half), Q = ceil4(2S), padding 0
+    int Q;
     float *colpart;         // [G][slots][NP+1][kW]
     double *foldpart;       // [G][8]
     double *kktpart;        // [G][8]
@@ -463,11 +465,14 @@ __device__ void phase_foldB(const Params &P, long long ell, double *red)
 
 template <typename TS, int NP> struct PairSmem {
     static constexpr int REC = RecLayout<NP>::REC;
-    static constexpr int kStages = sizeof(TS) == 4 ? 5 : 8;
     static constexpr size_t tile_bytes = (size_t)kRS * kW * sizeof(TS);
     static constexpr size_t rec_bytes = (size_t)kRS * REC * sizeof(float);
     static constexpr size_t stage_bytes = 2 * tile_bytes + rec_bytes;
     static constexpr size_t flush_bytes = (size_t)kWR * (NP + 1) * kW * sizeof(float);
+    // as many stages as fit next to the column-partial buffer (more bytes in flight per SM)
+    static constexpr int kFit = (int)((kSmemBudget - flush_bytes - 128) / stage_bytes);
+    static constexpr int kStages = kFit < kMaxStages ? kFit : kMaxStages;
+    static_assert(kStages >= 2, "pipeline needs at least two stages");
     static constexpr size_t bytes = kStages * stage_bytes + flush_bytes + 128;   // + base alignment slack
     static_assert(tile_bytes % 128 == 0 && rec_bytes % 128 == 0, "stage buffers must stay 128-byte aligned");
 };
@@ -540,7 +545,7 @@ __device__ __forceinline__ void pair_stage_rows(const TS *tcur, const TS *tprv, 
 // e = 4*bit4 + 2*bit3 + bit2 (of the lane id) in every lane.  Entry e is row
 // r_last - kRS*(3 - e/2) + rg + kWR*(e & 1); only the nb most recent stages are written.
 __device__ __forceinline__ void flush_row_sums(float (&v)[8], int nb, long long r_last, int rg, long long r1,
-                                               float *rp, int lane)
+                                               float *rp, int Q, int lane)
 {
     const unsigned full = 0xffffffffu;
 #pragma unroll
@@ -566,7 +571,7 @@ __device__ __forceinline__ void flush_row_sums(float (&v)[8], int nb, long long 
         const int e = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
         const int sp = e >> 1;
         const long long row = r_last - (long long)kRS * (3 - sp) + rg + kWR * (e & 1);
-        if (sp >= 4 - nb && row < r1) rp[row] = v[0];
+        if (sp >= 4 - nb && row < r1) rp[row * Q] = v[0];
     }
 }
 
@@ -690,7 +695,7 @@ __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, 
 #pragma unroll
             for (int q = 0; q < NP; ++q) acc[j][q] = 0.0f;
         }
-        float *rp = P.rowpart + (s * 2 + wc) * N;
+        float *rp = P.rowpart + (s * 2 + wc);   // row r's partial at rp[r * Q]
         const int cofs = wc * 128 + lane * 4;
         float rsb[8];
 #pragma unroll
@@ -741,7 +746,7 @@ __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, 
             rsb[7] = rb;
             ++nb;
             if (nb == 4 || r + kRS >= r1) {
-                flush_row_sums(rsb, nb, r, rg, r1, rp, lane);
+                flush_row_sums(rsb, nb, r, rg, r1, rp, P.Q, lane);
 #pragma unroll
                 for (int q = 0; q < 8; ++q) rsb[q] = 0.0f;
                 nb = 0;
@@ -780,30 +785,42 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red)
     const int p = (int)(ell & 1);
     const long long N = P.N;
     const int n = P.n;
+    const int Q4 = P.Q >> 2;   // row partials per row, in float4 units
     double a = 0.0, b = 0.0, cc = 0.0, mviol = 0.0, mcomp = 0.0, sviol = 0.0, smuy = 0.0;
     for (long long l = (long long)blockIdx.x * kThreads + threadIdx.x; l < N; l += (long long)P.G * kThreads) {
+        // row sum: the Q (>= 2S, zero padded) contiguous partials of row l, independent 16-byte loads
+        const float4 *rp4 = reinterpret_cast<const float4 *>(P.rowpart + l * P.Q);
         double R = 0.0;
-        for (int q = 0; q < 2 * P.S; ++q) R += (double)__ldcg(P.rowpart + (long long)q * N + l);
+#pragma unroll 8
+        for (int q = 0; q < Q4; ++q) {
+            const float4 t = __ldcg(rp4 + q);
+            R += ((double)t.x + (double)t.y) + ((double)t.z + (double)t.w);
+        }
         const long long s = l / kW, cl = l - s * kW;
         // CTAs whose unit range intersects stripe s, ascending
-        long long ua = s * N, ub = s * N + N - 1;
+        const long long ua = s * N, ub = s * N + N - 1;
         long long c0 = (long long)(((unsigned long long)ua * (unsigned long long)P.G) / (unsigned long long)P.total);
         while (c0 > 0 && unit_begin(P, c0) > ua) --c0;
         while (c0 + 1 < P.G && unit_begin(P, c0 + 1) <= ua) ++c0;
         double Cc = 0.0, TX[NP];
 #pragma unroll
         for (int k = 0; k < NP; ++k) TX[k] = 0.0;
-        for (long long cta = c0; cta < P.G && unit_begin(P, cta) <= ub; ++cta) {
-            if (unit_begin(P, cta + 1) <= unit_begin(P, cta)) continue;  // empty range
-            const long long fs = unit_begin(P, cta) / N;
-            const float *cp = P.colpart + ((cta * P.slots + (s - fs)) * (NP + 1)) * kW;
-            Cc += (double)__ldcg(cp + cl);
+        long long ubg = unit_begin(P, c0);
+        for (long long cta = c0; cta < P.G && ubg <= ub; ++cta) {
+            const long long unx = unit_begin(P, cta + 1);
+            if (unx > ubg) {
+                const long long fs = ubg / N;
+                const float *cp = P.colpart + ((cta * P.slots + (s - fs)) * (NP + 1)) * kW + cl;
+                Cc += (double)__ldcg(cp);
 #pragma unroll
-            for (int k = 0; k < NP; ++k) TX[k] += (double)__ldcg(cp + (1 + k) * kW + cl);
+                for (int k = 0; k < NP; ++k) TX[k] += (double)__ldcg(cp + (1 + k) * kW);
+            }
+            ubg = unx;
         }
         const double v = R - Cc;               // (A_1^T theta)_l = row sum - column sum
         P.v[p][l] = v;
-        const double y = __ldg(P.h + l) + v + __ldcg(P.mu[p] + l);   // Step 1 closed form
+        const double hl = __ldg(P.h + l), mu = __ldcg(P.mu[p] + l);
+        const double y = hl + v + mu;          // Step 1 closed form
         const double ys = y - P.shift;
         double d = 0.0, xin = 0.0;
 #pragma unroll
@@ -824,11 +841,10 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red)
         P.y1[l] = y;
         P.yrow1[l] = (float)ys;
         P.ccol1[l] = (float)(d - ys);
-        const double uu = y - __ldg(P.h + l);
+        const double uu = y - hl;
         a += uu * uu;
         b += xin;
         cc += uu * y;
-        const double mu = __ldcg(P.mu[p] + l);
         mviol = fmax(mviol, -y);
         mcomp = fmax(mcomp, mu * fabs(y));
         if (y < 0.0) sviol += y * y;

@@ -368,7 +368,7 @@ cr_status init_state(cr_ctx *h)
         CR_CUDA(h, cudaMemsetAsync(P.w[b], 0, sizeof(double) * h->N * h->n, h->stream));
         CR_CUDA(h, cudaMemsetAsync(P.mu[b], 0, sizeof(double) * h->N, h->stream));
     }
-    CR_CUDA(h, cudaMemsetAsync(P.rowpart, 0, sizeof(float) * 2 * (size_t)P.S * h->N, h->stream));
+    CR_CUDA(h, cudaMemsetAsync(P.rowpart, 0, sizeof(float) * (size_t)P.Q * h->N, h->stream));
     CR_CUDA(h, cudaMemsetAsync(P.colpart, 0, sizeof(float) * (size_t)P.G * P.slots * (h->NP + 1) * crk::kW, h->stream));
     DevState st;
     std::memset(&st, 0, sizeof st);
@@ -451,6 +451,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     h->ld = ((N + 15) / 16) * 16;
     P.ld = h->ld;
     P.S = (int)S;
+    P.Q = (int)(((2 * S) + 3) / 4 * 4);
     P.G = G;
     P.total = total;
     P.slots = max_slots(total, N, G);
@@ -515,7 +516,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
         CR_TRY(dev_alloc(h, &P.w[b], (size_t)N * n));
         CR_TRY(dev_alloc(h, &P.mu[b], N));
     }
-    CR_TRY(dev_alloc(h, &P.rowpart, 2 * (size_t)S * N));
+    CR_TRY(dev_alloc(h, &P.rowpart, (size_t)P.Q * N));
     CR_TRY(dev_alloc(h, &P.colpart, (size_t)G * P.slots * (h->NP + 1) * crk::kW));
     CR_TRY(dev_alloc(h, &P.foldpart, (size_t)G * 8));
     CR_TRY(dev_alloc(h, &P.kktpart, (size_t)G * 8));
