@@ -70,7 +70,8 @@ typedef struct {
     int32_t stochastic_round; /* 1: unbiased stochastic rounding of every theta store (counter-based hash) */
     int32_t kkt_every;        /* cr_solve evaluates the KKT residual every this many iterations (>= 1) */
     int32_t momentum;         /* 1: P-APG (Fig. 2); 0: dual gradient ascent (the paper's comparator, Sec. III) */
-    int32_t restart;          /* NOT IN THE PAPER. 1: reset the momentum (t <- 1) when the dual value decreases */
+    int32_t restart;          /* NOT IN THE PAPER. 1: reset the momentum (t <- 1) when the dual value decreases;
+                                 default 0 (plain P-APG, which converged faster in our measurements) */
     int32_t driver;           /* CR_DRIVER_* */
     int32_t grid;             /* CTAs used by the pair pass; 0 = tuned per device and size */
     int32_t fp16_exponent;    /* CR_THETA_F16 only: theta is stored as theta * 2^fp16_exponent */
@@ -83,6 +84,8 @@ typedef struct {
                                    that never come, so the bounded wait runs out on purpose */
     int32_t profile;          /* 1: record CUDA events around every kernel launch (see cr_profile) */
     int32_t reserved[5];
+    double restart_tol;       /* restart only when the dual value fell by more than restart_tol * |previous|
+                                 (guards the test against rounding noise); default 1e-7 */
 } cr_options;
 
 /* Fills *opt with the defaults documented above. */
@@ -182,6 +185,35 @@ cr_status cr_kkt_residual_noalloc(int64_t N, int32_t n, const float *dtheta, int
 
 /* Releases every resource of the handle (NULL is a no-op). */
 void cr_destroy(cr_handle h);
+
+/* ---- batched solves: many independent fits in one persistent launch ---------------------
+ * B independent instances (sizes N[i] x n[i], host FP64 arrays X[i], ybar[i]) advance together:
+ * one cooperative launch runs every phase of every instance, separated by bounded grid
+ * barriers.  Work items (a slice of an instance's stripes and rows) are spread over the
+ * physical CTAs by pair count; the item size is chosen at creation by an autotuner that
+ * times a few iterations per candidate (cr_options.grid > 0 fixes the granularity factor
+ * instead).  The launch is captured once in a CUDA graph and replayed chunk after chunk.
+ * Each instance keeps its own L, shift, momentum scalars and KKT test; an instance whose
+ * KKT residual reaches tol leaves the work, and its state stays at that iterate.  All
+ * instances share the options (gamma, theta_dtype ...), padded to the largest n. */
+typedef struct cr_batch_ctx *cr_batch_handle;
+
+cr_status cr_batch_create(int32_t B, const int64_t *N, const int32_t *n, const double *const *X,
+                          const double *const *ybar, const cr_options *opt, cr_batch_handle *out);
+/* Iterates until every instance reached KKT <= tol (checked every kkt_every iterations) or
+ * max_iter iterations; *converged (nullable) = instances that converged.  Blocks. */
+cr_status cr_batch_solve(cr_batch_handle b, double tol, int64_t max_iter, int64_t *converged);
+/* k iterations of every instance still running (no convergence test).  Blocks. */
+cr_status cr_batch_iterate(cr_batch_handle b, int64_t k);
+/* Every instance back to Iteration 0 of Fig. 2. */
+cr_status cr_batch_reset(cr_batch_handle b);
+/* Handle of instance i (owned by the batch): use cr_get_solution, cr_get_info, cr_objective or
+ * cr_kkt_residual on it; do not iterate or destroy it directly. */
+cr_status cr_batch_instance(cr_batch_handle b, int32_t i, cr_handle *h);
+/* Granularity factor picked by the autotuner, physical CTAs, iterations run. */
+cr_status cr_batch_info(cr_batch_handle b, int32_t *factor, int32_t *grid, int64_t *iters);
+void cr_batch_destroy(cr_batch_handle b);
+const char *cr_batch_last_error(cr_batch_handle b);
 
 /* Static description of a status code. */
 const char *cr_status_str(cr_status s);

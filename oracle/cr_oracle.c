@@ -318,6 +318,7 @@ typedef struct {
     int32_t restart;  /* NOT IN THE PAPER: 1 = reset t to 1 whenever g_gamma(theta^(1)_l) < g_gamma(theta^(1)_{l-1}) */
     int32_t check_every; /* evaluate the KKT metric every this many iterations (0 = never) */
     int32_t pad;
+    double restart_tol;  /* restart only if the dual value fell by more than restart_tol * |previous| */
 } orc_opts;
 
 /* Runs up to max_iter iterations of P-APG from the given state.  After each
@@ -369,7 +370,7 @@ ORC_API int64_t orc_papg(const double *X, const double *h, int64_t N, int32_t n,
         double t = scal[0];
         if (o->restart) {
             double dv = dual_value(y, xi, h, N, n, gamma);
-            if (dv < scal[2]) {
+            if (dv < scal[2] - o->restart_tol * fabs(scal[2])) {
                 t = 1.0; /* restart: the weight below becomes 0 */
                 scal[3] += 1.0;
             }

@@ -13,6 +13,10 @@ import threading
 
 import numpy as np
 
+# OpenMP threads of the oracle sleep instead of spinning when idle, so that it
+# degrades gracefully when other processes share the cores (set before load).
+os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cr_oracle.c")
 _LIB = os.path.join(_HERE, "libcr_oracle.so")
@@ -40,7 +44,7 @@ def build_oracle(force: bool = False) -> str:
 class _Opts(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("L", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("tol", ctypes.c_double), ("momentum", ctypes.c_int32), ("restart", ctypes.c_int32),
-                ("check_every", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("check_every", ctypes.c_int32), ("pad", ctypes.c_int32), ("restart_tol", ctypes.c_double)]
 
 
 def _load():
@@ -140,7 +144,7 @@ class Solver:
 
     def __init__(self, X, ybar, gamma: float = 1e-1, L: float | None = None, s: float | None = None,
                  momentum: bool = True, restart: bool = False, check_every: int = 0,
-                 theta0=None, mu0=None):
+                 theta0=None, mu0=None, restart_tol: float = 0.0):
         self.X = _f64(X)
         self.ybar = _f64(ybar)
         self.N, self.n = self.X.shape
@@ -154,6 +158,7 @@ class Solver:
         self.momentum = bool(momentum)
         self.restart = bool(restart)
         self.check_every = int(check_every)
+        self.restart_tol = float(restart_tol)
         N = self.N
         self.P = np.zeros((N, N))
         self.T2 = np.zeros((N, N))
@@ -176,7 +181,7 @@ class Solver:
 
     def _opts(self, tol):
         return _Opts(self.gamma, self.L, self.sigma, float(tol), int(self.momentum), int(self.restart),
-                     int(self.check_every), 0)
+                     int(self.check_every), 0, self.restart_tol)
 
     def iterate(self, k: int, tol: float = -1.0) -> int:
         o = self._opts(tol)

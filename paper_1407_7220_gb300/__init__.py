@@ -39,6 +39,8 @@ exported_symbols = (
     "cr_options_default", "cr_create", "cr_create_device", "cr_reset", "cr_iterate", "cr_solve",
     "cr_objective", "cr_kkt_residual", "cr_get_solution", "cr_get_info", "cr_destroy",
     "cr_status_str", "cr_last_error", "cr_profile", "cr_get_device_state", "cr_kkt_residual_noalloc",
+    "cr_batch_create", "cr_batch_solve", "cr_batch_iterate", "cr_batch_reset", "cr_batch_instance",
+    "cr_batch_info", "cr_batch_destroy", "cr_batch_last_error",
 )
 PROFILE_PAIR, PROFILE_FOLD, PROFILE_KKT, PROFILE_PERSISTENT = 0, 1, 2, 3
 
@@ -52,6 +54,7 @@ class Options(ctypes.Structure):
         ("driver", ctypes.c_int32), ("grid", ctypes.c_int32), ("fp16_exponent", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("barrier_timeout_ms", ctypes.c_int32),
         ("test_barrier_extra", ctypes.c_int32), ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
+        ("restart_tol", ctypes.c_double),
     ]
 
 
@@ -97,6 +100,21 @@ def lib():
             L.cr_kkt_residual_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int32, fp, ctypes.c_int64, fp, fp, fp, fp,
                                                   ctypes.c_double, fp, fp]
             L.cr_kkt_residual_noalloc.restype = ctypes.c_int
+            L.cr_batch_create.argtypes = [ctypes.c_int32, i64p, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(Options),
+                                          ctypes.POINTER(H)]
+            L.cr_batch_solve.argtypes = [H, ctypes.c_double, ctypes.c_int64, i64p]
+            L.cr_batch_iterate.argtypes = [H, ctypes.c_int64]
+            L.cr_batch_reset.argtypes = [H]
+            L.cr_batch_instance.argtypes = [H, ctypes.c_int32, ctypes.POINTER(H)]
+            L.cr_batch_info.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), i64p]
+            L.cr_batch_destroy.argtypes = [H]
+            L.cr_batch_destroy.restype = None
+            L.cr_batch_last_error.argtypes = [H]
+            L.cr_batch_last_error.restype = ctypes.c_char_p
+            for name in ("cr_batch_create", "cr_batch_solve", "cr_batch_iterate", "cr_batch_reset",
+                         "cr_batch_instance", "cr_batch_info"):
+                getattr(L, name).restype = ctypes.c_int
             L.cr_profile.argtypes = [H, ctypes.c_int32, dp, i64p]
             L.cr_profile.restype = ctypes.c_int
             L.cr_destroy.argtypes = [H]
@@ -236,3 +254,86 @@ class Solver:
                                               ctypes.byref(y), ctypes.byref(xi), ctypes.byref(mu), ctypes.byref(sg)))
         return {"theta": th.value, "ld": ld.value, "X": X.value, "y": y.value, "xi": xi.value, "mu": mu.value,
                 "sigma": sg.value}
+
+
+class _Member(Solver):
+    """A batch member's handle (owned by the batch; read-only use)."""
+
+    def __init__(self, h, N, n, opts):
+        self._h = h
+        self.N, self.n = N, n
+        self.options = opts
+
+    def close(self):
+        self._h = ctypes.c_void_p()
+
+
+class BatchSolver:
+    """Many independent fits in one persistent launch (``cr_batch_*``).
+
+    ``instances``: list of (X (N_i x n_i), ybar (N_i,)) host arrays.  Keyword arguments
+    set ``cr_options`` shared by all members (``grid`` > 0 fixes the work granularity
+    factor; 0 lets the autotuner pick it)."""
+
+    def __init__(self, instances, **opts):
+        L = lib()
+        o = default_options(**opts)
+        self.options = o
+        self._keep = []
+        B = len(instances)
+        Ns = (ctypes.c_int64 * B)()
+        ns = (ctypes.c_int32 * B)()
+        Xs = (ctypes.POINTER(ctypes.c_double) * B)()
+        ys = (ctypes.POINTER(ctypes.c_double) * B)()
+        self.sizes = []
+        for i, (X, yb) in enumerate(instances):
+            Xa = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
+            ya = np.ascontiguousarray(np.asarray(yb, dtype=np.float64))
+            self._keep += [Xa, ya]
+            Ns[i], ns[i] = Xa.shape
+            Xs[i] = _dptr(Xa)
+            ys[i] = _dptr(ya)
+            self.sizes.append(Xa.shape)
+        self._h = ctypes.c_void_p()
+        st = L.cr_batch_create(B, Ns, ns, Xs, ys, ctypes.byref(o), ctypes.byref(self._h))
+        if st != CR_OK:
+            raise CrError(st, L.cr_last_error(None).decode())
+        self.B = B
+
+    def _check(self, st, allow=(CR_OK,)):
+        if st not in allow:
+            raise CrError(st, lib().cr_batch_last_error(self._h).decode())
+        return st
+
+    def iterate(self, k: int):
+        self._check(lib().cr_batch_iterate(self._h, int(k)))
+
+    def solve(self, tol: float, max_iter: int) -> int:
+        c = ctypes.c_int64()
+        self._check(lib().cr_batch_solve(self._h, float(tol), int(max_iter), ctypes.byref(c)), (CR_OK, CR_NOT_CONVERGED))
+        return int(c.value)
+
+    def reset(self):
+        self._check(lib().cr_batch_reset(self._h))
+
+    def member(self, i: int) -> Solver:
+        h = ctypes.c_void_p()
+        self._check(lib().cr_batch_instance(self._h, int(i), ctypes.byref(h)))
+        N, n = self.sizes[i]
+        return _Member(h, N, n, self.options)
+
+    def info(self) -> dict:
+        f, g, it = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        self._check(lib().cr_batch_info(self._h, ctypes.byref(f), ctypes.byref(g), ctypes.byref(it)))
+        return {"factor": f.value, "grid": g.value, "iters": it.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cr_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -79,10 +79,11 @@ struct Params {
     int slots;          // column-partial slots per CTA
     long long total;    // S * N units
     // constants
-    double gamma, inv_gamma, L, invL_d, shift;
+    double gamma, inv_gamma, L, invL_d, shift, sigma;
     float invL;
     float st_scale, st_inv_scale;   // theta storage scale (FP16 only; 1 otherwise)
     int momentum, restart, sr;
+    double restart_tol;
     unsigned int seed;
     unsigned long long bar_timeout_ns;   // bound of every grid-barrier wait
     int bar_extra;                       // test hook: extra arrivals a barrier waits for (0 in use)
@@ -322,26 +323,29 @@ __device__ __forceinline__ void block_reduce(double (&v)[K], const bool (&is_max
     __syncthreads();
 }
 
-// Grid-wide barrier for the persistent (cooperative) launch.  Monotone counter:
-// barrier number b completes when the counter reaches (b+1)*G.  The wait is
-// bounded by wall time; on timeout the error word is set and every CTA leaves.
-__device__ __forceinline__ bool grid_barrier(const Params &P, unsigned long long &bar_no)
+// Grid-wide barrier for a cooperative launch of G CTAs.  Monotone counter:
+// barrier number b completes when the counter reaches (b+1)*G (+ extra, a test
+// hook).  The wait is bounded by wall time; on timeout the error word is set and
+// every CTA leaves.
+__device__ __forceinline__ bool bounded_grid_barrier(unsigned long long *count, int *error, unsigned long long G,
+                                                     unsigned long long extra, unsigned long long timeout_ns,
+                                                     unsigned long long &bar_no)
 {
     __syncthreads();
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;
         __threadfence();
-        unsigned long long target = (bar_no + 1ull) * (unsigned long long)P.G + (unsigned long long)P.bar_extra;
-        atomicAdd(&P.st->bar_count, 1ull);
-        unsigned long long t0 = globaltimer();
+        const unsigned long long target = (bar_no + 1ull) * G + extra;
+        atomicAdd(count, 1ull);
+        const unsigned long long t0 = globaltimer();
         while (true) {
             unsigned long long c;
-            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(c) : "l"(&P.st->bar_count) : "memory");
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(c) : "l"(count) : "memory");
             if (c >= target) break;
-            if (*((volatile int *)&P.st->error) != 0) { ok = 0; break; }
-            if (globaltimer() - t0 > P.bar_timeout_ns) {
-                atomicCAS(&P.st->error, 0, ERR_BARRIER);
+            if (*((volatile int *)error) != 0) { ok = 0; break; }
+            if (globaltimer() - t0 > timeout_ns) {
+                atomicCAS(error, 0, ERR_BARRIER);
                 ok = 0;
                 break;
             }
@@ -353,6 +357,12 @@ __device__ __forceinline__ bool grid_barrier(const Params &P, unsigned long long
     __syncthreads();
     ++bar_no;
     return s_ok != 0;
+}
+
+__device__ __forceinline__ bool grid_barrier(const Params &P, unsigned long long &bar_no)
+{
+    return bounded_grid_barrier(&P.st->bar_count, &P.st->error, (unsigned long long)P.G,
+                                (unsigned long long)P.bar_extra, P.bar_timeout_ns, bar_no);
 }
 
 // CTA c's unit range [u0, u1) of the stripe-major (stripe, row) order.
@@ -381,7 +391,7 @@ __device__ __forceinline__ bool mbar_wait(const Params &P, uint64_t *bar, uint32
 // foldB(l): Step 1 at theta^(2)_l (by linearity), mu update, Steps 3-4 scalars
 // ---------------------------------------------------------------------------
 template <int NP>
-__device__ void phase_foldB(const Params &P, long long ell, double *red)
+__device__ void phase_foldB(const Params &P, long long ell, double *red, long long vc)
 {
     const int c = (int)((ell - 1) & 1), p = (int)(ell & 1);
     __shared__ double s_beta;
@@ -409,7 +419,7 @@ __device__ void phase_foldB(const Params &P, long long ell, double *red)
                 // theta^T C eta = u^T y + gamma||xi||^2, u = y - h (Eq. (eq:g_gamma))
                 double dv = 0.5 * a - cc - 0.5 * P.gamma * b;
                 double t = old.t;
-                if (P.restart && dv < old.dual) {
+                if (P.restart && dv < old.dual - P.restart_tol * fabs(old.dual)) {
                     t = 1.0;
                     nw.restarts = old.restarts + 1;
                 }
@@ -420,14 +430,14 @@ __device__ void phase_foldB(const Params &P, long long ell, double *red)
             }
             nw.beta = beta;
             s_beta = beta;
-            if (blockIdx.x == 0) P.st->scal[p] = nw;
+            if (vc == 0) P.st->scal[p] = nw;
         }
     }
     __syncthreads();
     const double beta = s_beta, b1 = 1.0 + beta;
     const long long N = P.N;
     const int n = P.n;
-    for (long long l = (long long)blockIdx.x * kThreads + threadIdx.x; l < N; l += (long long)P.G * kThreads) {
+    for (long long l = vc * kThreads + threadIdx.x; l < N; l += (long long)P.G * kThreads) {
         double v2 = b1 * __ldcg(P.v[c] + l) - beta * __ldcg(P.v[p] + l);
         double mu2 = b1 * __ldcg(P.mu[c] + l) - beta * __ldcg(P.mu[p] + l);
         double y2 = __ldg(P.h + l) + v2 + mu2;
@@ -626,7 +636,7 @@ __device__ __forceinline__ bool produce_stage(const Params &P, unsigned char *st
 
 template <typename TS, int NP>
 __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, uint64_t *full, uint64_t *empty,
-                           unsigned long long &kstage)
+                           unsigned long long &kstage, long long vc)
 {
     using St = Store<TS>;
     using L = PairSmem<TS, NP>;
@@ -634,8 +644,8 @@ __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int p = (int)(ell & 1), c = 1 - p;
     const long long N = P.N, ld = P.ld;
-    const long long ubeg = unit_begin(P, blockIdx.x);
-    const long long uend = unit_begin(P, blockIdx.x + 1);
+    const long long ubeg = unit_begin(P, vc);
+    const long long uend = unit_begin(P, vc + 1);
     unsigned char *stage0 = smem;
     float *flush = reinterpret_cast<float *>(smem + S * L::stage_bytes);
 
@@ -754,7 +764,7 @@ __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, 
         }
         // column partials of this segment: reduce the 4 row groups in shared memory
         const int slotc = (int)(s - first_stripe);
-        float *cp = P.colpart + ((long long)blockIdx.x * P.slots + slotc) * (NP + 1) * kW;
+        float *cp = P.colpart + (vc * P.slots + slotc) * (NP + 1) * kW;
         const int cl = wc * 128 + lane * 4;
         named_barrier_sync(1, kCons);
         *reinterpret_cast<float4 *>(flush + (rg * (NP + 1)) * kW + cl) = make_float4(csum[0], csum[1], csum[2], csum[3]);
@@ -780,14 +790,14 @@ __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, 
 // foldA(l): reduce partials of theta^(1)_l in FP64; eta(theta^(1)_l); dual terms
 // ---------------------------------------------------------------------------
 template <int NP>
-__device__ void phase_foldA(const Params &P, long long ell, double *red)
+__device__ void phase_foldA(const Params &P, long long ell, double *red, long long vc)
 {
     const int p = (int)(ell & 1);
     const long long N = P.N;
     const int n = P.n;
     const int Q4 = P.Q >> 2;   // row partials per row, in float4 units
     double a = 0.0, b = 0.0, cc = 0.0, mviol = 0.0, mcomp = 0.0, sviol = 0.0, smuy = 0.0;
-    for (long long l = (long long)blockIdx.x * kThreads + threadIdx.x; l < N; l += (long long)P.G * kThreads) {
+    for (long long l = vc * kThreads + threadIdx.x; l < N; l += (long long)P.G * kThreads) {
         // row sum: the Q (>= 2S, zero padded) contiguous partials of row l, independent 16-byte loads
         const float4 *rp4 = reinterpret_cast<const float4 *>(P.rowpart + l * P.Q);
         double R = 0.0;
@@ -856,14 +866,14 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red)
     block_reduce<7>(vals, ismax, red);
     if (threadIdx.x == 0)
 #pragma unroll
-        for (int i = 0; i < 7; ++i) P.foldpart[blockIdx.x * 8 + i] = vals[i];
+        for (int i = 0; i < 7; ++i) P.foldpart[vc * 8 + i] = vals[i];
 }
 
 // ---------------------------------------------------------------------------
 // KKT pass at theta^(1)_l: per-pair g = (C eta)_p; FP32 (screen) or FP64
 // ---------------------------------------------------------------------------
 template <typename TS, int NP, bool F64>
-__device__ void phase_kkt(const Params &P, long long ell, double *red)
+__device__ void phase_kkt(const Params &P, long long ell, double *red, long long vc)
 {
     using St = Store<TS>;
     using Vec = typename St::Vec;
@@ -877,8 +887,8 @@ __device__ void phase_kkt(const Params &P, long long ell, double *red)
     double mviol = 0.0, mcomp = 0.0, sviol = 0.0, sthg = 0.0;
     constexpr int REC = RecLayout<NP>::REC;
 
-    long long u = unit_begin(P, blockIdx.x);
-    const long long uend = unit_begin(P, blockIdx.x + 1);
+    long long u = unit_begin(P, vc);
+    const long long uend = unit_begin(P, vc + 1);
     while (warp < kCons / 32 && u < uend) {
         const long long s = u / N;
         const long long r0 = u - s * N;
@@ -937,7 +947,7 @@ __device__ void phase_kkt(const Params &P, long long ell, double *red)
     block_reduce<4>(vals, ismax, red);
     if (threadIdx.x == 0)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) P.kktpart[blockIdx.x * 8 + i] = vals[i];
+        for (int i = 0; i < 4; ++i) P.kktpart[vc * 8 + i] = vals[i];
 }
 
 // Combine the KKT partials (pairs) and the fold partials (y >= 0 rows) into the

@@ -47,16 +47,16 @@ k_persistent(const __grid_constant__ Params P, long long ell0, long long ell1, i
     unsigned long long bar = 0, kstage = 0;
     init_pipeline(full, empty);
 
-    phase_foldB<NP>(P, ell0, red);
+    phase_foldB<NP>(P, ell0, red, blockIdx.x);
     if (!grid_barrier(P, bar)) return;
     for (long long ell = ell0; ell <= ell1; ++ell) {
-        phase_pair<TS, NP>(P, ell, sm, full, empty, kstage);
+        phase_pair<TS, NP>(P, ell, sm, full, empty, kstage, blockIdx.x);
         if (!grid_barrier(P, bar)) return;
-        phase_foldA<NP>(P, ell, red);
+        phase_foldA<NP>(P, ell, red, blockIdx.x);
         if (!grid_barrier(P, bar)) return;
         const bool check = check_every > 0 && ((ell % check_every) == 0 || ell == ell1);
         if (check) {
-            phase_kkt<TS, NP, false>(P, ell, red);
+            phase_kkt<TS, NP, false>(P, ell, red, blockIdx.x);
             if (!grid_barrier(P, bar)) return;
             if (threadIdx.x < 32) {
                 double m[5];
@@ -70,7 +70,7 @@ k_persistent(const __grid_constant__ Params P, long long ell0, long long ell1, i
             bool stop = s_m[0] <= tol;
             const double screen = s_m[5];
             if (stop) {
-                phase_kkt<TS, NP, true>(P, ell, red);
+                phase_kkt<TS, NP, true>(P, ell, red, blockIdx.x);
                 if (!grid_barrier(P, bar)) return;
                 if (threadIdx.x < 32) {
                     double m[5];
@@ -92,7 +92,7 @@ k_persistent(const __grid_constant__ Params P, long long ell0, long long ell1, i
             if (stop) return;
         }
         if (ell < ell1) {
-            phase_foldB<NP>(P, ell + 1, red);
+            phase_foldB<NP>(P, ell + 1, red, blockIdx.x);
             if (!grid_barrier(P, bar)) return;
         }
     }
@@ -112,16 +112,16 @@ k_phase(const __grid_constant__ Params P, int phase, long long ell, double tol, 
     if (err != 0) return;
     if (conv != 0 && phase != PH_KKT64 && phase != PH_DECIDE64) return;
     switch (phase) {
-    case PH_FOLDB: phase_foldB<NP>(P, ell, red); break;
+    case PH_FOLDB: phase_foldB<NP>(P, ell, red, blockIdx.x); break;
     case PH_PAIR: {
         unsigned long long kstage = 0;
         init_pipeline(full, empty);
-        phase_pair<TS, NP>(P, ell, aligned_smem(sm_raw), full, empty, kstage);
+        phase_pair<TS, NP>(P, ell, aligned_smem(sm_raw), full, empty, kstage, blockIdx.x);
         break;
     }
-    case PH_FOLDA: phase_foldA<NP>(P, ell, red); break;
-    case PH_KKT32: phase_kkt<TS, NP, false>(P, ell, red); break;
-    case PH_KKT64: phase_kkt<TS, NP, true>(P, ell, red); break;
+    case PH_FOLDA: phase_foldA<NP>(P, ell, red, blockIdx.x); break;
+    case PH_KKT32: phase_kkt<TS, NP, false>(P, ell, red, blockIdx.x); break;
+    case PH_KKT64: phase_kkt<TS, NP, true>(P, ell, red, blockIdx.x); break;
     case PH_DECIDE32:
     case PH_DECIDE64:
         // single CTA: reduce the KKT partials; tol < 0 only records the metrics
@@ -153,13 +153,117 @@ k_kkt64_if_screened(const __grid_constant__ Params P, long long ell)
 {
     __shared__ double red[72];
     if (__ldcg(&P.st->error) != 0 || __ldcg(&P.st->kkt[6]) == 0.0) return;
-    phase_kkt<TS, NP, true>(P, ell, red);
+    phase_kkt<TS, NP, true>(P, ell, red, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Batched persistent driver: many independent instances (one Params each, in
+// device memory) advance together in one cooperative launch.  Physical CTA b
+// owns the work items off[b]..off[b+1]-1; item j is virtual CTA item_vc[j] of
+// instance item_inst[j].  The phases and their order are those of k_persistent;
+// instances whose KKT test passed leave the work (active[i] = 0).  The first
+// iteration index is read from *ell_base, which the launch advances, so the same
+// launch can be replayed (CUDA graph) chunk after chunk.
+// ---------------------------------------------------------------------------
+struct BatchArgs {
+    const Params *inst;
+    const int *item_inst;
+    const int *item_vc;
+    const int *off;
+    int *active;
+    long long *ell_base;
+    unsigned long long *bar_count;
+    int *error;
+    unsigned long long bar_timeout_ns;
+    int Gphys;
+    int B;
+};
+
+template <typename TS, int NP>
+__global__ void __launch_bounds__(kThreads, 1)
+k_batch(const __grid_constant__ BatchArgs A, long long chunk, int check_every, double tol)
+{
+    extern __shared__ unsigned char sm_raw[];
+    unsigned char *sm = aligned_smem(sm_raw);
+    __shared__ double red[72];
+    __shared__ int s_flag;
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
+    unsigned long long bar = 0, kstage = 0;
+    init_pipeline(full, empty);
+    const int j0 = A.off[blockIdx.x], j1 = A.off[blockIdx.x + 1];
+    const long long ell0 = __ldcg(A.ell_base) + 1, ell1 = ell0 + chunk - 1;
+#define CR_BAR()                                                                                                \
+    if (!bounded_grid_barrier(A.bar_count, A.error, (unsigned long long)A.Gphys, 0ull, A.bar_timeout_ns, bar)) \
+        return;
+#define CR_ITEMS(...)                                           \
+    for (int j = j0; j < j1; ++j) {                             \
+        const int i = A.item_inst[j];                           \
+        const long long vc = A.item_vc[j];                      \
+        if (__ldcg(A.active + i) == 0) continue;                \
+        const Params &P = A.inst[i];                            \
+        __VA_ARGS__;                                            \
+    }
+
+    CR_ITEMS(phase_foldB<NP>(P, ell0, red, vc));
+    CR_BAR();
+    for (long long ell = ell0; ell <= ell1; ++ell) {
+        CR_ITEMS(phase_pair<TS, NP>(P, ell, sm, full, empty, kstage, vc));
+        CR_BAR();
+        CR_ITEMS(phase_foldA<NP>(P, ell, red, vc));
+        CR_BAR();
+        if (check_every > 0 && ((ell % check_every) == 0 || ell == ell1)) {
+            CR_ITEMS(phase_kkt<TS, NP, false>(P, ell, red, vc));
+            CR_BAR();
+            // screen decision per instance (owner = the CTA with its virtual CTA 0)
+            CR_ITEMS(if (vc == 0) {
+                if (threadIdx.x < 32) {
+                    double m[5];
+                    reduce_kkt(P, P.sigma, m);
+                    if (threadIdx.x == 0) {
+                        P.st->kkt[5] = m[0];
+                        P.st->kkt[6] = m[0] <= tol ? 1.0 : 0.0;
+                    }
+                }
+                __syncthreads();
+            });
+            CR_BAR();
+            CR_ITEMS(if (__ldcg(&P.st->kkt[6]) != 0.0) phase_kkt<TS, NP, true>(P, ell, red, vc));
+            CR_BAR();
+            CR_ITEMS(if (vc == 0 && __ldcg(&P.st->kkt[6]) != 0.0) {
+                if (threadIdx.x < 32) {
+                    double m[5];
+                    reduce_kkt(P, P.sigma, m);
+                    if (threadIdx.x == 0) {
+                        for (int q = 0; q < 5; ++q) P.st->kkt[q] = m[q];
+                        if (m[0] <= tol) {
+                            P.st->converged = 1;
+                            P.st->iters_done = ell;
+                            A.active[i] = 0;
+                        }
+                    }
+                }
+                __syncthreads();
+            });
+            CR_BAR();
+        }
+        if (ell < ell1) {
+            CR_ITEMS(phase_foldB<NP>(P, ell + 1, red, vc));
+            CR_BAR();
+        }
+    }
+    // record the iterations of the instances still running, then advance the base
+    CR_ITEMS(if (vc == 0 && threadIdx.x == 0) P.st->iters_done = ell1);
+    (void)s_flag;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *A.ell_base = ell1;
+#undef CR_ITEMS
+#undef CR_BAR
 }
 
 struct KernelSet {
     const void *persistent;
     const void *phase;
     const void *kkt64_if;
+    const void *batch;
     size_t smem;
     int NP;
 };
@@ -170,6 +274,7 @@ template <typename TS, int NP> KernelSet make_set()
     k.persistent = (const void *)k_persistent<TS, NP>;
     k.phase = (const void *)k_phase<TS, NP>;
     k.kkt64_if = (const void *)k_kkt64_if_screened<TS, NP>;
+    k.batch = (const void *)k_batch<TS, NP>;
     k.smem = pair_smem_bytes<TS, NP>();
     k.NP = NP;
     return k;

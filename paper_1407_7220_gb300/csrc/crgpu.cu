@@ -107,7 +107,7 @@ KernelSet kernels_for(int dtype, int NP)
     case CR_THETA_F32: return crk::kernels_f32(NP);
     case CR_THETA_BF16: return crk::kernels_bf16(NP);
     case CR_THETA_F16: return crk::kernels_f16(NP);
-    default: return KernelSet{nullptr, nullptr, nullptr, 0, 0};
+    default: return KernelSet{nullptr, nullptr, nullptr, nullptr, 0, 0};
     }
 }
 
@@ -385,7 +385,7 @@ cr_status init_state(cr_ctx *h)
 }
 
 cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long N, int n, const cr_options *opt,
-                      cr_handle *out)
+                      cr_handle *out, int np_override = 0)
 {
     cr_ctx *h = new (std::nothrow) cr_ctx();
     if (!h) return CR_ENOMEM;
@@ -398,7 +398,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     if (o.kkt_every < 1) return fail(h, CR_EINVAL, "kkt_every must be >= 1");
     h->N = N;
     h->n = n;
-    h->NP = padded_n(n);
+    h->NP = np_override > 0 ? np_override : padded_n(n);
     h->ks = kernels_for(o.theta_dtype, h->NP);
     if (!h->ks.phase) return fail(h, CR_EINVAL, "no kernel for n = %d", n);
 
@@ -429,6 +429,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     const long long min_units = 64;   // keep at least 64 (stripe,row) units per CTA
     if (o.grid <= 0) G = (int)std::max<long long>(1, std::min<long long>(G, total / min_units));
     h->persistent_ok = coop && per_sm > 0 && G <= max_coresident;
+    if (np_override > 0) h->persistent_ok = false;   // batch member: driven by the batch kernel only
     if (o.driver == CR_DRIVER_PERSISTENT && !h->persistent_ok)
         return fail(h, CR_EINVAL, "persistent driver: grid %d exceeds %d co-resident CTAs", G, max_coresident);
 
@@ -461,6 +462,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     P.invL_d = 1.0 / L;
     P.invL = (float)(1.0 / L);
     P.shift = s;
+    P.sigma = h->sigma;
     P.st_scale = 1.0f;
     P.st_inv_scale = 1.0f;
     if (o.theta_dtype == CR_THETA_F16) {
@@ -469,6 +471,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     }
     P.momentum = o.momentum;
     P.restart = o.restart;
+    P.restart_tol = o.restart_tol > 0.0 ? o.restart_tol : 0.0;
     P.sr = o.stochastic_round;
     P.seed = (unsigned)(o.seed ^ (o.seed >> 32));
     P.bar_timeout_ns = (unsigned long long)(o.barrier_timeout_ms > 0 ? o.barrier_timeout_ms : 4000) * 1000000ull;
@@ -590,12 +593,13 @@ void cr_options_default(cr_options *o)
     o->stochastic_round = 1;
     o->kkt_every = 10;
     o->momentum = 1;
-    o->restart = 1;
+    o->restart = 0;
     o->driver = CR_DRIVER_AUTO;
     o->grid = 0;
     o->fp16_exponent = 8;
     o->seed = 0x5eedULL;
     o->stream = nullptr;
+    o->restart_tol = 1e-7;
 }
 
 cr_status cr_create(const double *X, const double *ybar, int64_t N, int32_t n, const cr_options *opt, cr_handle *out)
@@ -796,5 +800,402 @@ void cr_destroy(cr_handle h)
 const char *cr_status_str(cr_status s) { return cr_status_str_impl(s); }
 
 const char *cr_last_error(cr_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+}  // extern "C"
+
+// ===========================================================================
+// Batched solves: many independent instances in one persistent launch
+// ===========================================================================
+struct cr_batch_ctx {
+    std::vector<cr_handle> inst;
+    std::vector<long long> Gfine;     // finest virtual-CTA count per instance
+    int B = 0, NP = 0;
+    KernelSet ks{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int Gphys = 0;
+    Params *dP = nullptr;
+    int *d_item_inst = nullptr, *d_item_vc = nullptr, *d_off = nullptr, *d_active = nullptr, *d_err = nullptr;
+    long long *d_ell = nullptr;
+    unsigned long long *d_bar = nullptr;
+    std::vector<void *> allocs;
+    cudaGraphExec_t gexec = nullptr;
+    long long gchunk = 0;
+    int gcheck = 0;
+    double gtol = -1.0;
+    bool graph_ok = true;
+    int factor = 1;                   // work granularity chosen by the autotuner
+    long long iters = 0;
+    std::string err;
+    std::vector<double> tune_ms;      // autotuner measurements (ms per iteration) per candidate
+    std::vector<int> tune_factor;
+};
+
+namespace {
+
+const int kTuneFactors[] = {1, 2, 4, 8, 16};
+constexpr long long kPairsPerItemFine = 1ll << 17;   // finest work item: ~131k pairs
+
+cr_status bfail(cr_batch_ctx *b, cr_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    g_create_err = buf;
+    return s;
+}
+
+#define CR_BCUDA(b, call)                                                             \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) return bfail(b, CR_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Sets every instance's virtual-CTA count for granularity factor f, assigns the work
+// items to the physical CTAs (longest-processing-time first by pair count) and
+// uploads the instance parameters and the item lists.
+cr_status batch_plan(cr_batch_ctx *b, int f)
+{
+    struct Item {
+        int i;
+        int vc;
+        double cost;
+    };
+    std::vector<Item> items;
+    std::vector<Params> hp(b->B);
+    for (int i = 0; i < b->B; ++i) {
+        cr_ctx *h = b->inst[i];
+        const long long G = std::max<long long>(1, b->Gfine[i] / f);
+        h->P.G = (int)G;
+        h->P.slots = max_slots(h->P.total, h->N, (int)G);
+        hp[i] = h->P;
+        const double pairs = (double)h->N * (double)(h->N - 1);
+        for (long long v = 0; v < G; ++v) items.push_back({i, (int)v, pairs / (double)G + 2.0e4});
+    }
+    std::vector<int> order(items.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return items[x].cost > items[y].cost; });
+    std::vector<double> load(b->Gphys, 0.0);
+    std::vector<std::vector<int>> per(b->Gphys);
+    for (int k : order) {
+        int best = 0;
+        for (int c = 1; c < b->Gphys; ++c)
+            if (load[c] < load[best]) best = c;
+        load[best] += items[k].cost;
+        per[best].push_back(k);
+    }
+    std::vector<int> ii, vv, off(b->Gphys + 1, 0);
+    for (int c = 0; c < b->Gphys; ++c) {
+        std::sort(per[c].begin(), per[c].end(), [&](int x, int y) {
+            return items[x].i != items[y].i ? items[x].i < items[y].i : items[x].vc < items[y].vc;
+        });
+        for (int k : per[c]) {
+            ii.push_back(items[k].i);
+            vv.push_back(items[k].vc);
+        }
+        off[c + 1] = (int)ii.size();
+    }
+    // item arrays are sized for the finest plan (most items)
+    CR_BCUDA(b, cudaMemcpyAsync(b->dP, hp.data(), sizeof(Params) * b->B, cudaMemcpyHostToDevice, b->stream));
+    CR_BCUDA(b, cudaMemcpyAsync(b->d_item_inst, ii.data(), sizeof(int) * ii.size(), cudaMemcpyHostToDevice, b->stream));
+    CR_BCUDA(b, cudaMemcpyAsync(b->d_item_vc, vv.data(), sizeof(int) * vv.size(), cudaMemcpyHostToDevice, b->stream));
+    CR_BCUDA(b, cudaMemcpyAsync(b->d_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, b->stream));
+    CR_BCUDA(b, cudaStreamSynchronize(b->stream));
+    b->factor = f;
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    return CR_OK;
+}
+
+cr_status batch_reset(cr_batch_ctx *b)
+{
+    for (int i = 0; i < b->B; ++i) {
+        cr_status s = init_state(b->inst[i]);
+        if (s != CR_OK) return bfail(b, s, "instance %d: %s", i, b->inst[i]->err.c_str());
+    }
+    std::vector<int> ones(b->B, 1);
+    CR_BCUDA(b, cudaMemcpyAsync(b->d_active, ones.data(), sizeof(int) * b->B, cudaMemcpyHostToDevice, b->stream));
+    CR_BCUDA(b, cudaMemsetAsync(b->d_ell, 0, sizeof(long long), b->stream));
+    CR_BCUDA(b, cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
+    CR_BCUDA(b, cudaStreamSynchronize(b->stream));
+    b->iters = 0;
+    return CR_OK;
+}
+
+// One launch of `chunk` iterations (a graph replay when the launch could be captured).
+cr_status batch_launch(cr_batch_ctx *b, long long chunk, int check_every, double tol)
+{
+    crk::BatchArgs A;
+    A.inst = b->dP;
+    A.item_inst = b->d_item_inst;
+    A.item_vc = b->d_item_vc;
+    A.off = b->d_off;
+    A.active = b->d_active;
+    A.ell_base = b->d_ell;
+    A.bar_count = b->d_bar;
+    A.error = b->d_err;
+    A.bar_timeout_ns = b->inst[0]->P.bar_timeout_ns;
+    A.Gphys = b->Gphys;
+    A.B = b->B;
+    void *args[] = {&A, &chunk, &check_every, &tol};
+    const bool same = b->gexec && b->gchunk == chunk && b->gcheck == check_every && b->gtol == tol;
+    if (!same && b->graph_ok) {
+        if (b->gexec) {
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        bool ok = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned long long), b->stream);
+            cudaLaunchCooperativeKernel(b->ks.batch, dim3(b->Gphys), dim3(crk::kThreads), args, b->ks.smem, b->stream);
+            ok = cudaStreamEndCapture(b->stream, &g) == cudaSuccess && g;
+        }
+        if (ok) ok = cudaGraphInstantiate(&b->gexec, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        if (!ok) {
+            (void)cudaGetLastError();
+            b->gexec = nullptr;
+            b->graph_ok = false;   // cooperative launches not capturable here: launch directly
+        } else {
+            b->gchunk = chunk;
+            b->gcheck = check_every;
+            b->gtol = tol;
+        }
+    }
+    if (b->gexec) {
+        CR_BCUDA(b, cudaGraphLaunch(b->gexec, b->stream));
+    } else {
+        CR_BCUDA(b, cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned long long), b->stream));
+        CR_BCUDA(b, cudaLaunchCooperativeKernel(b->ks.batch, dim3(b->Gphys), dim3(crk::kThreads), args, b->ks.smem,
+                                                b->stream));
+    }
+    return CR_OK;
+}
+
+cr_status batch_sync_error(cr_batch_ctx *b)
+{
+    int e = 0;
+    CR_BCUDA(b, cudaMemcpyAsync(&e, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    CR_BCUDA(b, cudaStreamSynchronize(b->stream));
+    if (e == crk::ERR_BARRIER || e == crk::ERR_PIPE) return bfail(b, CR_ETIMEOUT, "a bounded device wait gave up");
+    if (e != 0) return bfail(b, CR_ENUMERIC, "device error %d", e);
+    return CR_OK;
+}
+
+// Autotuner: times `probe` iterations for each work granularity and keeps the fastest.
+cr_status batch_autotune(cr_batch_ctx *b, int probe)
+{
+    cudaEvent_t e0, e1;
+    CR_BCUDA(b, cudaEventCreate(&e0));
+    CR_BCUDA(b, cudaEventCreate(&e1));
+    double best = 1e300;
+    int bestf = 1;
+    b->tune_ms.clear();
+    b->tune_factor.clear();
+    for (int f : kTuneFactors) {
+        CR_TRY(batch_plan(b, f));
+        CR_TRY(batch_reset(b));
+        CR_TRY(batch_launch(b, 2, 0, -1.0));   // warm-up
+        CR_BCUDA(b, cudaEventRecord(e0, b->stream));
+        CR_TRY(batch_launch(b, probe, 0, -1.0));
+        CR_BCUDA(b, cudaEventRecord(e1, b->stream));
+        CR_TRY(batch_sync_error(b));
+        float ms = 0.0f;
+        CR_BCUDA(b, cudaEventElapsedTime(&ms, e0, e1));
+        b->tune_ms.push_back(ms / probe);
+        b->tune_factor.push_back(f);
+        if (ms < best) {
+            best = ms;
+            bestf = f;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CR_TRY(batch_plan(b, bestf));
+    return batch_reset(b);
+}
+
+}  // namespace
+
+extern "C" {
+
+cr_status cr_batch_create(int32_t B, const int64_t *N, const int32_t *n, const double *const *X,
+                          const double *const *ybar, const cr_options *opt, cr_batch_handle *out)
+{
+    if (!out) return create_error(CR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (B < 1 || !N || !n || !X || !ybar) return create_error(CR_EINVAL, "need B >= 1 and non-NULL arrays");
+    cr_options o;
+    if (opt) o = *opt;
+    else cr_options_default(&o);
+    int nmax = 0;
+    for (int i = 0; i < B; ++i) {
+        if (check_inputs(X[i], ybar[i], N[i], n[i]) != CR_OK)
+            return create_error(CR_EINVAL, ("instance " + std::to_string(i) + ": invalid sizes or values").c_str());
+        nmax = std::max(nmax, (int)n[i]);
+    }
+    cr_batch_ctx *b = new (std::nothrow) cr_batch_ctx();
+    if (!b) return create_error(CR_ENOMEM, "out of host memory");
+    b->B = B;
+    b->NP = padded_n(nmax);
+    b->ks = kernels_for(o.theta_dtype, b->NP);
+    auto cleanup = [&](cr_status s) {
+        cr_batch_destroy(b);
+        return s;
+    };
+    if (!b->ks.batch) return cleanup(create_error(CR_EINVAL, "no kernel for this dtype / n"));
+    if (o.stream) {
+        b->stream = (cudaStream_t)o.stream;
+    } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        return cleanup(create_error(CR_ECUDA, "cannot create a stream"));
+    } else {
+        b->own_stream = true;
+    }
+    // instances: finest work items, shared stream, the batch's padded n
+    for (int i = 0; i < B; ++i) {
+        cr_options oi = o;
+        oi.stream = b->stream;
+        const double pairs = (double)N[i] * (double)(N[i] - 1);
+        const long long Gf = std::max<long long>(1, (long long)std::ceil(pairs / (double)kPairsPerItemFine));
+        oi.grid = (int)Gf;
+        oi.driver = CR_DRIVER_PHASES;
+        std::vector<double> Xv(X[i], X[i] + (size_t)N[i] * n[i]), yv(ybar[i], ybar[i] + N[i]);
+        cr_handle h = nullptr;
+        cr_status s = create_impl(Xv, yv, N[i], n[i], &oi, &h, b->NP);
+        if (s != CR_OK) {
+            std::string m = h ? h->err : "";
+            cr_destroy(h);
+            return cleanup(create_error(s, ("instance " + std::to_string(i) + ": " + m).c_str()));
+        }
+        b->inst.push_back(h);
+        b->Gfine.push_back(Gf);
+        // column partials sized for every granularity the autotuner may pick
+        long long need = 0;
+        for (int f : kTuneFactors) {
+            const long long G = std::max<long long>(1, Gf / f);
+            need = std::max<long long>(need, G * max_slots(h->P.total, h->N, (int)G));
+        }
+        if (need > (long long)h->P.G * h->P.slots) {
+            float *cp = nullptr;
+            if (dev_alloc(h, &cp, (size_t)need * (b->NP + 1) * crk::kW) != CR_OK)
+                return cleanup(create_error(CR_ENOMEM, "column partials"));
+            cudaMemsetAsync(cp, 0, sizeof(float) * (size_t)need * (b->NP + 1) * crk::kW, b->stream);
+            h->P.colpart = cp;
+        }
+    }
+    // physical grid: every co-resident CTA of the batch kernel
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(b->ks.batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->ks.smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b->ks.batch, crk::kThreads, b->ks.smem) != cudaSuccess ||
+        per_sm < 1)
+        return cleanup(create_error(CR_ECUDA, "batch kernel does not fit on this device"));
+    b->Gphys = sms * per_sm;
+    long long nitems = 0;
+    for (long long g : b->Gfine) nitems += g;
+    auto balloc = [&](void **p, size_t bytes) {
+        if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
+        b->allocs.push_back(*p);
+        return true;
+    };
+    if (!balloc((void **)&b->dP, sizeof(Params) * B) || !balloc((void **)&b->d_item_inst, sizeof(int) * nitems) ||
+        !balloc((void **)&b->d_item_vc, sizeof(int) * nitems) || !balloc((void **)&b->d_off, sizeof(int) * (b->Gphys + 1)) ||
+        !balloc((void **)&b->d_active, sizeof(int) * B) || !balloc((void **)&b->d_ell, sizeof(long long)) ||
+        !balloc((void **)&b->d_bar, sizeof(unsigned long long)) || !balloc((void **)&b->d_err, sizeof(int)))
+        return cleanup(create_error(CR_ENOMEM, "batch descriptors"));
+    cr_status s = (o.grid > 0) ? batch_plan(b, std::max(1, o.grid)) : batch_autotune(b, 8);
+    if (s == CR_OK && o.grid > 0) s = batch_reset(b);
+    if (s != CR_OK) return cleanup(create_error(s, b->err.c_str()));
+    *out = b;
+    return CR_OK;
+}
+
+cr_status cr_batch_solve(cr_batch_handle b, double tol, int64_t max_iter, int64_t *converged)
+{
+    if (!b || max_iter < 0) return CR_EINVAL;
+    if (converged) *converged = 0;
+    const int check = std::max(1, (int)b->inst[0]->opt.kkt_every);
+    long long done = 0;
+    std::vector<int> act(b->B);
+    int nact = b->B;
+    while (done < max_iter && nact > 0) {
+        const long long chunk = std::min<long long>(max_iter - done, 2000);
+        CR_TRY(batch_launch(b, chunk, tol >= 0.0 ? check : 0, tol));
+        CR_TRY(batch_sync_error(b));
+        CR_BCUDA(b, cudaMemcpy(act.data(), b->d_active, sizeof(int) * b->B, cudaMemcpyDeviceToHost));
+        nact = 0;
+        for (int a : act) nact += a;
+        done += chunk;
+        b->iters += chunk;
+    }
+    // iteration counts of the instances (host view)
+    for (int i = 0; i < b->B; ++i) {
+        DevState st;
+        CR_TRY(read_state(b->inst[i], &st));
+        b->inst[i]->iters = st.iters_done;
+    }
+    if (converged) *converged = b->B - nact;
+    return nact == 0 ? CR_OK : CR_NOT_CONVERGED;
+}
+
+cr_status cr_batch_iterate(cr_batch_handle b, int64_t k)
+{
+    if (!b || k < 0) return CR_EINVAL;
+    long long done = 0;
+    while (done < k) {
+        const long long chunk = std::min<long long>(k - done, 2000);
+        CR_TRY(batch_launch(b, chunk, 0, -1.0));
+        done += chunk;
+    }
+    CR_TRY(batch_sync_error(b));
+    b->iters += k;
+    for (int i = 0; i < b->B; ++i) {
+        DevState st;
+        CR_TRY(read_state(b->inst[i], &st));
+        b->inst[i]->iters = st.iters_done;
+    }
+    return CR_OK;
+}
+
+cr_status cr_batch_reset(cr_batch_handle b)
+{
+    if (!b) return CR_EINVAL;
+    return batch_reset(b);
+}
+
+cr_status cr_batch_instance(cr_batch_handle b, int32_t i, cr_handle *h)
+{
+    if (!b || i < 0 || i >= b->B || !h) return CR_EINVAL;
+    *h = b->inst[i];
+    return CR_OK;
+}
+
+cr_status cr_batch_info(cr_batch_handle b, int32_t *factor, int32_t *grid, int64_t *iters)
+{
+    if (!b) return CR_EINVAL;
+    if (factor) *factor = b->factor;
+    if (grid) *grid = b->Gphys;
+    if (iters) *iters = b->iters;
+    return CR_OK;
+}
+
+void cr_batch_destroy(cr_batch_handle b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (cr_handle h : b->inst) cr_destroy(h);
+    for (void *p : b->allocs) cudaFree(p);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+const char *cr_batch_last_error(cr_batch_handle b) { return b ? b->err.c_str() : g_create_err.c_str(); }
 
 }  // extern "C"

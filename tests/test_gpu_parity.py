@@ -32,7 +32,8 @@ def _pair(crg, X, yb, k, gamma=0.1, **opts):
     """Run k iterations on both sides from Iteration 0; returns (gpu Solver, oracle Solver)."""
     g = crg.Solver(X, yb, gamma=gamma, **opts)
     o = O.Solver(X, yb, gamma=gamma, L=g.info()["L"], s=g.info()["shift"],
-                 momentum=bool(g.options.momentum), restart=bool(g.options.restart))
+                 momentum=bool(g.options.momentum), restart=bool(g.options.restart),
+                 restart_tol=g.options.restart_tol)
     if k:
         g.iterate(k)
         o.iterate(k)
@@ -142,7 +143,7 @@ def test_converged_fit_matches_oracle_reference(crg):
     ref = np.load(path)
     X, yb, _ = datagen.make("sq2", N=500)
     assert float(ref["X_sum"]) == pytest.approx(X.sum(), rel=0, abs=1e-12)
-    g = crg.Solver(X, yb, gamma=0.1, stochastic_round=1, restart=1, kkt_every=50)
+    g = crg.Solver(X, yb, gamma=0.1, stochastic_round=1, restart=0, kkt_every=50)
     conv, iters = g.solve(1e-6, 3_000_000)
     k = g.kkt_residual()
     y, xi = g.solution()
