@@ -83,7 +83,9 @@ typedef struct {
     int32_t test_barrier_extra; /* test hook, 0 in use: barriers wait for this many extra arrivals
                                    that never come, so the bounded wait runs out on purpose */
     int32_t profile;          /* 1: record CUDA events around every kernel launch (see cr_profile) */
-    int32_t reserved[5];
+    int32_t record_every;     /* > 0: cr_iterate keeps a checkpoint every this many iterations so that
+                                 cr_backward can differentiate the unrolled iterations (FP32 theta, n <= 10) */
+    int32_t reserved[4];
     double restart_tol;       /* restart only when the dual value fell by more than restart_tol * |previous|
                                  (guards the test against rounding noise); default 1e-7 */
 } cr_options;
@@ -133,6 +135,16 @@ cr_status cr_objective(cr_handle h, double *primal, double *dual, double *gap);
  *   gap_norm    = theta^T C eta / (N^2 - N)                    (Sec. III)
  * Every per-pair term is evaluated in FP64.  Any pointer may be NULL.  Blocks. */
 cr_status cr_kkt_residual(cr_handle h, double *kkt, double *infeas_norm, double *gap_norm);
+
+/* Reverse mode through the iterations run so far (all by cr_iterate from Iteration 0 with
+ * record_every > 0): given dL_dyhat (device, N floats) = dLoss/dyhat of the current fitted
+ * values, writes dLoss/dybar (device, N floats) and dLoss/dX (device, N x n floats).  The
+ * iterations are plain P-APG (restart = 0) with gamma, L and the shift s held fixed; the
+ * projection max(0, .) differentiates to its active indicator (0 at a tie).  Every
+ * record_every iterations form a segment: the segment is recomputed from its checkpoint
+ * (bit for bit) and then reversed.  The handle's state is restored afterwards.  Workspace:
+ * record_every + 3 multiplier arrays plus O(N n) vectors.  Blocks. */
+cr_status cr_backward(cr_handle h, const float *dL_dyhat, float *dL_dybar, float *dL_dX);
 
 /* Fitted values yhat (N, shift removed) and subgradients xi (N x n, row-major) at the current
  * dual iterate, in FP64, to host buffers (either may be NULL).  Blocks. */

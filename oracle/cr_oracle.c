@@ -413,6 +413,124 @@ ORC_API int64_t orc_papg(const double *X, const double *h, int64_t N, int32_t n,
     return it;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Forward-mode derivative of K iterations of P-APG (Fig. 2) from Iteration 0 */
+/* ------------------------------------------------------------------------ */
+
+/* Tangent of the fitted values yhat = y(theta^(1)_K) - s along a direction
+ * (dybar, dX) of the data, with gamma, L and the shift s held fixed and plain
+ * P-APG momentum (no restart).  Every step of the loop is differentiated as
+ * written: Step 1 (closed form, linear in theta and in X through A_2), Step 2
+ * (the projection max(0, .) differentiates to its active indicator), Steps 3-4
+ * (linear).  Returns yhat (N) and its tangent dyhat (N). */
+ORC_API void orc_papg_jvp(const double *X, const double *ybar, int64_t N, int32_t n, double gamma, double L,
+                          double s, int64_t K, const double *dybar, const double *dX, double *yhat,
+                          double *dyhat)
+{
+    const size_t NN = (size_t)N * (size_t)N;
+    double *P = (double *)calloc(NN, sizeof(double)), *T2 = (double *)calloc(NN, sizeof(double));
+    double *dP = (double *)calloc(NN, sizeof(double)), *dT2 = (double *)calloc(NN, sizeof(double));
+    double *muP = (double *)calloc(N, sizeof(double)), *mu2 = (double *)calloc(N, sizeof(double));
+    double *dmuP = (double *)calloc(N, sizeof(double)), *dmu2 = (double *)calloc(N, sizeof(double));
+    double *h = (double *)malloc(sizeof(double) * N), *y = (double *)malloc(sizeof(double) * N);
+    double *dy = (double *)malloc(sizeof(double) * N), *xi = (double *)malloc(sizeof(double) * N * n);
+    double *dxi = (double *)malloc(sizeof(double) * N * n);
+    double *nw = (double *)malloc(sizeof(double) * NN), *dnw = (double *)malloc(sizeof(double) * NN);
+    double *mun = (double *)malloc(sizeof(double) * N), *dmun = (double *)malloc(sizeof(double) * N);
+    const double invL = 1.0 / L;
+    for (int64_t l = 0; l < N; ++l) h[l] = ybar[l] + s;
+    double t = 1.0;
+    for (int64_t it = 0; it < K; ++it) {
+        /* Step 1 and its tangent:
+         *   y = h + sum_m T2[l][m] - sum_m T2[m][l] + mu2,       dy = dybar + (same with dT2) + dmu2
+         *   gamma xi_l = sum_m T2[m][l] (x_l - x_m),
+         *   gamma dxi_l = sum_m dT2[m][l] (x_l - x_m) + sum_m T2[m][l] (dx_l - dx_m) */
+#pragma omp parallel for schedule(static)
+        for (int64_t l = 0; l < N; ++l) {
+            double r = 0.0, dr = 0.0, c = 0.0, dc = 0.0;
+            for (int64_t m = 0; m < N; ++m) {
+                if (m == l) continue;
+                r += T2[l * N + m] - T2[m * N + l];
+                dr += dT2[l * N + m] - dT2[m * N + l];
+            }
+            (void)c;
+            (void)dc;
+            y[l] = h[l] + r + mu2[l];
+            dy[l] = dybar[l] + dr + dmu2[l];
+            for (int k = 0; k < n; ++k) {
+                double a = 0.0, da = 0.0;
+                for (int64_t m = 0; m < N; ++m) {
+                    if (m == l) continue;
+                    const double tm = T2[m * N + l], dtm = dT2[m * N + l];
+                    a += tm * (X[l * n + k] - X[m * n + k]);
+                    da += dtm * (X[l * n + k] - X[m * n + k]) + tm * (dX[l * n + k] - dX[m * n + k]);
+                }
+                xi[l * n + k] = a / gamma;
+                dxi[l * n + k] = da / gamma;
+            }
+        }
+        /* Step 2 and its tangent: new = max(0, T2 - g/L), g = y_l1 - y_l2 - xi_l2 (x_l1 - x_l2) */
+#pragma omp parallel for schedule(static)
+        for (int64_t l1 = 0; l1 < N; ++l1) {
+            for (int64_t l2 = 0; l2 < N; ++l2) {
+                const size_t q = (size_t)l1 * N + l2;
+                if (l1 == l2) {
+                    nw[q] = 0.0;
+                    dnw[q] = 0.0;
+                    continue;
+                }
+                double g = y[l1] - y[l2], dg = dy[l1] - dy[l2];
+                for (int k = 0; k < n; ++k) {
+                    const double dx = X[l1 * n + k] - X[l2 * n + k];
+                    g -= xi[l2 * n + k] * dx;
+                    dg -= dxi[l2 * n + k] * dx + xi[l2 * n + k] * (dX[l1 * n + k] - dX[l2 * n + k]);
+                }
+                const double v = T2[q] - g * invL;
+                nw[q] = v > 0.0 ? v : 0.0;
+                dnw[q] = v > 0.0 ? dT2[q] - dg * invL : 0.0;
+            }
+        }
+        for (int64_t l = 0; l < N; ++l) {
+            const double v = mu2[l] - y[l] * invL;
+            mun[l] = v > 0.0 ? v : 0.0;
+            dmun[l] = v > 0.0 ? dmu2[l] - dy[l] * invL : 0.0;
+        }
+        /* Steps 3-4 */
+        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        const double beta = (t - 1.0) / tn;
+        t = tn;
+#pragma omp parallel for schedule(static)
+        for (int64_t l1 = 0; l1 < N; ++l1)
+            for (int64_t l2 = 0; l2 < N; ++l2) {
+                const size_t q = (size_t)l1 * N + l2;
+                T2[q] = nw[q] + beta * (nw[q] - P[q]);
+                dT2[q] = dnw[q] + beta * (dnw[q] - dP[q]);
+                P[q] = nw[q];
+                dP[q] = dnw[q];
+            }
+        for (int64_t l = 0; l < N; ++l) {
+            mu2[l] = mun[l] + beta * (mun[l] - muP[l]);
+            dmu2[l] = dmun[l] + beta * (dmun[l] - dmuP[l]);
+            muP[l] = mun[l];
+            dmuP[l] = dmun[l];
+        }
+    }
+    /* fitted values at theta^(1)_K = P: yhat = ybar + A_1^T P + muP */
+#pragma omp parallel for schedule(static)
+    for (int64_t l = 0; l < N; ++l) {
+        double r = 0.0, dr = 0.0;
+        for (int64_t m = 0; m < N; ++m) {
+            if (m == l) continue;
+            r += P[l * N + m] - P[m * N + l];
+            dr += dP[l * N + m] - dP[m * N + l];
+        }
+        yhat[l] = ybar[l] + r + muP[l];
+        dyhat[l] = dybar[l] + dr + dmuP[l];
+    }
+    free(P); free(T2); free(dP); free(dT2); free(muP); free(mu2); free(dmuP); free(dmu2);
+    free(h); free(y); free(dy); free(xi); free(dxi); free(nw); free(dnw); free(mun); free(dmun);
+}
+
 ORC_API int orc_num_threads(void)
 {
 #ifdef _OPENMP

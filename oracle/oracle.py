@@ -25,7 +25,7 @@ _lib = None
 
 __all__ = [
     "build_oracle", "shift", "lipschitz", "eta", "residual", "metrics", "Solver",
-    "METRIC_NAMES", "num_threads",
+    "METRIC_NAMES", "num_threads", "papg_jvp",
 ]
 
 METRIC_NAMES = ("kkt", "pri", "comp", "infeas", "gap", "primal", "dual", "fit", "sum_check")
@@ -70,6 +70,8 @@ def _load():
             lib.orc_papg.argtypes = [dp, dp, i64, i32, ctypes.POINTER(_Opts), dp, dp, dp, dp, dp, i64,
                                      dp, dp, dp]
             lib.orc_papg.restype = i64
+            lib.orc_papg_jvp.argtypes = [dp, dp, i64, i32, d, d, d, i64, dp, dp, dp, dp]
+            lib.orc_papg_jvp.restype = None
             lib.orc_num_threads.argtypes = []
             lib.orc_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -127,6 +129,18 @@ def metrics(theta, mu, y, xi, X, h, gamma: float, sigma: float) -> dict:
     _load().orc_metrics(_p(theta), _p(mu), _p(y), _p(xi), _p(X), _p(h), N, n, float(gamma),
                         float(sigma), _p(out))
     return dict(zip(METRIC_NAMES, out.tolist()))
+
+
+def papg_jvp(X, ybar, gamma: float, L: float, s: float, K: int, dybar, dX):
+    """(yhat, d yhat) after K iterations of plain P-APG from Iteration 0, forward-mode along
+    (dybar, dX), with gamma, L and the shift s held fixed."""
+    X, ybar, dybar, dX = _f64(X), _f64(ybar), _f64(dybar), _f64(dX)
+    N, n = X.shape
+    yhat = np.empty(N)
+    dyhat = np.empty(N)
+    _load().orc_papg_jvp(_p(X), _p(ybar), N, n, float(gamma), float(L), float(s), int(K), _p(dybar), _p(dX),
+                         _p(yhat), _p(dyhat))
+    return yhat, dyhat
 
 
 def data_scale(ybar) -> float:

@@ -40,7 +40,7 @@ exported_symbols = (
     "cr_objective", "cr_kkt_residual", "cr_get_solution", "cr_get_info", "cr_destroy",
     "cr_status_str", "cr_last_error", "cr_profile", "cr_get_device_state", "cr_kkt_residual_noalloc",
     "cr_batch_create", "cr_batch_solve", "cr_batch_iterate", "cr_batch_reset", "cr_batch_instance",
-    "cr_batch_info", "cr_batch_destroy", "cr_batch_last_error",
+    "cr_batch_info", "cr_batch_destroy", "cr_batch_last_error", "cr_backward",
 )
 PROFILE_PAIR, PROFILE_FOLD, PROFILE_KKT, PROFILE_PERSISTENT = 0, 1, 2, 3
 
@@ -53,7 +53,8 @@ class Options(ctypes.Structure):
         ("kkt_every", ctypes.c_int32), ("momentum", ctypes.c_int32), ("restart", ctypes.c_int32),
         ("driver", ctypes.c_int32), ("grid", ctypes.c_int32), ("fp16_exponent", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("barrier_timeout_ms", ctypes.c_int32),
-        ("test_barrier_extra", ctypes.c_int32), ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
+        ("test_barrier_extra", ctypes.c_int32), ("profile", ctypes.c_int32), ("record_every", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
         ("restart_tol", ctypes.c_double),
     ]
 
@@ -115,6 +116,8 @@ def lib():
             for name in ("cr_batch_create", "cr_batch_solve", "cr_batch_iterate", "cr_batch_reset",
                          "cr_batch_instance", "cr_batch_info"):
                 getattr(L, name).restype = ctypes.c_int
+            L.cr_backward.argtypes = [H, fp, fp, fp]
+            L.cr_backward.restype = ctypes.c_int
             L.cr_profile.argtypes = [H, ctypes.c_int32, dp, i64p]
             L.cr_profile.restype = ctypes.c_int
             L.cr_destroy.argtypes = [H]
@@ -239,6 +242,13 @@ class Solver:
         Lc, s = ctypes.c_double(), ctypes.c_double()
         self._check(lib().cr_get_info(self._h, ctypes.byref(it), ctypes.byref(rs), ctypes.byref(Lc), ctypes.byref(s)))
         return {"iters": it.value, "restarts": rs.value, "L": Lc.value, "shift": s.value}
+
+    def backward(self, dL_dyhat, dL_dybar, dL_dX):
+        """Reverse mode through the recorded iterations; device float32 torch tensors (N,), (N,), (N, n)."""
+        for t in (dL_dyhat, dL_dybar, dL_dX):
+            assert t.is_cuda and t.dtype.is_floating_point and t.is_contiguous()
+        self._check(lib().cr_backward(self._h, ctypes.c_void_p(dL_dyhat.data_ptr()),
+                                      ctypes.c_void_p(dL_dybar.data_ptr()), ctypes.c_void_p(dL_dX.data_ptr())))
 
     def profile(self, kind: int) -> tuple[float, int]:
         """(summed device ms, launches) of one kernel kind since the last read (needs profile=1)."""

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "cr_kernels.cuh"
+#include "cr_backward.cuh"
 
 namespace crk {
 
@@ -266,7 +267,12 @@ struct KernelSet {
     const void *batch;
     size_t smem;
     int NP;
+    BwdKernels bwd;
 };
+
+// dLoss/dybar = ubar + accumulated, dLoss/dX = accumulated (FP64 -> FP32 outputs)
+__global__ void k_bwd_finish(long long N, int n, const float *ubar, const double *ybar_acc, const double *X_acc,
+                             float *dybar, float *dX);
 
 template <typename TS, int NP> KernelSet make_set()
 {
@@ -277,6 +283,7 @@ template <typename TS, int NP> KernelSet make_set()
     k.batch = (const void *)k_batch<TS, NP>;
     k.smem = pair_smem_bytes<TS, NP>();
     k.NP = NP;
+    k.bwd = make_bwd<NP>();
     return k;
 }
 

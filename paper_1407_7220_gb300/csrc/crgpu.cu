@@ -21,6 +21,17 @@
 #include "cr_launch.cuh"
 #include "crgpu.h"
 
+namespace crk {
+__global__ void k_bwd_finish(long long N, int n, const float *ubar, const double *ybar_acc, const double *X_acc,
+                             float *dybar, float *dX)
+{
+    for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < N; l += (long long)gridDim.x * blockDim.x) {
+        dybar[l] = (float)((double)ubar[l] + ybar_acc[l]);   // yhat = ybar + A_1^T theta + mu
+        for (int k = 0; k < n; ++k) dX[l * n + k] = (float)X_acc[l * n + k];
+    }
+}
+}  // namespace crk
+
 using crk::DevState;
 using crk::KernelSet;
 using crk::Params;
@@ -52,6 +63,21 @@ struct cr_ctx {
     std::vector<cudaEvent_t> pool;
     double prof_ms[4] = {0, 0, 0, 0};
     long long prof_n[4] = {0, 0, 0, 0};
+    // differentiation: checkpoints every record_every iterations (cr_options.reserved[0])
+    struct Checkpoint {
+        long long iter = -1;
+        void *th[2] = {nullptr, nullptr};
+        double *v[2] = {nullptr, nullptr}, *w[2] = {nullptr, nullptr}, *mu[2] = {nullptr, nullptr};
+        DevState st;
+        // full snapshots also keep the minimizer at theta^(1) and the fold partials
+        bool full = false;
+        double *y1 = nullptr, *xi1_64 = nullptr, *foldpart = nullptr;
+        float *yrow1 = nullptr, *ccol1 = nullptr, *xi1 = nullptr;
+    };
+    int record_every = 0;
+    std::vector<Checkpoint> ckpt;       // at iterations 0, k, 2k, ...
+    std::vector<void *> ckpt_allocs;
+    std::vector<void *> bwd_allocs;     // reverse-mode workspace (lazily allocated)
 };
 
 namespace {
@@ -107,7 +133,7 @@ KernelSet kernels_for(int dtype, int NP)
     case CR_THETA_F32: return crk::kernels_f32(NP);
     case CR_THETA_BF16: return crk::kernels_bf16(NP);
     case CR_THETA_F16: return crk::kernels_f16(NP);
-    default: return KernelSet{nullptr, nullptr, nullptr, nullptr, 0, 0};
+    default: return KernelSet{nullptr, nullptr, nullptr, nullptr, 0, 0, {nullptr, nullptr, nullptr, nullptr}};
     }
 }
 
@@ -384,6 +410,87 @@ cr_status init_state(cr_ctx *h)
     return CR_OK;
 }
 
+// ---- checkpoints of the iteration state (differentiation) ------------------
+cr_status ckpt_save(cr_ctx *h, cr_ctx::Checkpoint &c)
+{
+    const size_t th = (size_t)h->N * h->ld * sizeof(float);
+    const long long N = h->N;
+    auto al = [&](void **p, size_t bytes) {
+        if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+        h->ckpt_allocs.push_back(*p);
+        return true;
+    };
+    if (!c.th[0]) {
+        for (int b = 0; b < 2; ++b)
+            if (!al(&c.th[b], th) || !al((void **)&c.v[b], sizeof(double) * h->N) ||
+                !al((void **)&c.w[b], sizeof(double) * h->N * h->n) || !al((void **)&c.mu[b], sizeof(double) * h->N)) {
+                (void)cudaGetLastError();
+                return fail(h, CR_ENOMEM, "checkpoint allocation failed");
+            }
+    }
+    if (c.full && !c.y1) {
+        if (!al((void **)&c.y1, sizeof(double) * N) || !al((void **)&c.xi1_64, sizeof(double) * N * h->n) ||
+            !al((void **)&c.foldpart, sizeof(double) * h->P.G * 8) || !al((void **)&c.yrow1, sizeof(float) * N) ||
+            !al((void **)&c.ccol1, sizeof(float) * N) || !al((void **)&c.xi1, sizeof(float) * N * h->NP)) {
+            (void)cudaGetLastError();
+            return fail(h, CR_ENOMEM, "checkpoint allocation failed");
+        }
+    }
+    if (c.full) {
+        CR_CUDA(h, cudaMemcpyAsync(c.y1, h->P.y1, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(c.xi1_64, h->P.xi1_64, sizeof(double) * N * h->n, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(c.foldpart, h->P.foldpart, sizeof(double) * h->P.G * 8, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(c.yrow1, h->P.yrow1, sizeof(float) * N, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(c.ccol1, h->P.ccol1, sizeof(float) * N, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(c.xi1, h->P.xi1, sizeof(float) * N * h->NP, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    for (int b = 0; b < 2; ++b) {
+        CR_CUDA(h, cudaMemcpyAsync(c.th[b], h->P.theta[b], th, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(c.v[b], h->P.v[b], sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(c.w[b], h->P.w[b], sizeof(double) * h->N * h->n, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(c.mu[b], h->P.mu[b], sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    CR_CUDA(h, cudaMemcpyAsync(&c.st, h->P.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    CR_CUDA(h, cudaStreamSynchronize(h->stream));
+    c.iter = h->iters;
+    return CR_OK;
+}
+
+cr_status ckpt_restore(cr_ctx *h, const cr_ctx::Checkpoint &c)
+{
+    const size_t th = (size_t)h->N * h->ld * sizeof(float);
+    for (int b = 0; b < 2; ++b) {
+        CR_CUDA(h, cudaMemcpyAsync(h->P.theta[b], c.th[b], th, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(h->P.v[b], c.v[b], sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(h->P.w[b], c.w[b], sizeof(double) * h->N * h->n, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(h->P.mu[b], c.mu[b], sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    if (c.full) {
+        const long long N = h->N;
+        CR_CUDA(h, cudaMemcpyAsync(h->P.y1, c.y1, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(h->P.xi1_64, c.xi1_64, sizeof(double) * N * h->n, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(h->P.foldpart, c.foldpart, sizeof(double) * h->P.G * 8, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(h->P.yrow1, c.yrow1, sizeof(float) * N, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(h->P.ccol1, c.ccol1, sizeof(float) * N, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(h->P.xi1, c.xi1, sizeof(float) * N * h->NP, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    DevState st = c.st;
+    st.bar_count = 0;
+    st.converged = 0;
+    st.error = 0;
+    CR_CUDA(h, cudaMemcpyAsync(h->P.st, &st, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+    h->iters = c.iter;
+    return CR_OK;
+}
+
+void ckpt_clear(cr_ctx *h)
+{
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (void *p : h->ckpt_allocs) cudaFree(p);
+    h->ckpt_allocs.clear();
+    h->ckpt.clear();
+}
+
 cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long N, int n, const cr_options *opt,
                       cr_handle *out, int np_override = 0)
 {
@@ -476,6 +583,9 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     P.seed = (unsigned)(o.seed ^ (o.seed >> 32));
     P.bar_timeout_ns = (unsigned long long)(o.barrier_timeout_ms > 0 ? o.barrier_timeout_ms : 4000) * 1000000ull;
     P.bar_extra = o.test_barrier_extra > 0 ? o.test_barrier_extra : 0;
+    h->record_every = o.record_every > 0 ? o.record_every : 0;
+    if (h->record_every > 0 && (o.theta_dtype != CR_THETA_F32 || !h->ks.bwd.pass1))
+        return fail(h, CR_EINVAL, "record_every needs FP32 theta and n <= 10");
 
     const size_t es = theta_elem_size(o.theta_dtype);
     for (int b = 0; b < 2; ++b) {
@@ -634,7 +744,19 @@ cr_status cr_create_device(const float *dX, const float *dybar, int64_t N, int32
 cr_status cr_reset(cr_handle h)
 {
     if (!h) return CR_EINVAL;
+    ckpt_clear(h);
     return init_state(h);
+}
+
+static cr_status run_iters(cr_handle h, long long k)
+{
+    CR_CUDA(h, cudaMemsetAsync(&h->P.st->converged, 0, sizeof(int), h->stream));
+    const long long ell0 = h->iters + 1, ell1 = h->iters + k;
+    const bool pers = h->opt.driver != CR_DRIVER_PHASES && h->persistent_ok;
+    if (pers) CR_TRY(launch_persistent(h, ell0, ell1, 0, -1.0));
+    else CR_TRY(run_phases(h, ell0, ell1, 0, -1.0));
+    h->iters = ell1;
+    return CR_OK;
 }
 
 cr_status cr_iterate(cr_handle h, int64_t k)
@@ -642,12 +764,25 @@ cr_status cr_iterate(cr_handle h, int64_t k)
     CR_TRY(usable(h));
     if (k < 0) return fail(h, CR_EINVAL, "k < 0");
     if (k == 0) return CR_OK;
-    CR_CUDA(h, cudaMemsetAsync(&h->P.st->converged, 0, sizeof(int), h->stream));
-    const long long ell0 = h->iters + 1, ell1 = h->iters + k;
-    const bool pers = h->opt.driver != CR_DRIVER_PHASES && h->persistent_ok;
-    if (pers) CR_TRY(launch_persistent(h, ell0, ell1, 0, -1.0));
-    else CR_TRY(run_phases(h, ell0, ell1, 0, -1.0));
-    h->iters = ell1;
+    if (h->record_every <= 0) return run_iters(h, k);
+    // differentiation: a checkpoint at iteration 0 and after every record_every iterations
+    if (h->ckpt.empty()) {
+        if (h->iters != 0) return fail(h, CR_ESTATE, "recording must start at iteration 0 (cr_reset)");
+        h->ckpt.emplace_back();
+        CR_TRY(ckpt_save(h, h->ckpt.back()));
+    }
+    long long left = k;
+    const long long re = h->record_every;
+    while (left > 0) {
+        const long long nb = (h->iters / re + 1) * re;
+        const long long step = std::min(left, nb - h->iters);
+        CR_TRY(run_iters(h, step));
+        left -= step;
+        if (h->iters % re == 0) {
+            h->ckpt.emplace_back();
+            CR_TRY(ckpt_save(h, h->ckpt.back()));
+        }
+    }
     return CR_OK;
 }
 
@@ -768,6 +903,155 @@ cr_status cr_profile(cr_handle h, int32_t kind, double *ms, int64_t *launches)
     return CR_OK;
 }
 
+cr_status cr_backward(cr_handle h, const float *dL_dyhat, float *dL_dybar, float *dL_dX)
+{
+    CR_TRY(usable(h));
+    if (!dL_dyhat || !dL_dybar || !dL_dX) return fail(h, CR_EINVAL, "NULL buffer");
+    if (h->record_every <= 0 || h->ckpt.empty() || h->opt.theta_dtype != CR_THETA_F32)
+        return fail(h, CR_ESTATE, "cr_backward needs iterations run with record_every > 0 (FP32 theta)");
+    const long long K = h->iters, k = h->record_every, N = h->N, ld = h->ld;
+    const int n = h->n, NP = h->NP, K1 = NP + 1, REC = rec_floats(NP);
+    if ((long long)h->ckpt.size() < (K + k - 1) / k) return fail(h, CR_ESTATE, "missing checkpoints");
+    const size_t thb = (size_t)N * ld * sizeof(float);
+    // workspace
+    auto al = [&](void **p, size_t bytes) {
+        if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
+        h->bwd_allocs.push_back(*p);
+        return true;
+    };
+    for (void *p : h->bwd_allocs) cudaFree(p);
+    h->bwd_allocs.clear();
+    std::vector<float *> segTh(k + 1), segRec(k), segCcol(k), segXi(k);
+    std::vector<double *> segV(k + 2), segMu(k + 2);
+    float *bb[2], *yb2, *ccolb, *xib;
+    double *mub[2], *acc_row, *acc_col, *ybar_acc, *X_acc;
+    bool ok = true;
+    for (long long i = 0; i <= k && ok; ++i) ok = al((void **)&segTh[i], thb);
+    for (long long i = 0; i < k && ok; ++i)
+        ok = al((void **)&segRec[i], sizeof(float) * N * REC) && al((void **)&segCcol[i], sizeof(float) * N) &&
+             al((void **)&segXi[i], sizeof(float) * N * NP);
+    for (long long i = 0; i < k + 2 && ok; ++i)
+        ok = al((void **)&segV[i], sizeof(double) * N) && al((void **)&segMu[i], sizeof(double) * N);
+    ok = ok && al((void **)&bb[0], thb) && al((void **)&bb[1], thb) && al((void **)&mub[0], sizeof(double) * N) &&
+         al((void **)&mub[1], sizeof(double) * N) && al((void **)&acc_row, sizeof(double) * N * K1) &&
+         al((void **)&acc_col, sizeof(double) * N * K1) && al((void **)&ybar_acc, sizeof(double) * N) &&
+         al((void **)&X_acc, sizeof(double) * N * n) && al((void **)&yb2, sizeof(float) * N) &&
+         al((void **)&ccolb, sizeof(float) * N) && al((void **)&xib, sizeof(float) * N * NP);
+    if (!ok) {
+        (void)cudaGetLastError();
+        return fail(h, CR_ENOMEM, "reverse-mode workspace allocation failed");
+    }
+    CR_CUDA(h, cudaMemsetAsync(acc_row, 0, sizeof(double) * N * K1, h->stream));
+    CR_CUDA(h, cudaMemsetAsync(acc_col, 0, sizeof(double) * N * K1, h->stream));
+    CR_CUDA(h, cudaMemsetAsync(ybar_acc, 0, sizeof(double) * N, h->stream));
+    CR_CUDA(h, cudaMemsetAsync(X_acc, 0, sizeof(double) * N * n, h->stream));
+    for (int b = 0; b < 2; ++b) {
+        CR_CUDA(h, cudaMemsetAsync(bb[b], 0, thb, h->stream));
+        CR_CUDA(h, cudaMemsetAsync(mub[b], 0, sizeof(double) * N, h->stream));
+    }
+    // the final forward state, restored at the end
+    cr_ctx::Checkpoint fin;
+    fin.full = true;
+    CR_TRY(ckpt_save(h, fin));
+    std::vector<double> beta(K + 3, 0.0);
+    const int prev_driver = h->opt.driver;
+    const long long S128 = (N + crk::kBCols - 1) / crk::kBCols;
+    const long long ntask = S128 * ((N + crk::kBRows - 1) / crk::kBRows);
+    const int gpass = (int)std::min<long long>(ntask, (long long)h->num_sms * 8);
+    const int gfold = (int)std::max<long long>(1, std::min<long long>((N + 255) / 256, (long long)h->num_sms * 8));
+    const long long nseg = (K + k - 1) / k;
+    cr_status status = CR_OK;
+    for (long long j = nseg - 1; j >= 0 && status == CR_OK; --j) {
+        const long long c = j * k, e = std::min(c + k, K);
+        CR_TRY(ckpt_restore(h, h->ckpt[j]));
+        // segment entry i holds theta1_{c-1+i} (entries 0, 1 from the checkpoint)
+        CR_CUDA(h, cudaMemcpyAsync(segTh[0], h->P.theta[(c + 1) & 1], thb, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(segTh[1], h->P.theta[c & 1], thb, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(segV[0], h->P.v[(c + 1) & 1], sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(segMu[0], h->P.mu[(c + 1) & 1], sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(segV[1], h->P.v[c & 1], sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(segMu[1], h->P.mu[c & 1], sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+        // recompute the segment (bit for bit: same kernels, same partition, same rounding seeds)
+        for (long long ell = c + 1; ell <= e; ++ell) {
+            CR_TRY(run_iters(h, 1));
+            const long long q = ell - c;
+            if (ell < e)
+                CR_CUDA(h, cudaMemcpyAsync(segTh[q + 1], h->P.theta[ell & 1], thb, cudaMemcpyDeviceToDevice, h->stream));
+            CR_CUDA(h, cudaMemcpyAsync(segRec[q - 1], h->P.rowrec, sizeof(float) * N * REC, cudaMemcpyDeviceToDevice, h->stream));
+            CR_CUDA(h, cudaMemcpyAsync(segCcol[q - 1], h->P.ccol2, sizeof(float) * N, cudaMemcpyDeviceToDevice, h->stream));
+            CR_CUDA(h, cudaMemcpyAsync(segXi[q - 1], h->P.xi2, sizeof(float) * N * NP, cudaMemcpyDeviceToDevice, h->stream));
+            CR_CUDA(h, cudaMemcpyAsync(segV[q + 1], h->P.v[ell & 1], sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+            CR_CUDA(h, cudaMemcpyAsync(segMu[q + 1], h->P.mu[ell & 1], sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+            DevState st;
+            CR_TRY(read_state(h, &st));
+            beta[ell] = st.scal[ell & 1].beta;
+        }
+        // reverse the segment
+        for (long long ell = e; ell > c; --ell) {
+            const long long q = ell - c;
+            crk::BwdParams B{};
+            B.N = N;
+            B.ld = ld;
+            B.n = n;
+            B.S128 = (int)S128;
+            B.REC = REC;
+            B.invL = h->P.invL;
+            B.invL_d = h->P.invL_d;
+            B.inv_gamma = h->P.inv_gamma;
+            B.shift = h->P.shift;
+            B.beta = (float)beta[ell];
+            B.beta_d = beta[ell];
+            B.c1_d = ell + 1 <= K ? 1.0 + beta[ell + 1] : 0.0;
+            B.c2_d = ell + 2 <= K ? -beta[ell + 2] : 0.0;
+            B.c1 = (float)B.c1_d;
+            B.c2 = (float)B.c2_d;
+            B.thc = segTh[q];
+            B.thp = segTh[q - 1];
+            B.rowrec = segRec[q - 1];
+            B.ccol2 = segCcol[q - 1];
+            B.xi2 = segXi[q - 1];
+            B.b1 = ell + 1 <= K ? bb[(ell + 1) & 1] : nullptr;
+            B.b2 = ell + 2 <= K ? bb[ell & 1] : nullptr;
+            B.outb = bb[ell & 1];
+            B.mub1 = ell + 1 <= K ? mub[(ell + 1) & 1] : nullptr;
+            B.mub2 = ell + 2 <= K ? mub[ell & 1] : nullptr;
+            B.mub_out = mub[ell & 1];
+            B.ubar = ell == K ? dL_dyhat : nullptr;
+            B.v1 = segV[q];
+            B.v2 = segV[q - 1];
+            B.mu1 = segMu[q];
+            B.mu2 = segMu[q - 1];
+            B.X64 = h->P.X64;
+            B.h = h->P.h;
+            B.acc_row = acc_row;
+            B.acc_col = acc_col;
+            B.ybar_acc = ybar_acc;
+            B.X_acc = X_acc;
+            B.yb2 = yb2;
+            B.ccolb = ccolb;
+            B.xib = xib;
+            B.yb2_out = yb2;
+            B.ccolb_out = ccolb;
+            B.xib_out = xib;
+            void *args[] = {&B};
+            CR_CUDA(h, cudaLaunchKernel(h->ks.bwd.pass1, dim3(gpass), dim3(256), args, 0, h->stream));
+            CR_CUDA(h, cudaLaunchKernel(h->ks.bwd.fold1, dim3(gfold), dim3(256), args, 0, h->stream));
+            CR_CUDA(h, cudaLaunchKernel(h->ks.bwd.pass2, dim3(gpass), dim3(256), args, 0, h->stream));
+            CR_CUDA(h, cudaLaunchKernel(h->ks.bwd.fold2, dim3(gfold), dim3(256), args, 0, h->stream));
+        }
+    }
+    h->opt.driver = prev_driver;
+    {
+        long long NN = N;
+        int nn = n;
+        void *args[] = {&NN, &nn, (void *)&dL_dyhat, &ybar_acc, &X_acc, &dL_dybar, &dL_dX};
+        CR_CUDA(h, cudaLaunchKernel((const void *)crk::k_bwd_finish, dim3(gfold), dim3(256), args, 0, h->stream));
+    }
+    CR_TRY(ckpt_restore(h, fin));
+    CR_CUDA(h, cudaStreamSynchronize(h->stream));
+    return status;
+}
+
 cr_status cr_get_device_state(cr_handle h, const void **dtheta, int64_t *ld, const double **dX, const double **dy,
                               const double **dxi, const double **dmu, double *sigma)
 {
@@ -787,6 +1071,8 @@ void cr_destroy(cr_handle h)
 {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    ckpt_clear(h);
+    for (void *p : h->bwd_allocs) cudaFree(p);
     for (auto &e : h->evs) {
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);

@@ -246,3 +246,32 @@ def test_planted_sign_error_is_caught():
     th = D.theta_vec(T, pairs)
     bad_xi = (-A2.T @ th) / 0.5
     assert np.abs(bad_xi - xi.ravel()).max() > 1e-3
+
+
+# --------------------------------------------------------------------------
+# Forward-mode derivative of K unrolled iterations (differentiation reference)
+# --------------------------------------------------------------------------
+def test_oracle_jvp_matches_central_differences():
+    X, yb, _ = datagen.make("sumexp", N=30, n=3, seed=4)
+    g = 0.1
+    L = O.lipschitz(X, g)
+    s = O.shift(yb)
+    K = 20
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        dy = rng.normal(size=yb.shape)
+        dX = rng.normal(size=X.shape)
+        yh, dyh = O.papg_jvp(X, yb, g, L, s, K, dy, dX)
+        eps = 1e-6
+        yp, _ = O.papg_jvp(X + eps * dX, yb + eps * dy, g, L, s, K, dy, dX)
+        ym, _ = O.papg_jvp(X - eps * dX, yb - eps * dy, g, L, s, K, dy, dX)
+        fd = (yp - ym) / (2 * eps)
+        assert np.abs(fd - dyh).max() <= 1e-7 * np.abs(fd).max()
+    # the primal of the JVP routine is the P-APG iterate of the Solver
+    o = O.Solver(X, yb, gamma=g, L=L, s=s, restart=False)
+    o.iterate(K)
+    np.testing.assert_allclose(yh, o.y_hat, rtol=0, atol=1e-12)
+    # linearity in the direction
+    _, d1 = O.papg_jvp(X, yb, g, L, s, K, dy, dX)
+    _, d2 = O.papg_jvp(X, yb, g, L, s, K, 2.5 * dy, 2.5 * dX)
+    np.testing.assert_allclose(d2, 2.5 * d1, rtol=1e-12, atol=1e-12)
