@@ -97,6 +97,22 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def dist_max(x: float, device=None) -> float:
+    """Max over ranks (the slowest rank's time); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, steps: int, ms_max: float, world: int) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank * steps / (ms_max / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -179,11 +195,7 @@ def run_ours(args):
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier()
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = dist_max(ev0.elapsed_time(ev1), dev)
     pair_ms, pair_n = s.profile(crg.PROFILE_PAIR)
     fold_ms, fold_n = s.profile(crg.PROFILE_FOLD)
     pers_ms, pers_n = s.profile(crg.PROFILE_PERSISTENT)
@@ -194,7 +206,7 @@ def run_ours(args):
 
     pairs = N * (N - 1)
     b = 4 if args.dtype == "f32" else 2
-    value = ws * pairs * args.steps / (ms / 1e3)
+    value = job_value(pairs, args.steps, ms, ws)
     peak, peak_kind = peaks()
     # dominant kernel: the pair pass (phase driver) or the persistent launch
     if pair_n:
@@ -219,18 +231,14 @@ def run_ours(args):
     yout[:] = y_out
     e.close()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = dist_max(time.perf_counter() - t0, dev)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        Ns = 2000
-        rate, dt, cores = oracle_rate(Ns, 8, 1)
+        Ns = 8000
+        rate, dt, cores = oracle_rate(Ns, 60, 1)
         cpu = {"value": rate, "unit": "pair-updates/s", "cores": cores, "kind": "oracle",
-               "sample": f"8 P-APG iterations of the FP64 oracle at N={Ns}, n={n} of the same recipe ({dt:.1f} s)"}
+               "sample": f"60 P-APG iterations of the FP64 oracle at N={Ns}, n={n} of the same recipe ({dt:.1f} s)"}
 
     if rank == 0:
         line = {
@@ -262,6 +270,129 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# the other workloads (one JSON line each; not part of the default run)
+# ---------------------------------------------------------------------------
+def _sync_time(fn):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize()
+    return r, time.perf_counter() - t0
+
+
+def run_sq2(args):
+    """Recipe (1): N=500, n=2, FP32, gamma=0.1: time to FP64-confirmed KKT 1e-6."""
+    import torch
+    import paper_1407_7220_gb300 as crg
+    torch.cuda.set_device(0)
+    X, yb, _ = datagen.make("sq2", N=500)
+    s = crg.Solver(X, yb, gamma=0.1, stochastic_round=1, restart=0, kkt_every=50)
+    s.iterate(3)
+    s.reset()
+    with Clocks(0) as clk:
+        (conv, iters), dt = _sync_time(lambda: s.solve(1e-6, 3_000_000))
+    k = s.kkt_residual()
+    y, _ = s.solution()
+    line = {"metric": "time to KKT 1e-6", "value": dt, "unit": "s", "higher_is_better": False, "n_gpus": 1,
+            "dtype": "f32", "data": "synthetic", "converged": conv, "iterations": iters, "kkt": k["kkt"],
+            "pair_updates_per_s": 500 * 499 * iters / dt, "us_per_iteration": 1e6 * dt / max(iters, 1),
+            "config": {"workload": "sq2 recipe N=500 n=2 gamma=0.1, FP32 theta, stochastic rounding, plain P-APG"},
+            "clocks": clk.summary()}
+    gold = os.path.join(ROOT, "tests", "golden", "sq2_N500_g0.1.npz")
+    if os.path.exists(gold):
+        ref = np.load(gold)
+        line["fit_rel_err_vs_oracle"] = float(np.abs(y - ref["y_hat"]).max() / np.abs(ref["y_hat"]).max())
+        line["oracle_reference_kkt"] = float(ref["kkt"])
+    print(json.dumps(line))
+
+
+def run_lse(args):
+    """Recipe (3): N=100000, n=20; BF16 or FP16 multipliers: pair-updates/s and error vs FP32."""
+    import torch
+    import paper_1407_7220_gb300 as crg
+    torch.cuda.set_device(0)
+    N, n = args.N if args.N != N_DEF else 100000, 20
+    X, yb, _ = datagen.make("lse", N=N, n=n)
+    dt_ = args.dtype if args.dtype != "f32" else "bf16"
+    s = crg.Solver(X, yb, gamma=GAMMA, theta_dtype=dt_, stochastic_round=1, restart=0, driver=2, profile=1)
+    s.iterate(args.warmup)
+    for k in range(4):
+        s.profile(k)
+    with Clocks(0) as clk:
+        _, dt = _sync_time(lambda: s.iterate(args.steps))
+    pair_ms, pair_n = s.profile(crg.PROFILE_PAIR)
+    y16, _ = s.solution()
+    s.close()
+    pairs = N * (N - 1)
+    line = {"metric": "pair-updates/s", "value": pairs * args.steps / dt, "unit": "pair-updates/s",
+            "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "dtype": dt_, "data": "synthetic",
+            "config": {"workload": f"lse recipe N={N} n={n} gamma={GAMMA}, {dt_} theta (2 x {pairs * 2 / 1e9:.0f} GB)"},
+            "roofline": {"bound": "hbm", "achieved": 3 * 2 * pairs / (pair_ms / pair_n / 1e3) / 1e9,
+                         "peak": peaks()[0], "unit": "GB/s"},
+            "clocks": clk.summary()}
+    line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
+    if not args.no_cpu_baseline:
+        # same iterations in FP32 at full size, fitted values compared
+        f = crg.Solver(X, yb, gamma=GAMMA, theta_dtype="f32", stochastic_round=1, restart=0)
+        f.iterate(args.warmup + args.steps)
+        y32, _ = f.solution()
+        f.close()
+        line["fit_rel_err_vs_f32_same_iterations"] = float(np.abs(y16 - y32).max() / np.abs(y32).max())
+    print(json.dumps(line))
+
+
+def run_batch(args):
+    """Recipe (4): 1024 fits of uneven size in one persistent launch: fits/s to KKT 1e-4."""
+    import torch
+    import paper_1407_7220_gb300 as crg
+    torch.cuda.set_device(0)
+    inst = [(X, yb) for X, yb, _ in datagen.make_batch(args.batch)]
+    (bs), t_create = _sync_time(lambda: crg.BatchSolver(inst, gamma=0.1, stochastic_round=1, restart=0, kkt_every=50))
+    info = bs.info()
+    with Clocks(0) as clk:
+        conv, dt = _sync_time(lambda: bs.solve(1e-4, args.batch_iters))
+    its = np.array([bs.member(i).info()["iters"] for i in range(len(inst))])
+    pair_updates = float(sum((X.shape[0] * (X.shape[0] - 1)) * it for (X, _), it in zip(inst, its)))
+    line = {"metric": "fits/s to KKT 1e-4", "value": conv / dt, "unit": "fits/s", "higher_is_better": True,
+            "n_gpus": 1, "dtype": "f32", "data": "synthetic", "fits": len(inst), "converged": conv,
+            "seconds": dt, "create_and_autotune_s": t_create, "granularity_factor": info["factor"],
+            "physical_ctas": info["grid"], "pair_updates_per_s": pair_updates / dt,
+            "iterations": {"median": float(np.median(its)), "p90": float(np.percentile(its, 90)), "max": int(its.max()),
+                           "cap": args.batch_iters},
+            "config": {"workload": f"batch recipe: {len(inst)} fits, N_i log-uniform [64, 4096], n_i in {{1,2,5}}, "
+                                   "gamma=0.1, FP32 theta, plain P-APG"},
+            "clocks": clk.summary()}
+    print(json.dumps(line))
+
+
+def run_sumexp(args):
+    """Recipe (5): N=5000, n=5: 500 unrolled iterations (checkpoint every 50), forward and backward."""
+    import torch
+    import paper_1407_7220_gb300 as crg
+    torch.cuda.set_device(0)
+    X, yb, f0 = datagen.make("sumexp", N=5000, n=5)
+    K, k = 500, 50
+    s = crg.Solver(X, yb, gamma=0.1, stochastic_round=0, restart=0, record_every=k)
+    _, t_fwd = _sync_time(lambda: s.iterate(K))
+    y, _ = s.solution()
+    u = torch.tensor(2.0 * (y - f0), dtype=torch.float32, device="cuda")   # loss ||yhat - f0||^2
+    dyb = torch.empty_like(u)
+    dX = torch.empty((5000, 5), dtype=torch.float32, device="cuda")
+    _, t_bwd = _sync_time(lambda: s.backward(u, dyb, dX))
+    pairs = 5000 * 4999
+    line = {"metric": "forward + backward time, 500 unrolled iterations", "value": t_fwd + t_bwd, "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "forward_s": t_fwd, "backward_s": t_bwd, "backward_over_forward": t_bwd / t_fwd,
+            "forward_pair_updates_per_s": pairs * K / t_fwd,
+            "grad_norms": {"dybar": float(dyb.norm()), "dX": float(dX.norm())},
+            "config": {"workload": "sumexp recipe N=5000 n=5 gamma=0.1, FP32 theta, checkpoint every 50, "
+                                   "loss ||yhat - f0||^2"}}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,10 +404,16 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--driver", type=int, default=2, help="1 persistent, 2 phase kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", default="maxaff", choices=["maxaff", "sq2", "lse", "batch", "sumexp"],
+                    help="workload (default: the headline workload, recipe (2))")
+    ap.add_argument("--batch", type=int, default=1024)
+    ap.add_argument("--batch-iters", type=int, default=20000)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
+    if args.config != "maxaff":
+        return {"sq2": run_sq2, "lse": run_lse, "batch": run_batch, "sumexp": run_sumexp}[args.config](args)
     return run_ours(args)
 
 

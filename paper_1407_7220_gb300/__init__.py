@@ -347,3 +347,34 @@ class BatchSolver:
             self.close()
         except Exception:
             pass
+
+
+def convex_fit(X, ybar, iters: int, record_every: int = 50, **opts):
+    """Differentiable fitted values: yhat = P-APG(X, ybar) after ``iters`` iterations.
+
+    X (N, n) and ybar (N,) are CUDA tensors; the result is a CUDA tensor of ybar's dtype.
+    Backward runs ``cr_backward`` (reverse mode through the unrolled iterations, checkpoint
+    every ``record_every``), giving dLoss/dX and dLoss/dybar.  gamma, L and the shift are
+    held fixed; plain P-APG (restart = 0).  Extra keyword arguments are ``cr_options``."""
+    import torch
+
+    class _ConvexFit(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, X_, y_):
+            s = Solver(X_.detach(), y_.detach(), record_every=int(record_every), restart=0, **opts)
+            s.iterate(int(iters))
+            yhat, _ = s.solution()
+            ctx.solver = s
+            ctx.meta = (X_.shape, X_.dtype, y_.dtype)
+            return torch.as_tensor(yhat, device=y_.device).to(y_.dtype)
+
+        @staticmethod
+        def backward(ctx, gy):
+            shape, xdt, ydt = ctx.meta
+            u = gy.detach().contiguous().to(torch.float32)
+            dyb = torch.empty_like(u)
+            dX = torch.empty(tuple(shape), dtype=torch.float32, device=u.device)
+            ctx.solver.backward(u, dyb, dX)
+            return dX.to(xdt), dyb.to(ydt)
+
+    return _ConvexFit.apply(X, ybar)

@@ -57,3 +57,29 @@ def test_backward_independent_of_checkpoint_spacing_and_linear():
     _, d_y, d_X = _vjp(crg, X, yb, 36, 5, 2.0 * u1 - 3.0 * u2)
     np.testing.assert_allclose(d_y, 2.0 * b_y - 3.0 * c_y, rtol=0, atol=1e-4 * np.abs(d_y).max())
     np.testing.assert_allclose(d_X, 2.0 * b_X - 3.0 * c_X, rtol=0, atol=1e-4 * np.abs(d_X).max())
+
+
+def test_autograd_function_gradient_matches_oracle():
+    import torch
+    import paper_1407_7220_gb300 as crg
+    X, yb, f0 = datagen.make("sumexp", N=150, n=5, seed=7)
+    Xt = torch.tensor(X, dtype=torch.float32, device="cuda", requires_grad=True)
+    yt = torch.tensor(yb, dtype=torch.float32, device="cuda", requires_grad=True)
+    K = 30
+    yhat = crg.convex_fit(Xt, yt, iters=K, record_every=10, gamma=0.1, stochastic_round=0)
+    target = torch.tensor(f0, dtype=torch.float32, device="cuda")
+    loss = ((yhat - target) ** 2).sum()          # the differentiation workload's loss
+    loss.backward()
+    # the solver works on the FP32-rounded inputs; compare with the oracle on the same data
+    Xr = Xt.detach().double().cpu().numpy()
+    yr = yt.detach().double().cpu().numpy()
+    s = crg.Solver(Xr, yr, gamma=0.1)
+    info = s.info()
+    rng = np.random.default_rng(11)
+    for _ in range(4):
+        dy = rng.normal(size=yb.shape)
+        dX = rng.normal(size=X.shape)
+        yo, jv = O.papg_jvp(Xr, yr, 0.1, info["L"], info["shift"], K, dy, dX)
+        want = float(2.0 * (yo - f0) @ jv)
+        got = float((yt.grad.double().cpu().numpy() * dy).sum() + (Xt.grad.double().cpu().numpy() * dX).sum())
+        assert abs(got - want) <= 2e-3 * abs(want) + 1e-6, (got, want)
