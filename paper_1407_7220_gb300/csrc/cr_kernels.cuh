@@ -34,7 +34,10 @@ constexpr int kThreads = 256;   // 8 warps per CTA
 constexpr int kCons = kThreads; // every warp consumes pair-pass stages; lane 0 of warp 0 also produces them
 constexpr int kW = 256;         // stripe width (columns)
 constexpr int kWR = 4;          // row groups of consumer warps (2 warps per row)
-constexpr int kRS = 8;          // rows per pipeline stage
+constexpr int kRS = 16;         // rows per pipeline stage
+constexpr int kRPW = kRS / kWR; // rows of a stage per consumer warp
+constexpr int kSB = 8 / kRPW;   // stages per row-sum batch (8 row sums per warp)
+static_assert(kRS % kWR == 0 && 8 % kRPW == 0, "row split of a stage");
 constexpr int kMaxStages = 16;
 constexpr size_t kSmemBudget = 227 * 1024 - 2048;   // dynamic shared memory per CTA (static arrays excluded)
 
@@ -100,7 +103,7 @@ struct Params {
     double *mu[2];          // multipliers of the y >= 0 rows (N)
     float *rowpart;         // [N][Q]: row sums per (stripe, column half), Q = ceil4(2S), padding 0
     int Q;
-    float *colpart;         // [G][slots][NP+1][kW]
+    float *colpart;         // [G][slots][kWR][NP+1][kW]: column partials per CTA, stripe slot and row group
     double *foldpart;       // [G][8]
     double *kktpart;        // [G][8]
     DevState *st;
@@ -111,17 +114,64 @@ struct Params {
 // ---------------------------------------------------------------------------
 template <typename TS> struct Store;
 
-__device__ __forceinline__ uint32_t hash3(uint32_t a, uint32_t b, uint32_t c)
+// Counter-based generator: a multiply-xor mix of the counters (a, b, c) followed by the
+// "lowbias32" integer finalizer (C. Wellons' hash-prospector).  hash_col carries the
+// (b, c) part so that a loop over a with fixed (b, c) pays for it once.
+__device__ __forceinline__ uint32_t hash_col(uint32_t b, uint32_t c)
 {
-    // counter-based: a multiply-xor mix of the counters followed by the
-    // "lowbias32" integer finalizer (C. Wellons' hash-prospector)
-    uint32_t x = a * 0x9E3779B1u ^ (b * 0x85EBCA77u + 0x165667B1u) ^ (c * 0xC2B2AE3Du + 0x27D4EB2Fu);
+    return (b * 0x85EBCA77u + 0x165667B1u) ^ (c * 0xC2B2AE3Du + 0x27D4EB2Fu);
+}
+__device__ __forceinline__ uint32_t hash_row(uint32_t hcol, uint32_t a)
+{
+    uint32_t x = a * 0x9E3779B1u ^ hcol;
     x ^= x >> 16;
     x *= 0x7feb352du;
     x ^= x >> 15;
     x *= 0x846ca68bu;
     x ^= x >> 16;
     return x;
+}
+
+// Packed FP32 pairs (the f32x2 arithmetic of sm_100 and later): one instruction performs
+// two IEEE single-precision operations, each half rounded exactly as the scalar one, so a
+// packed expression gives the same bits as the scalar expression in the same order.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_make(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_split(f2 v, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_add_rm(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
 }
 
 template <> struct Store<float> {
@@ -152,6 +202,47 @@ template <> struct Store<float> {
     __device__ static __forceinline__ float encode(float v, float) { return v; }
     __device__ static __forceinline__ Vec pack(const float (&s)[4]) { return make_float4(s[0], s[1], s[2], s[3]); }
     __device__ static __forceinline__ float decoded(float s, float) { return s; }
+
+    // --- packed forms used by the pair pass (two adjacent columns per f2) ---
+    __device__ static __forceinline__ void unpack2(const float *p, f2 (&o)[2], float)
+    {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(p);
+        o[0] = t.x;
+        o[1] = t.y;
+    }
+    // round<SR> on both halves; rnd holds the two 16-bit uniforms (low half -> low column).
+    // floor(e/ulp + 1 + u) is taken exactly as the integer part of RD(t + 1.5*2^23).
+    template <bool SR>
+    __device__ static __forceinline__ f2 round2(f2 th2, f2 g, f2 ninvL2, float, uint32_t rnd, float)
+    {
+        const f2 v = f2_fma(g, ninvL2, th2);
+        float v0, v1;
+        f2_split(v, v0, v1);
+        float r0 = v0, r1 = v1;
+        if (SR) {
+            const f2 e = f2_fma(g, ninvL2, f2_sub(th2, v));
+            const uint32_t b0 = __float_as_uint(v0), b1 = __float_as_uint(v1);
+            const float iu0 = __uint_as_float(0x8A800000u - max(b0 & 0x7F800000u, 23u << 23));
+            const float iu1 = __uint_as_float(0x8A800000u - max(b1 & 0x7F800000u, 23u << 23));
+            const float u0 = __uint_as_float(0x3F800000u | ((rnd << 7) & 0x007FFF80u));
+            const float u1 = __uint_as_float(0x3F800000u | ((rnd >> 9) & 0x007FFF80u));
+            const f2 t = f2_fma(e, f2_make(iu0, iu1), f2_make(u0, u1));
+            const f2 fl = f2_add_rm(t, f2_make(12582912.0f, 12582912.0f));
+            float fl0, fl1;
+            f2_split(fl, fl0, fl1);
+            r0 = __uint_as_float(b0 + __float_as_uint(fl0) - 0x4B400001u);
+            r1 = __uint_as_float(b1 + __float_as_uint(fl1) - 0x4B400001u);
+        }
+        return f2_make(v0 > 0.0f ? r0 : 0.0f, v1 > 0.0f ? r1 : 0.0f);
+    }
+    __device__ static __forceinline__ Vec pack2(const f2 (&s)[2])
+    {
+        Vec v;
+        f2_split(s[0], v.x, v.y);
+        f2_split(s[1], v.z, v.w);
+        return v;
+    }
+    __device__ static __forceinline__ f2 decoded2(f2 s, f2) { return s; }
 };
 
 template <> struct Store<__nv_bfloat16> {
@@ -181,6 +272,29 @@ template <> struct Store<__nv_bfloat16> {
         return v;
     }
     __device__ static __forceinline__ float decoded(float s, float) { return s; }
+
+    __device__ static __forceinline__ void unpack2(const __nv_bfloat16 *p, f2 (&o)[2], float)
+    {
+        const uint2 t = *reinterpret_cast<const uint2 *>(p);
+        o[0] = f2_make(b2f(t.x & 0xFFFFu), b2f(t.x >> 16));
+        o[1] = f2_make(b2f(t.y & 0xFFFFu), b2f(t.y >> 16));
+    }
+    template <bool SR>
+    __device__ static __forceinline__ f2 round2(f2 th2, f2 g, f2, float invL, uint32_t rnd, float scl)
+    {
+        float t0, t1, g0, g1;
+        f2_split(th2, t0, t1);
+        f2_split(g, g0, g1);
+        return f2_make(round<SR>(t0, g0, invL, rnd & 0xFFFFu, scl), round<SR>(t1, g1, invL, rnd >> 16, scl));
+    }
+    __device__ static __forceinline__ Vec pack2(const f2 (&s)[2])
+    {
+        float a[4];
+        f2_split(s[0], a[0], a[1]);
+        f2_split(s[1], a[2], a[3]);
+        return pack(a);
+    }
+    __device__ static __forceinline__ f2 decoded2(f2 s, f2) { return s; }
 };
 
 template <> struct Store<__half> {
@@ -219,6 +333,29 @@ template <> struct Store<__half> {
         return v;
     }
     __device__ static __forceinline__ float decoded(float s, float inv_scale) { return s * inv_scale; }
+
+    __device__ static __forceinline__ void unpack2(const __half *p, f2 (&o)[2], float inv_scale)
+    {
+        const uint2 t = *reinterpret_cast<const uint2 *>(p);
+        o[0] = f2_make(h2f(t.x & 0xFFFFu, inv_scale), h2f(t.x >> 16, inv_scale));
+        o[1] = f2_make(h2f(t.y & 0xFFFFu, inv_scale), h2f(t.y >> 16, inv_scale));
+    }
+    template <bool SR>
+    __device__ static __forceinline__ f2 round2(f2 th2, f2 g, f2, float invL, uint32_t rnd, float scl)
+    {
+        float t0, t1, g0, g1;
+        f2_split(th2, t0, t1);
+        f2_split(g, g0, g1);
+        return f2_make(round<SR>(t0, g0, invL, rnd & 0xFFFFu, scl), round<SR>(t1, g1, invL, rnd >> 16, scl));
+    }
+    __device__ static __forceinline__ Vec pack2(const f2 (&s)[2])
+    {
+        float a[4];
+        f2_split(s[0], a[0], a[1]);
+        f2_split(s[1], a[2], a[3]);
+        return pack(a);
+    }
+    __device__ static __forceinline__ f2 decoded2(f2 s, f2 iscl2) { return f2_mul(s, iscl2); }
 };
 
 // ---------------------------------------------------------------------------
@@ -478,31 +615,35 @@ template <typename TS, int NP> struct PairSmem {
     static constexpr size_t tile_bytes = (size_t)kRS * kW * sizeof(TS);
     static constexpr size_t rec_bytes = (size_t)kRS * REC * sizeof(float);
     static constexpr size_t stage_bytes = 2 * tile_bytes + rec_bytes;
-    static constexpr size_t flush_bytes = (size_t)kWR * (NP + 1) * kW * sizeof(float);
-    // as many stages as fit next to the column-partial buffer (more bytes in flight per SM)
-    static constexpr int kFit = (int)((kSmemBudget - flush_bytes - 128) / stage_bytes);
+    // as many stages as fit (more bytes in flight per SM)
+    static constexpr int kFit = (int)((kSmemBudget - 128) / stage_bytes);
     static constexpr int kStages = kFit < kMaxStages ? kFit : kMaxStages;
     static_assert(kStages >= 2, "pipeline needs at least two stages");
-    static constexpr size_t bytes = kStages * stage_bytes + flush_bytes + 128;   // + base alignment slack
+    static constexpr size_t bytes = kStages * stage_bytes + 128;   // + base alignment slack
     static_assert(tile_bytes % 128 == 0 && rec_bytes % 128 == 0, "stage buffers must stay 128-byte aligned");
 };
 
-// The two rows (rg, rg + 4) of one pipeline stage for one consumer warp, 4 columns per
-// lane.  MASK handles the diagonal (l1 == l2), columns >= N and rows past the segment;
-// stages without any of these take the unmasked instantiation.  SR: stochastic rounding.
+// The kRPW rows (rg, rg + kWR, ...) of one pipeline stage for one consumer warp, 4 columns per
+// lane held as two f32x2 column pairs.  MASK handles the diagonal (l1 == l2), columns >= N
+// and rows past the segment; stages without any of these take the unmasked instantiation.
+// SR: stochastic rounding.  nxi = -xi of the lane's columns; ninvL2 = (-1/L, -1/L).
+// The arithmetic of every pair is the scalar expression order of Step 2 (two chains of the
+// xi.x product, even and odd k), so the residual and the projection mask are reproducible
+// by a scalar evaluation.
 template <typename TS, int NP, bool MASK, bool SR>
 __device__ __forceinline__ void pair_stage_rows(const TS *tcur, const TS *tprv, const float *rec, int rg, int cofs,
                                                 long long r, long long r1, long long col0, long long N, long long ld,
-                                                const float (&ccol)[4], const float (&xi)[4][NP], float (&acc)[4][NP],
-                                                float (&csum)[4], float beta, float invL, uint32_t rseed, float scl,
-                                                float iscl, TS *__restrict__ nxt, bool vec_ok, float &rs0, float &rs1)
+                                                const f2 (&ccol)[2], const f2 (&nxi)[2][NP], f2 (&acc)[2][NP],
+                                                f2 (&csum)[2], f2 beta2, f2 ninvL2, float invL, uint32_t hcol,
+                                                float scl, float iscl, f2 iscl2, TS *__restrict__ nxt, bool vec_ok,
+                                                float (&rsv)[kRPW])
 {
     using St = Store<TS>;
     using Vec = typename St::Vec;
     constexpr int REC = RecLayout<NP>::REC;
-    float rsv[2];
+    const f2 zero2 = 0ull;
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kRPW; ++i) {
         const int rl = rg + i * kWR;
         const long long rr = r + rl;
         const bool valid = !MASK || rr < r1;
@@ -512,48 +653,56 @@ __device__ __forceinline__ void pair_stage_rows(const TS *tcur, const TS *tprv, 
             const float4 t4 = *reinterpret_cast<const float4 *>(rec + rl * REC + q);
             rv[q] = t4.x; rv[q + 1] = t4.y; rv[q + 2] = t4.z; rv[q + 3] = t4.w;
         }
-        float tc[4], tp[4], outv[4];
-        St::unpack(*reinterpret_cast<const Vec *>(tcur + rl * kW + cofs), tc, iscl);
-        St::unpack(*reinterpret_cast<const Vec *>(tprv + rl * kW + cofs), tp, iscl);
-        uint32_t h = 0, h2 = 0;
-        if (SR) {
-            h = hash3((uint32_t)rr, (uint32_t)(col0 >> 2), rseed);
-            h2 = (h ^ (h >> 15)) * 0x2C1B3C6Du;
-        }
-        const uint32_t rnd[4] = {h & 0xFFFFu, h >> 16, h2 & 0xFFFFu, h2 >> 16};
-        float rs = 0.0f;
+        f2 xb[NP];   // (x_k, x_k) of this row
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float th2 = fmaf(beta, tc[j] - tp[j], tc[j]);  // theta^(2) = theta^(1) + beta (theta^(1) - prev)
+        for (int k = 0; k < NP; ++k) xb[k] = f2_make(rv[1 + k], rv[1 + k]);
+        const f2 yb = f2_make(rv[0], rv[0]);
+        f2 tc[2], tp[2], outv[2];
+        St::unpack2(tcur + rl * kW + cofs, tc, iscl);
+        St::unpack2(tprv + rl * kW + cofs, tp, iscl);
+        uint32_t hP[2] = {0u, 0u};
+        if (SR) {
+            hP[0] = hash_row(hcol, (uint32_t)rr);
+            hP[1] = (hP[0] ^ (hP[0] >> 15)) * 0x2C1B3C6Du;
+        }
+        f2 rs2 = zero2;
+#pragma unroll
+        for (int P = 0; P < 2; ++P) {
+            const f2 th2 = f2_fma(beta2, f2_sub(tc[P], tp[P]), tc[P]);   // theta^(2) = theta^(1) + beta (theta^(1) - prev)
             // (C eta)_p = y_l1 - y_l2 + xi_l2.x_l2 - xi_l2.x_l1, summed in two chains
-            float g0 = rv[0] + ccol[j], g1 = 0.0f;
+            f2 g0 = f2_add(yb, ccol[P]), g1 = zero2;
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
-                if (k & 1) g1 = fmaf(-xi[j][k], rv[1 + k], g1);
-                else g0 = fmaf(-xi[j][k], rv[1 + k], g0);
+                if (k & 1) g1 = f2_fma(nxi[P][k], xb[k], g1);
+                else g0 = f2_fma(nxi[P][k], xb[k], g0);
             }
-            float sv = St::template round<SR>(th2, g0 + g1, invL, rnd[j], scl);   // Pi_{>=0}(theta^(2) - g/L)
+            f2 sv = St::template round2<SR>(th2, f2_add(g0, g1), ninvL2, invL, hP[P], scl);   // Pi_{>=0}(theta^(2) - g/L)
             if (MASK) {
-                if (!valid || col0 + j >= N || col0 + j == rr) sv = 0.0f;
+                float s0, s1;
+                f2_split(sv, s0, s1);
+                const long long c = col0 + 2 * P;
+                if (!valid || c >= N || c == rr) s0 = 0.0f;
+                if (!valid || c + 1 >= N || c + 1 == rr) s1 = 0.0f;
+                sv = f2_make(s0, s1);
             }
-            outv[j] = sv;
-            const float vv = St::decoded(sv, iscl);
-            rs += vv;                                                // row sum    (A_1^T, + part)
-            csum[j] += vv;                                           // column sum (A_1^T, - part)
+            outv[P] = sv;
+            const f2 vv = St::decoded2(sv, iscl2);
+            rs2 = f2_add(rs2, vv);                                          // row sum    (A_1^T, + part)
+            csum[P] = f2_add(csum[P], vv);                                  // column sum (A_1^T, - part)
 #pragma unroll
-            for (int k = 0; k < NP; ++k) acc[j][k] = fmaf(vv, rv[1 + k], acc[j][k]);   // theta^T X (A_2^T)
+            for (int k = 0; k < NP; ++k) acc[P][k] = f2_fma(vv, xb[k], acc[P][k]);   // theta^T X (A_2^T)
         }
-        if (vec_ok && valid) *reinterpret_cast<Vec *>(nxt + rr * ld + col0) = St::pack(outv);
-        rsv[i] = rs;
+        if (vec_ok && valid) *reinterpret_cast<Vec *>(nxt + rr * ld + col0) = St::pack2(outv);
+        float a, b;
+        f2_split(rs2, a, b);
+        rsv[i] = a + b;
     }
-    rs0 = rsv[0];
-    rs1 = rsv[1];
 }
 
-// Row sums of a batch of up to 4 stages (8 rows per warp) reduced across the warp with a
+// Row sums of a batch of up to kSB stages (8 rows per warp) reduced across the warp with a
 // transposing butterfly: 9 shuffles leave the full sum of batch entry
 // e = 4*bit4 + 2*bit3 + bit2 (of the lane id) in every lane.  Entry e is row
-// r_last - kRS*(3 - e/2) + rg + kWR*(e & 1); only the nb most recent stages are written.
+// r_last - kRS*(kSB - 1 - e/kRPW) + rg + kWR*(e % kRPW); only the nb most recent stages are written.
 __device__ __forceinline__ void flush_row_sums(float (&v)[8], int nb, long long r_last, int rg, long long r1,
                                                float *rp, int Q, int lane)
 {
@@ -579,9 +728,9 @@ __device__ __forceinline__ void flush_row_sums(float (&v)[8], int nb, long long 
     v[0] += __shfl_xor_sync(full, v[0], 1);
     if ((lane & 3) == 0) {
         const int e = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-        const int sp = e >> 1;
-        const long long row = r_last - (long long)kRS * (3 - sp) + rg + kWR * (e & 1);
-        if (sp >= 4 - nb && row < r1) rp[row * Q] = v[0];
+        const int sp = e / kRPW;
+        const long long row = r_last - (long long)kRS * (kSB - 1 - sp) + rg + kWR * (e % kRPW);
+        if (sp >= kSB - nb && row < r1) rp[row * Q] = v[0];
     }
 }
 
@@ -613,18 +762,36 @@ struct StageCursor {
     }
 };
 
-// Issue stage number k (global count) into its ring slot: wait until the slot's previous
-// occupant (stage k - S) was released by all 8 warps, then two tiled TMA loads and one
-// bulk copy complete on the slot's "full" barrier.
+// Position of stage k in the ring of S slots: slot = k mod S and the parity of k / S,
+// advanced one stage at a time without a division.
+template <int S> struct RingPos {
+    int slot;
+    uint32_t phase;
+    __device__ __forceinline__ void init(unsigned long long k)
+    {
+        slot = (int)(k % S);
+        phase = (uint32_t)((k / S) & 1);
+    }
+    __device__ __forceinline__ void next()
+    {
+        if (++slot == S) {
+            slot = 0;
+            phase ^= 1u;
+        }
+    }
+};
+
+// Issue the stage at ring position pos: unless this is the slot's first use (reuse false),
+// wait until its previous occupant (S stages earlier) was released by all 8 warps, then
+// two tiled TMA loads and one bulk copy complete on the slot's "full" barrier.
 template <typename TS, int NP>
 __device__ __forceinline__ bool produce_stage(const Params &P, unsigned char *stage0, uint64_t *full, uint64_t *empty,
-                                              unsigned long long k, const StageCursor &cur, int c, int p)
+                                              const RingPos<PairSmem<TS, NP>::kStages> &pos, bool reuse,
+                                              const StageCursor &cur, int c, int p)
 {
     using L = PairSmem<TS, NP>;
-    constexpr int S = L::kStages;
-    const int slot = (int)(k % S);
-    const unsigned long long round = k / S;
-    if (round > 0 && !mbar_wait(P, &empty[slot], (uint32_t)((round - 1) & 1))) return false;
+    const int slot = pos.slot;
+    if (reuse && !mbar_wait(P, &empty[slot], pos.phase ^ 1u)) return false;
     const int nrows = (int)min((long long)kRS, cur.r1 - cur.r);
     unsigned char *st = stage0 + slot * L::stage_bytes;
     mbar_arrive_expect_tx(&full[slot], (uint32_t)(2 * L::tile_bytes + (size_t)nrows * L::REC * 4));
@@ -647,7 +814,6 @@ __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, 
     const long long ubeg = unit_begin(P, vc);
     const long long uend = unit_begin(P, vc + 1);
     unsigned char *stage0 = smem;
-    float *flush = reinterpret_cast<float *>(smem + S * L::stage_bytes);
 
     // number of stages of this pass (identical in every thread)
     unsigned long long nst = 0;
@@ -662,13 +828,16 @@ __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, 
     const bool producer = (tid == 0);
     StageCursor pc;
     unsigned long long kprod = kstage;
+    RingPos<S> ppos;
     bool pok = true;
     if (producer) {
         fence_proxy_async();
         pc.begin(ubeg, uend, N);
+        ppos.init(kprod);
         for (; kprod < kend && kprod < kstage + S && pok; ++kprod) {
-            pok = produce_stage<TS, NP>(P, stage0, full, empty, kprod, pc, c, p);
+            pok = produce_stage<TS, NP>(P, stage0, full, empty, ppos, kprod >= (unsigned long long)S, pc, c, p);
             pc.advance(N);
+            ppos.next();
         }
     }
     __syncwarp();
@@ -677,11 +846,13 @@ __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, 
     const float beta = (float)__ldcg(&P.st->scal[p].beta);
     const float invL = P.invL;
     const float scl = P.st_scale, iscl = P.st_inv_scale;
+    const f2 beta2 = f2_make(beta, beta), ninvL2 = f2_make(-invL, -invL), iscl2 = f2_make(iscl, iscl);
     const bool sr = P.sr != 0;
     const uint32_t rseed = P.seed ^ (uint32_t)ell * 0x632BE5ABu;
     TS *__restrict__ nxt = (TS *)P.theta[p];   // theta^(1)_{l-2} on entry, theta^(1)_l on exit
     const long long first_stripe = ubeg / N;
-    unsigned long long k = kstage;
+    RingPos<S> cpos;
+    cpos.init(kstage);
     bool ok = true;
     for (long long u = ubeg; u < uend;) {
         const long long s = u / N, r0 = u - s * N, r1 = min(N, r0 + (uend - u));
@@ -689,32 +860,36 @@ __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, 
         const long long col0 = colw + lane * 4;
         const bool vec_ok = col0 < ld;
         const bool ragged = (s * kW + kW) > N;
-        float ccol[4], xi[4][NP];
+        f2 ccol[2], nxi[2][NP];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const long long cj = col0 + j;
-            const bool v = cj < N;
-            ccol[j] = v ? __ldcg(P.ccol2 + cj) : 0.0f;
+        for (int P2 = 0; P2 < 2; ++P2) {
+            const long long ca = col0 + 2 * P2, cb = ca + 1;
+            const bool va = ca < N, vb = cb < N;
+            ccol[P2] = f2_make(va ? __ldcg(P.ccol2 + ca) : 0.0f, vb ? __ldcg(P.ccol2 + cb) : 0.0f);
 #pragma unroll
-            for (int q = 0; q < NP; ++q) xi[j][q] = v ? __ldcg(P.xi2 + cj * NP + q) : 0.0f;
+            for (int q = 0; q < NP; ++q)
+                nxi[P2][q] = f2_make(va ? -__ldcg(P.xi2 + ca * NP + q) : 0.0f, vb ? -__ldcg(P.xi2 + cb * NP + q) : 0.0f);
         }
-        float acc[4][NP], csum[4];
+        f2 acc[2][NP], csum[2];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            csum[j] = 0.0f;
+        for (int P2 = 0; P2 < 2; ++P2) {
+            csum[P2] = 0ull;
 #pragma unroll
-            for (int q = 0; q < NP; ++q) acc[j][q] = 0.0f;
+            for (int q = 0; q < NP; ++q) acc[P2][q] = 0ull;
         }
+        const uint32_t hcol = hash_col((uint32_t)(col0 >> 2), rseed);
         float *rp = P.rowpart + (s * 2 + wc);   // row r's partial at rp[r * Q]
         const int cofs = wc * 128 + lane * 4;
         float rsb[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) rsb[q] = 0.0f;
         int nb = 0;
-        for (long long r = r0; r < r1; r += kRS, ++k) {
-            const int slot = (int)(k % S);
-            if (ok && !mbar_wait(P, &full[slot], (uint32_t)((k / S) & 1))) ok = false;
-            float ra = 0.0f, rb = 0.0f;
+        for (long long r = r0; r < r1; r += kRS, cpos.next()) {
+            const int slot = cpos.slot;
+            if (ok && !mbar_wait(P, &full[slot], cpos.phase)) ok = false;
+            float rsn[kRPW];
+#pragma unroll
+            for (int i = 0; i < kRPW; ++i) rsn[i] = 0.0f;
             if (ok) {
                 const unsigned char *st = stage0 + slot * L::stage_bytes;
                 const TS *tcur = reinterpret_cast<const TS *>(st);
@@ -723,63 +898,44 @@ __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, 
                 const bool fast = !ragged && (r + kRS <= r1) && !(r < colw + 128 && colw < r + kRS);
                 if (sr) {
                     if (fast)
-                        pair_stage_rows<TS, NP, false, true>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, xi,
-                                                             acc, csum, beta, invL, rseed, scl, iscl, nxt, vec_ok,
-                                                             ra, rb);
+                        pair_stage_rows<TS, NP, false, true>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn);
                     else
-                        pair_stage_rows<TS, NP, true, true>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, xi,
-                                                            acc, csum, beta, invL, rseed, scl, iscl, nxt, vec_ok,
-                                                            ra, rb);
+                        pair_stage_rows<TS, NP, true, true>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn);
                 } else {
                     if (fast)
-                        pair_stage_rows<TS, NP, false, false>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol,
-                                                              xi, acc, csum, beta, invL, rseed, scl, iscl, nxt,
-                                                              vec_ok, ra, rb);
+                        pair_stage_rows<TS, NP, false, false>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn);
                     else
-                        pair_stage_rows<TS, NP, true, false>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol,
-                                                             xi, acc, csum, beta, invL, rseed, scl, iscl, nxt,
-                                                             vec_ok, ra, rb);
+                        pair_stage_rows<TS, NP, true, false>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn);
                 }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[slot]);
-            if (producer && pok && kprod < kend) {   // refill this slot with stage k + S
-                pok = produce_stage<TS, NP>(P, stage0, full, empty, kprod, pc, c, p);
+            if (producer && pok && kprod < kend) {   // refill this slot with the stage S ahead
+                pok = produce_stage<TS, NP>(P, stage0, full, empty, ppos, kprod >= (unsigned long long)S, pc, c, p);
                 pc.advance(N);
+                ppos.next();
                 ++kprod;
             }
             __syncwarp();   // reconverge warp 0 after the producer lane
-            // shift the row-sum batch (most recent stage in entries 6, 7)
+            // shift the row-sum batch (most recent stage in the last kRPW entries)
 #pragma unroll
-            for (int q = 0; q < 6; ++q) rsb[q] = rsb[q + 2];
-            rsb[6] = ra;
-            rsb[7] = rb;
+            for (int q = 0; q < 8 - kRPW; ++q) rsb[q] = rsb[q + kRPW];
+#pragma unroll
+            for (int i = 0; i < kRPW; ++i) rsb[8 - kRPW + i] = rsn[i];
             ++nb;
-            if (nb == 4 || r + kRS >= r1) {
+            if (nb == kSB || r + kRS >= r1) {
                 flush_row_sums(rsb, nb, r, rg, r1, rp, P.Q, lane);
 #pragma unroll
                 for (int q = 0; q < 8; ++q) rsb[q] = 0.0f;
                 nb = 0;
             }
         }
-        // column partials of this segment: reduce the 4 row groups in shared memory
+        // column partials of this segment, one block per row group (summed in FP64 by foldA)
         const int slotc = (int)(s - first_stripe);
-        float *cp = P.colpart + (vc * P.slots + slotc) * (NP + 1) * kW;
-        const int cl = wc * 128 + lane * 4;
-        named_barrier_sync(1, kCons);
-        *reinterpret_cast<float4 *>(flush + (rg * (NP + 1)) * kW + cl) = make_float4(csum[0], csum[1], csum[2], csum[3]);
+        float *cp = P.colpart + (((vc * P.slots + slotc) * kWR + rg) * (NP + 1)) * kW + wc * 128 + lane * 4;
+        *reinterpret_cast<ulonglong2 *>(cp) = make_ulonglong2(csum[0], csum[1]);
 #pragma unroll
-        for (int q = 0; q < NP; ++q)
-            *reinterpret_cast<float4 *>(flush + (rg * (NP + 1) + 1 + q) * kW + cl) =
-                make_float4(acc[0][q], acc[1][q], acc[2][q], acc[3][q]);
-        named_barrier_sync(1, kCons);
-        for (int e = tid; e < (NP + 1) * kW; e += kCons) {
-            float a = flush[e];
-#pragma unroll
-            for (int q = 1; q < kWR; ++q) a += flush[q * (NP + 1) * kW + e];
-            cp[e] = a;
-        }
-        named_barrier_sync(1, kCons);
+        for (int q = 0; q < NP; ++q) *reinterpret_cast<ulonglong2 *>(cp + (1 + q) * kW) = make_ulonglong2(acc[0][q], acc[1][q]);
         u += r1 - r0;
     }
     kstage += nst;
@@ -820,10 +976,14 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red, long lo
             const long long unx = unit_begin(P, cta + 1);
             if (unx > ubg) {
                 const long long fs = ubg / N;
-                const float *cp = P.colpart + ((cta * P.slots + (s - fs)) * (NP + 1)) * kW + cl;
-                Cc += (double)__ldcg(cp);
+                const float *cp0 = P.colpart + ((cta * P.slots + (s - fs)) * kWR * (NP + 1)) * kW + cl;
 #pragma unroll
-                for (int k = 0; k < NP; ++k) TX[k] += (double)__ldcg(cp + (1 + k) * kW);
+                for (int g = 0; g < kWR; ++g) {
+                    const float *cp = cp0 + g * (NP + 1) * kW;
+                    Cc += (double)__ldcg(cp);
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) TX[k] += (double)__ldcg(cp + (1 + k) * kW);
+                }
             }
             ubg = unx;
         }

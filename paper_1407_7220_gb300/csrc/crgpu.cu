@@ -395,7 +395,7 @@ cr_status init_state(cr_ctx *h)
         CR_CUDA(h, cudaMemsetAsync(P.mu[b], 0, sizeof(double) * h->N, h->stream));
     }
     CR_CUDA(h, cudaMemsetAsync(P.rowpart, 0, sizeof(float) * (size_t)P.Q * h->N, h->stream));
-    CR_CUDA(h, cudaMemsetAsync(P.colpart, 0, sizeof(float) * (size_t)P.G * P.slots * (h->NP + 1) * crk::kW, h->stream));
+    CR_CUDA(h, cudaMemsetAsync(P.colpart, 0, sizeof(float) * (size_t)P.G * P.slots * crk::kWR * (h->NP + 1) * crk::kW, h->stream));
     DevState st;
     std::memset(&st, 0, sizeof st);
     st.scal[0].t = 1.0;   // t_1 = 1 (Iteration 0 of Fig. 2)
@@ -630,7 +630,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
         CR_TRY(dev_alloc(h, &P.mu[b], N));
     }
     CR_TRY(dev_alloc(h, &P.rowpart, (size_t)P.Q * N));
-    CR_TRY(dev_alloc(h, &P.colpart, (size_t)G * P.slots * (h->NP + 1) * crk::kW));
+    CR_TRY(dev_alloc(h, &P.colpart, (size_t)G * P.slots * crk::kWR * (h->NP + 1) * crk::kW));
     CR_TRY(dev_alloc(h, &P.foldpart, (size_t)G * 8));
     CR_TRY(dev_alloc(h, &P.kktpart, (size_t)G * 8));
     CR_TRY(dev_alloc(h, &P.st, 1));
@@ -1369,9 +1369,9 @@ cr_status cr_batch_create(int32_t B, const int64_t *N, const int32_t *n, const d
         }
         if (need > (long long)h->P.G * h->P.slots) {
             float *cp = nullptr;
-            if (dev_alloc(h, &cp, (size_t)need * (b->NP + 1) * crk::kW) != CR_OK)
+            if (dev_alloc(h, &cp, (size_t)need * crk::kWR * (b->NP + 1) * crk::kW) != CR_OK)
                 return cleanup(create_error(CR_ENOMEM, "column partials"));
-            cudaMemsetAsync(cp, 0, sizeof(float) * (size_t)need * (b->NP + 1) * crk::kW, b->stream);
+            cudaMemsetAsync(cp, 0, sizeof(float) * (size_t)need * crk::kWR * (b->NP + 1) * crk::kW, b->stream);
             h->P.colpart = cp;
         }
     }
