@@ -1,7 +1,7 @@
 """GPU (CUDA, sm_103a) path against the FP64 CPU oracle, through the C ABI.
 
 Inputs are the seeded recipes of ``paper_1407_7220_gb300.datagen``; both sides
-get the same arrays.  Tolerances are derived in the design doc: FP32 multipliers
+get the same arrays.  Tolerances follow from the arithmetic: FP32 multipliers
 carry a relative rounding of 2^-24 per store, and the fold divides A_2^T theta
 by gamma, so subgradients lose more digits than fitted values.
 """
@@ -140,7 +140,7 @@ def test_grid_partitions_give_same_iterates(crg, grid):
 # -------------------------------------------------------------------------
 def test_converged_fit_matches_oracle_reference(crg):
     # FP32 multipliers cannot resolve this solution to KKT 1e-6: entries near 2 have an
-    # ulp of 2.4e-7 while the constraint values need theta to ~5e-8 (DESIGN.md, Sec. 7).
+    # ulp of 2.4e-7 while the constraint values need theta to ~5e-8.
     # With stochastic rounding the FP32 path keeps converging (round-to-nearest stalls);
     # it is checked at KKT 1e-4 against the FP64 oracle's converged fit, where the fit
     # error measured 1.8e-4 (the same 1-3 x KKT relation the oracle shows on NNLS-pinned cases).
