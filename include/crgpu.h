@@ -61,6 +61,16 @@ enum {
     CR_DRIVER_PHASES = 2      /* one kernel launch per phase per iteration */
 };
 
+/* Pair-pass engine (cr_options.pair_engine).  The pair pass needs, per stage of 16 rows x 256
+ * columns, the residual dot products xi_l2 . x_l1 and the adjoint sums sum_l1 theta x_l1,
+ * sum_l1 theta: two rank-n products. */
+enum {
+    CR_PAIR_AUTO = 0,         /* tensor cores for n >= 8 unless record_every > 0; CUDA cores otherwise */
+    CR_PAIR_CUDA_CORES = 1,   /* packed FP32 FMA on the CUDA cores (bitwise reproducible by cr_backward) */
+    CR_PAIR_TENSOR_CORES = 2  /* tcgen05 TF32 MMA, three TF32 products per FP32 product (~FP32 accuracy);
+                                 not with record_every > 0 and not in a batch */
+};
+
 typedef struct {
     double gamma;   /* Tikhonov parameter of (regularize), > 0.  The paper gives no value; default 1e-2 */
     double L;       /* step constant L_g of Eq. (eq:lischitz); <= 0: the closed-form bound
@@ -85,7 +95,8 @@ typedef struct {
     int32_t profile;          /* 1: record CUDA events around every kernel launch (see cr_profile) */
     int32_t record_every;     /* > 0: cr_iterate keeps a checkpoint every this many iterations so that
                                  cr_backward can differentiate the unrolled iterations (FP32 theta, n <= 10) */
-    int32_t reserved[4];
+    int32_t pair_engine;      /* CR_PAIR_*: where the pair pass computes its two dense products */
+    int32_t reserved[3];
     double restart_tol;       /* restart only when the dual value fell by more than restart_tol * |previous|
                                  (guards the test against rounding noise); default 1e-7 */
 } cr_options;
@@ -153,6 +164,10 @@ cr_status cr_get_solution(cr_handle h, double *yhat, double *xi);
 /* Iterations run since creation/reset, momentum restarts so far, the step constant L used,
  * and the shift s.  Any pointer may be NULL. */
 cr_status cr_get_info(cr_handle h, int64_t *iters, int64_t *restarts, double *L, double *shift);
+
+/* The pair-pass engine the handle resolved at creation: CR_PAIR_CUDA_CORES or
+ * CR_PAIR_TENSOR_CORES (CR_PAIR_AUTO is decided by n and record_every). */
+cr_status cr_get_engine(cr_handle h, int32_t *engine);
 
 /* Kernel timing collected since the last call when cr_options.profile = 1 (CUDA events on the
  * handle's stream around each launch).  kind: 0 = pair pass (Step 2 + fused adjoint, the

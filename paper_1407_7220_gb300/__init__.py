@@ -22,6 +22,7 @@ import numpy as np
 __all__ = [
     "CrError", "Options", "Solver", "lib", "library_path", "exported_symbols",
     "THETA_F32", "THETA_BF16", "THETA_F16", "DRIVER_AUTO", "DRIVER_PERSISTENT", "DRIVER_PHASES",
+    "PAIR_AUTO", "PAIR_CUDA_CORES", "PAIR_TENSOR_CORES",
     "CR_OK", "CR_NOT_CONVERGED",
 ]
 
@@ -31,6 +32,7 @@ library_path = os.path.join(HERE, "libcrgpu.so")
 CR_OK, CR_NOT_CONVERGED, CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ETIMEOUT, CR_ENUMERIC, CR_ESTATE = 0, 1, -1, -2, -3, -4, -5, -6
 THETA_F32, THETA_BF16, THETA_F16 = 0, 1, 2
 DRIVER_AUTO, DRIVER_PERSISTENT, DRIVER_PHASES = 0, 1, 2
+PAIR_AUTO, PAIR_CUDA_CORES, PAIR_TENSOR_CORES = 0, 1, 2
 _DTYPES = {"f32": THETA_F32, "fp32": THETA_F32, "float32": THETA_F32, "bf16": THETA_BF16,
            "bfloat16": THETA_BF16, "f16": THETA_F16, "fp16": THETA_F16, "float16": THETA_F16}
 
@@ -40,7 +42,7 @@ exported_symbols = (
     "cr_objective", "cr_kkt_residual", "cr_get_solution", "cr_get_info", "cr_destroy",
     "cr_status_str", "cr_last_error", "cr_profile", "cr_get_device_state", "cr_kkt_residual_noalloc",
     "cr_batch_create", "cr_batch_solve", "cr_batch_iterate", "cr_batch_reset", "cr_batch_instance",
-    "cr_batch_info", "cr_batch_destroy", "cr_batch_last_error", "cr_backward",
+    "cr_batch_info", "cr_batch_destroy", "cr_batch_last_error", "cr_backward", "cr_get_engine",
 )
 PROFILE_PAIR, PROFILE_FOLD, PROFILE_KKT, PROFILE_PERSISTENT = 0, 1, 2, 3
 
@@ -54,7 +56,7 @@ class Options(ctypes.Structure):
         ("driver", ctypes.c_int32), ("grid", ctypes.c_int32), ("fp16_exponent", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("barrier_timeout_ms", ctypes.c_int32),
         ("test_barrier_extra", ctypes.c_int32), ("profile", ctypes.c_int32), ("record_every", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("pair_engine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
         ("restart_tol", ctypes.c_double),
     ]
 
@@ -95,6 +97,7 @@ def lib():
             L.cr_kkt_residual.argtypes = [H, dp, dp, dp]
             L.cr_get_solution.argtypes = [H, dp, dp]
             L.cr_get_info.argtypes = [H, i64p, i64p, dp, dp]
+            L.cr_get_engine.argtypes = [H, ctypes.POINTER(ctypes.c_int32)]
             vpp = ctypes.POINTER(ctypes.c_void_p)
             L.cr_get_device_state.argtypes = [H, vpp, i64p, vpp, vpp, vpp, vpp, dp]
             L.cr_get_device_state.restype = ctypes.c_int
@@ -241,7 +244,10 @@ class Solver:
         it, rs = ctypes.c_int64(), ctypes.c_int64()
         Lc, s = ctypes.c_double(), ctypes.c_double()
         self._check(lib().cr_get_info(self._h, ctypes.byref(it), ctypes.byref(rs), ctypes.byref(Lc), ctypes.byref(s)))
-        return {"iters": it.value, "restarts": rs.value, "L": Lc.value, "shift": s.value}
+        eng = ctypes.c_int32()
+        self._check(lib().cr_get_engine(self._h, ctypes.byref(eng)))
+        return {"iters": it.value, "restarts": rs.value, "L": Lc.value, "shift": s.value,
+                "engine": "tensor_cores" if eng.value == PAIR_TENSOR_CORES else "cuda_cores"}
 
     def backward(self, dL_dyhat, dL_dybar, dL_dX):
         """Reverse mode through the recorded iterations; device float32 torch tensors (N,), (N,), (N, n)."""

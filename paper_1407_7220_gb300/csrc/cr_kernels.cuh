@@ -103,7 +103,11 @@ struct Params {
     double *mu[2];          // multipliers of the y >= 0 rows (N)
     float *rowpart;         // [N][Q]: row sums per (stripe, column half), Q = ceil4(2S), padding 0
     int Q;
-    float *colpart;         // [G][slots][kWR][NP+1][kW]: column partials per CTA, stripe slot and row group
+    float *colpart;         // [G][slots][cgroups][NP+1][kW]: column partials per CTA, stripe slot and group
+    int cgroups;            // column-partial groups per CTA segment: kWR row groups of warps, or 1
+    int tc;                 // 1: the pair pass runs its two products on the tensor cores
+    float *xi_tc;           // tensor-core operands (TF32 hi/lo): Xi per stripe, written by every foldB
+    float *xr_tc, *xt_tc;   // X rows and [X | 1] transposed per 8-row block (constant)
     double *foldpart;       // [G][8]
     double *kktpart;        // [G][8]
     DevState *st;
@@ -396,6 +400,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
+// Non-blocking probe of a phase (try_wait may suspend the thread for a while; test_wait does not).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
 {
     asm volatile(
@@ -503,9 +520,13 @@ __device__ __forceinline__ bool grid_barrier(const Params &P, unsigned long long
 }
 
 // CTA c's unit range [u0, u1) of the stripe-major (stripe, row) order.
+// First (stripe, row) unit of CTA c: an even split of the S*N units, each segment starting
+// on an 8-row boundary (whole 8-row blocks for the tensor-core operands).
 __device__ __forceinline__ long long unit_begin(const Params &P, long long c)
 {
-    return (long long)(((unsigned long long)c * (unsigned long long)P.total) / (unsigned long long)P.G);
+    const long long u = (long long)(((unsigned long long)c * (unsigned long long)P.total) / (unsigned long long)P.G);
+    const long long s = u / P.N;
+    return s * P.N + ((u - s * P.N) & ~7ll);
 }
 
 // Bounded mbarrier phase wait: gives up (and sets the error word) after the
@@ -594,6 +615,26 @@ __device__ void phase_foldB(const Params &P, long long ell, double *red, long lo
         }
         P.rowrec[l * RecLayout<NP>::REC] = (float)ys;
         P.ccol2[l] = (float)(d - ys);
+        if (P.tc) {
+            // Xi of column l as the A operand of the residual product: stripe l/256, column pair
+            // (l%256)/2 = lane, even/odd column = MMA; TF32 hi and lo parts
+            constexpr int KP = (NP + 7) / 8 * 8;
+            const long long st = l / kW;
+            const int cl = (int)(l - st * kW), eo = cl & 1, mm = cl >> 1;
+            float *base = P.xi_tc + (size_t)st * (2 * 2 * 128 * KP);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const float xf = P.xi2[l * NP + k];
+                uint32_t hb;
+                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(xf));
+                const float hi = __uint_as_float(hb);
+                uint32_t lb;
+                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"(xf - hi));
+                const size_t o = ((size_t)(mm >> 3) * (KP / 4) + (k >> 2)) * 32 + (mm & 7) * 4 + (k & 3);
+                base[(size_t)(eo * 2 + 0) * 128 * KP + o] = hi;
+                base[(size_t)(eo * 2 + 1) * 128 * KP + o] = __uint_as_float(lb);
+            }
+        }
     }
 }
 
@@ -976,9 +1017,8 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red, long lo
             const long long unx = unit_begin(P, cta + 1);
             if (unx > ubg) {
                 const long long fs = ubg / N;
-                const float *cp0 = P.colpart + ((cta * P.slots + (s - fs)) * kWR * (NP + 1)) * kW + cl;
-#pragma unroll
-                for (int g = 0; g < kWR; ++g) {
+                const float *cp0 = P.colpart + ((cta * P.slots + (s - fs)) * P.cgroups * (NP + 1)) * kW + cl;
+                for (int g = 0; g < P.cgroups; ++g) {
                     const float *cp = cp0 + g * (NP + 1) * kW;
                     Cc += (double)__ldcg(cp);
 #pragma unroll

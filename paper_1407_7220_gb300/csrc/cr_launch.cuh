@@ -4,13 +4,17 @@
 
 #include "cr_kernels.cuh"
 #include "cr_backward.cuh"
+#include "cr_pair_tc.cuh"
 
 namespace crk {
 
 enum Phase : int { PH_FOLDB = 0, PH_PAIR = 1, PH_FOLDA = 2, PH_KKT32 = 3, PH_KKT64 = 4, PH_DECIDE32 = 5, PH_DECIDE64 = 6 };
 
-// Dynamic shared memory of the pair pass (pipeline stages + column-partial reduction).
-template <typename TS, int NP> constexpr size_t pair_smem_bytes() { return PairSmem<TS, NP>::bytes; }
+// Dynamic shared memory of the pair pass (the larger of the CUDA-core and tensor-core layouts).
+template <typename TS, int NP> constexpr size_t pair_smem_bytes()
+{
+    return PairSmem<TS, NP>::bytes > TcShape<TS, NP>::bytes ? PairSmem<TS, NP>::bytes : TcShape<TS, NP>::bytes;
+}
 
 // 128-byte aligned base of the dynamic shared memory (TMA destinations).
 __device__ __forceinline__ unsigned char *aligned_smem(unsigned char *raw)
@@ -31,23 +35,16 @@ __device__ __forceinline__ void init_pipeline(uint64_t *full, uint64_t *empty)
     __syncthreads();
 }
 
-// Persistent driver: iterations ell0..ell1 in one cooperative launch.  Phases are
+// Persistent driver: iterations ell0..ell1 in one cooperative launch (CUDA-core pair pass).  Phases are
 // separated by bounded grid barriers; every CTA takes the same decisions from the
 // same reduced values.  check_every > 0 enables the convergence test (FP32 screen,
 // FP64 confirmation) every check_every iterations and at ell1.
 template <typename TS, int NP>
-__global__ void __launch_bounds__(kThreads, 1)
-k_persistent(const __grid_constant__ Params P, long long ell0, long long ell1, int check_every, double tol,
-             double sigma)
+__device__ __forceinline__ void persistent_body(const Params &P, long long ell0, long long ell1, int check_every,
+                                                double tol, double sigma, unsigned char *sm, double *red, double *s_m,
+                                                uint64_t *full, uint64_t *empty)
 {
-    extern __shared__ unsigned char sm_raw[];
-    unsigned char *sm = aligned_smem(sm_raw);
-    __shared__ double red[72];
-    __shared__ double s_m[8];
-    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
     unsigned long long bar = 0, kstage = 0;
-    init_pipeline(full, empty);
-
     phase_foldB<NP>(P, ell0, red, blockIdx.x);
     if (!grid_barrier(P, bar)) return;
     for (long long ell = ell0; ell <= ell1; ++ell) {
@@ -98,6 +95,20 @@ k_persistent(const __grid_constant__ Params P, long long ell0, long long ell1, i
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) P.st->iters_done = ell1;
+}
+
+template <typename TS, int NP>
+__global__ void __launch_bounds__(kThreads, 1)
+k_persistent(const __grid_constant__ Params P, long long ell0, long long ell1, int check_every, double tol,
+             double sigma)
+{
+    extern __shared__ unsigned char sm_raw[];
+    unsigned char *sm = aligned_smem(sm_raw);
+    __shared__ double red[72];
+    __shared__ double s_m[8];
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
+    init_pipeline(full, empty);
+    persistent_body<TS, NP>(P, ell0, ell1, check_every, tol, sigma, sm, red, s_m, full, empty);
 }
 
 // One phase of one iteration (the CR_DRIVER_PHASES path and the stand-alone metric
@@ -260,9 +271,30 @@ k_batch(const __grid_constant__ BatchArgs A, long long chunk, int check_every, d
 #undef CR_BAR
 }
 
+// The pair pass with its products on the tensor cores (phase driver): 16 consumer warps
+// plus one leader warp.  No-op once the state says converged or failed.
+template <typename TS, int NP>
+__global__ void __launch_bounds__(kTcThreads, 1) k_pair_tc(const __grid_constant__ Params P, long long ell)
+{
+    extern __shared__ unsigned char sm_raw[];
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
+    __shared__ __align__(8) TcBars tcb;
+    __shared__ int s_skip;
+    if (threadIdx.x == 0) s_skip = (__ldcg(&P.st->error) != 0 || __ldcg(&P.st->converged) != 0) ? 1 : 0;
+    __syncthreads();
+    if (s_skip) return;   // block-uniform
+    unsigned long long kstage = 0, kseg = 0, kgrp = 0;
+    tc_init_pipeline(full, empty);
+    tc_init_bars(tcb);
+    tc_alloc<TS, NP>(tcb);   // includes a block barrier
+    phase_pair_tc<TS, NP>(P, ell, aligned_smem(sm_raw), full, empty, tcb, kstage, kseg, kgrp, blockIdx.x);
+    tc_free<TS, NP>(tcb);
+}
+
 struct KernelSet {
     const void *persistent;
     const void *phase;
+    const void *pair_tc;
     const void *kkt64_if;
     const void *batch;
     size_t smem;
@@ -279,6 +311,7 @@ template <typename TS, int NP> KernelSet make_set()
     KernelSet k;
     k.persistent = (const void *)k_persistent<TS, NP>;
     k.phase = (const void *)k_phase<TS, NP>;
+    k.pair_tc = (const void *)k_pair_tc<TS, NP>;
     k.kkt64_if = (const void *)k_kkt64_if_screened<TS, NP>;
     k.batch = (const void *)k_batch<TS, NP>;
     k.smem = pair_smem_bytes<TS, NP>();

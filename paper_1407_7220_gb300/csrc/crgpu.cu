@@ -133,7 +133,7 @@ KernelSet kernels_for(int dtype, int NP)
     case CR_THETA_F32: return crk::kernels_f32(NP);
     case CR_THETA_BF16: return crk::kernels_bf16(NP);
     case CR_THETA_F16: return crk::kernels_f16(NP);
-    default: return KernelSet{nullptr, nullptr, nullptr, nullptr, 0, 0, {nullptr, nullptr, nullptr, nullptr}};
+    default: return KernelSet{nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, {nullptr, nullptr, nullptr, nullptr}};
     }
 }
 
@@ -279,13 +279,22 @@ template <typename T> cr_status dev_alloc(cr_ctx *h, T **p, size_t count)
         if (s_ != CR_OK) return s_;        \
     } while (0)
 
+// First unit of CTA c (the device's unit_begin): an even split, rounded down to an 8-row
+// boundary inside the stripe.
+long long unit_begin_host(long long c, long long total, long long N, int G)
+{
+    const long long u = (long long)(((unsigned long long)c * total) / G);
+    const long long s = u / N;
+    return s * N + ((u - s * N) & ~7ll);
+}
+
 // Work partition of the pair pass: the number of column-partial slots per CTA.
 int max_slots(long long total, long long N, int G)
 {
     int best = 1;
     for (long long c = 0; c < G; ++c) {
-        long long u0 = (long long)(((unsigned long long)c * total) / G);
-        long long u1 = (long long)(((unsigned long long)(c + 1) * total) / G);
+        long long u0 = unit_begin_host(c, total, N, G);
+        long long u1 = unit_begin_host(c + 1, total, N, G);
         if (u1 <= u0) continue;
         best = std::max(best, (int)((u1 - 1) / N - u0 / N + 1));
     }
@@ -337,6 +346,11 @@ cr_status launch_phase(cr_ctx *h, int phase, long long ell, double tol, int grid
     void *args[] = {&P, &phase, &ell, &tol, &h->sigma};
     const int g = grid > 0 ? grid : h->P.G;
     ProfScope ps(h, phase_kind(phase));
+    if (phase == crk::PH_PAIR && h->P.tc) {
+        void *targs[] = {&P, &ell};
+        CR_CUDA(h, cudaLaunchKernel(h->ks.pair_tc, dim3(g), dim3(crk::kTcThreads), targs, h->ks.smem, h->stream));
+        return CR_OK;
+    }
     CR_CUDA(h, cudaLaunchKernel(h->ks.phase, dim3(g), dim3(crk::kThreads), args, h->ks.smem, h->stream));
     return CR_OK;
 }
@@ -384,6 +398,57 @@ cr_status read_state(cr_ctx *h, DevState *st)
     return CR_OK;
 }
 
+// Tensor-core operands that do not change: X rows (B of the residual product) and [X | 1]
+// transposed (B of the adjoint product), TF32 hi/lo, in 8-row blocks of the canonical K-major
+// layout (see cr_pair_tc.cuh); one group of zero padding past the last row.  The Xi array is
+// zeroed here and written by every foldB.
+float tf32_round_host(float x)
+{
+    // round to nearest, ties away from zero, to 10 explicit mantissa bits (finite inputs)
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    b = (b + 0x1000u) & 0xFFFFE000u;
+    float r;
+    std::memcpy(&r, &b, 4);
+    return r;
+}
+
+cr_status setup_tc_operands(cr_ctx *h, const std::vector<double> &X)
+{
+    Params &P = h->P;
+    const long long N = h->N;
+    const int n = h->n, NP = h->NP;
+    const int KP = crk::tc_kp(NP), N2 = crk::tc_n2(NP);
+    const long long NB = (N + 7) / 8 + crk::kGR / 8;   // padding: a group load reads kGR/8 blocks
+    std::vector<float> xr((size_t)NB * crk::tc_xr_floats(NP), 0.0f), xt((size_t)NB * crk::tc_xt_floats(NP), 0.0f);
+    for (long long r = 0; r < N; ++r) {
+        const long long blk = r >> 3;
+        const int r8 = (int)(r & 7);
+        for (int j = 0; j <= n; ++j) {
+            const float v = j < n ? (float)X[(size_t)r * n + j] : 1.0f;
+            const float hi = tf32_round_host(v), lo = tf32_round_host(v - hi);
+            if (j < n) {
+                const size_t o = (size_t)blk * crk::tc_xr_floats(NP) + (size_t)(j >> 2) * 32 + r8 * 4 + (j & 3);
+                xr[o] = hi;
+                xr[o + (size_t)KP * 8] = lo;
+            }
+            const size_t o = (size_t)blk * crk::tc_xt_floats(NP) + ((size_t)(j >> 3) * 2 + (r8 >> 2)) * 32 +
+                             (j & 7) * 4 + (r8 & 3);
+            xt[o] = hi;
+            xt[o + (size_t)N2 * 8] = lo;
+        }
+    }
+    CR_TRY(dev_alloc(h, &P.xr_tc, xr.size()));
+    CR_TRY(dev_alloc(h, &P.xt_tc, xt.size()));
+    CR_TRY(dev_alloc(h, &P.xi_tc, (size_t)P.S * crk::tc_xi_floats(NP)));
+    CR_CUDA(h, cudaMemcpyAsync(P.xr_tc, xr.data(), sizeof(float) * xr.size(), cudaMemcpyHostToDevice, h->stream));
+    CR_CUDA(h, cudaMemcpyAsync(P.xt_tc, xt.data(), sizeof(float) * xt.size(), cudaMemcpyHostToDevice, h->stream));
+    CR_CUDA(h, cudaMemsetAsync(P.xi_tc, 0, sizeof(float) * (size_t)P.S * crk::tc_xi_floats(NP), h->stream));
+    // the host vectors are released at return: finish the copies first
+    CR_CUDA(h, cudaStreamSynchronize(h->stream));
+    return CR_OK;
+}
+
 cr_status init_state(cr_ctx *h)
 {
     const Params &P = h->P;
@@ -395,7 +460,7 @@ cr_status init_state(cr_ctx *h)
         CR_CUDA(h, cudaMemsetAsync(P.mu[b], 0, sizeof(double) * h->N, h->stream));
     }
     CR_CUDA(h, cudaMemsetAsync(P.rowpart, 0, sizeof(float) * (size_t)P.Q * h->N, h->stream));
-    CR_CUDA(h, cudaMemsetAsync(P.colpart, 0, sizeof(float) * (size_t)P.G * P.slots * crk::kWR * (h->NP + 1) * crk::kW, h->stream));
+    CR_CUDA(h, cudaMemsetAsync(P.colpart, 0, sizeof(float) * (size_t)P.G * P.slots * P.cgroups * (h->NP + 1) * crk::kW, h->stream));
     DevState st;
     std::memset(&st, 0, sizeof st);
     st.scal[0].t = 1.0;   // t_1 = 1 (Iteration 0 of Fig. 2)
@@ -523,6 +588,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     }
     CR_CUDA(h, cudaFuncSetAttribute(h->ks.persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem));
     CR_CUDA(h, cudaFuncSetAttribute(h->ks.phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem));
+    CR_CUDA(h, cudaFuncSetAttribute(h->ks.pair_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem));
     int per_sm = 0;
     CR_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, h->ks.persistent, crk::kThreads, h->ks.smem));
     int coop = 0;
@@ -559,7 +625,22 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     h->ld = ((N + 15) / 16) * 16;
     P.ld = h->ld;
     P.S = (int)S;
-    P.Q = (int)(((2 * S) + 3) / 4 * 4);
+    // pair-pass engine: tensor cores for the two products when n is not tiny, unless the
+    // iterations are recorded for cr_backward (which re-evaluates the CUDA-core arithmetic)
+    const bool batch_member = np_override > 0;
+    if (o.pair_engine < CR_PAIR_AUTO || o.pair_engine > CR_PAIR_TENSOR_CORES)
+        return fail(h, CR_EINVAL, "unknown pair_engine %d", o.pair_engine);
+    if (o.pair_engine == CR_PAIR_TENSOR_CORES &&
+        (o.record_every > 0 || batch_member || o.driver == CR_DRIVER_PERSISTENT))
+        return fail(h, CR_EINVAL, "pair_engine tensor cores: not with record_every > 0, the persistent driver or a batch");
+    P.tc = (o.pair_engine == CR_PAIR_TENSOR_CORES ||
+            (o.pair_engine == CR_PAIR_AUTO && h->NP >= 8 && o.record_every <= 0 && !batch_member &&
+             o.driver != CR_DRIVER_PERSISTENT))
+               ? 1
+               : 0;
+    if (P.tc) h->persistent_ok = false;   // the tensor-core pass runs in its own launch (phase driver)
+    P.Q = (int)(((P.tc ? 4 : 2) * S + 3) / 4 * 4);   // row partials per row: one per warp column slab
+    P.cgroups = P.tc ? 1 : crk::kWR;
     P.G = G;
     P.total = total;
     P.slots = max_slots(total, N, G);
@@ -630,7 +711,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
         CR_TRY(dev_alloc(h, &P.mu[b], N));
     }
     CR_TRY(dev_alloc(h, &P.rowpart, (size_t)P.Q * N));
-    CR_TRY(dev_alloc(h, &P.colpart, (size_t)G * P.slots * crk::kWR * (h->NP + 1) * crk::kW));
+    CR_TRY(dev_alloc(h, &P.colpart, (size_t)G * P.slots * P.cgroups * (h->NP + 1) * crk::kW));
     CR_TRY(dev_alloc(h, &P.foldpart, (size_t)G * 8));
     CR_TRY(dev_alloc(h, &P.kktpart, (size_t)G * 8));
     CR_TRY(dev_alloc(h, &P.st, 1));
@@ -645,6 +726,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     CR_CUDA(h, cudaMemcpyAsync(X64, X.data(), sizeof(double) * N * n, cudaMemcpyHostToDevice, h->stream));
     CR_CUDA(h, cudaMemcpyAsync(P.rowrec, rec.data(), sizeof(float) * rec.size(), cudaMemcpyHostToDevice, h->stream));
     CR_CUDA(h, cudaMemcpyAsync(hh, hv.data(), sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+    if (P.tc) CR_TRY(setup_tc_operands(h, X));
     return init_state(h);
 }
 
@@ -710,6 +792,7 @@ void cr_options_default(cr_options *o)
     o->seed = 0x5eedULL;
     o->stream = nullptr;
     o->restart_tol = 1e-7;
+    o->pair_engine = CR_PAIR_AUTO;
 }
 
 cr_status cr_create(const double *X, const double *ybar, int64_t N, int32_t n, const cr_options *opt, cr_handle *out)
@@ -879,6 +962,13 @@ cr_status cr_get_info(cr_handle h, int64_t *iters, int64_t *restarts, double *L,
         CR_TRY(read_state(h, &st));
         *restarts = st.scal[h->iters & 1].restarts;
     }
+    return CR_OK;
+}
+
+cr_status cr_get_engine(cr_handle h, int32_t *engine)
+{
+    if (!h || !engine) return CR_EINVAL;
+    *engine = h->P.tc ? CR_PAIR_TENSOR_CORES : CR_PAIR_CUDA_CORES;
     return CR_OK;
 }
 

@@ -1,0 +1,116 @@
+"""The tensor-core pair pass (tcgen05 MMA for the residual and adjoint products) through the C ABI.
+
+The two dense products of Step 2 and of the fused adjoint run as three TF32 products per
+FP32 product, so the iterates differ from the CUDA-core engine only at FP32 rounding level.
+The same trajectory bars as the CUDA-core parity tests apply against the FP64 oracle:
+fitted values within 2e-6 relative, subgradients within 2e-4 of max(1, max|xi|), dual
+value within 1e-5 relative.  Sizes cover several 256-column stripes, a ragged last stripe,
+N not a multiple of 8 or 16, segments that change stripe inside a CTA, and every compiled
+padded width from 8 up.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1407_7220_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def crg():
+    import paper_1407_7220_gb300 as m
+    return m
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _recipe(n):
+    return "maxaff" if n <= 10 else "lse"
+
+
+def test_engine_selection(crg):
+    X, yb, _ = datagen.make("maxaff", N=300, n=10)
+    assert crg.Solver(X, yb).info()["engine"] == "tensor_cores"
+    assert crg.Solver(X, yb, pair_engine=crg.PAIR_CUDA_CORES).info()["engine"] == "cuda_cores"
+    assert crg.Solver(X, yb, record_every=10).info()["engine"] == "cuda_cores"
+    assert crg.Solver(X, yb, driver=crg.DRIVER_PERSISTENT).info()["engine"] == "cuda_cores"
+    with pytest.raises(crg.CrError):
+        crg.Solver(X, yb, driver=crg.DRIVER_PERSISTENT, pair_engine=crg.PAIR_TENSOR_CORES)
+    X5, y5, _ = datagen.make("sumexp", N=300, n=5)
+    assert crg.Solver(X5, y5).info()["engine"] == "cuda_cores"
+    assert crg.Solver(X5, y5, pair_engine=crg.PAIR_TENSOR_CORES).info()["engine"] == "tensor_cores"
+
+
+@pytest.mark.parametrize("N,n", [(300, 8), (1031, 10), (517, 16), (777, 20), (300, 32), (301, 5)])
+@pytest.mark.parametrize("k", [1, 3, 40])
+def test_trajectory_matches_oracle(crg, N, n, k):
+    X, yb, _ = datagen.make(_recipe(n), N=N, n=n)
+    g = crg.Solver(X, yb, gamma=0.1, stochastic_round=0, restart=0, pair_engine=crg.PAIR_TENSOR_CORES)
+    assert g.info()["engine"] == "tensor_cores"
+    o = O.Solver(X, yb, gamma=0.1, L=g.info()["L"], s=g.info()["shift"], momentum=True, restart=False)
+    g.iterate(k)
+    o.iterate(k)
+    y, xi = g.solution()
+    assert _rel(y, o.y_hat) <= 2e-6, _rel(y, o.y_hat)
+    assert np.abs(xi - o.xi).max() <= 2e-4 * max(1.0, np.abs(o.xi).max())
+    assert g.objective()["dual"] == pytest.approx(o.metrics["dual"], rel=1e-5, abs=1e-9)
+
+
+@pytest.mark.parametrize("N,n", [(1031, 10), (777, 20)])
+def test_engines_agree(crg, N, n):
+    X, yb, _ = datagen.make(_recipe(n), N=N, n=n)
+    r = {}
+    for eng in (crg.PAIR_TENSOR_CORES, crg.PAIR_CUDA_CORES):
+        s = crg.Solver(X, yb, gamma=0.1, stochastic_round=0, restart=0, pair_engine=eng)
+        s.iterate(60)
+        r[eng] = s.solution()
+    assert _rel(r[crg.PAIR_TENSOR_CORES][0], r[crg.PAIR_CUDA_CORES][0]) <= 1e-6
+
+
+@pytest.mark.parametrize("dtype,tol", [("bf16", 2e-3), ("f16", 2e-4)])
+def test_16bit_storage_matches_oracle(crg, dtype, tol):
+    # theta rounded to 8 (BF16) or 11 (FP16) significant bits per store
+    X, yb, _ = datagen.make("lse", N=640, n=20)
+    g = crg.Solver(X, yb, gamma=0.1, theta_dtype=dtype, stochastic_round=0, restart=0)
+    assert g.info()["engine"] == "tensor_cores"
+    o = O.Solver(X, yb, gamma=0.1, L=g.info()["L"], s=g.info()["shift"], momentum=True, restart=False)
+    g.iterate(20)
+    o.iterate(20)
+    assert _rel(g.solution()[0], o.y_hat) <= tol
+
+
+@pytest.mark.parametrize("grid", [1, 2, 7, 40])
+def test_partitions_give_same_iterates(crg, grid):
+    # one CTA walks every stripe (Xi reloaded at each segment); more CTAs split stripes
+    X, yb, _ = datagen.make("maxaff", N=1201, n=10)
+    ref = crg.Solver(X, yb, stochastic_round=0, restart=0, grid=64)
+    s = crg.Solver(X, yb, stochastic_round=0, restart=0, grid=grid)
+    assert s.info()["engine"] == "tensor_cores"
+    ref.iterate(15)
+    s.iterate(15)
+    assert _rel(s.solution()[0], ref.solution()[0]) <= 1e-6
+
+
+def test_deterministic_with_stochastic_rounding(crg):
+    X, yb, _ = datagen.make("lse", N=900, n=20)
+    r = []
+    for _ in range(2):
+        s = crg.Solver(X, yb, theta_dtype="bf16", stochastic_round=1, seed=7)
+        s.iterate(12)
+        r.append(s.solution())
+    assert np.array_equal(r[0][0], r[1][0]) and np.array_equal(r[0][1], r[1][1])
+
+
+def test_solve_reaches_fp64_confirmed_kkt(crg):
+    X, yb, _ = datagen.make("maxaff", N=800, n=10)
+    tc = crg.Solver(X, yb, gamma=0.1, stochastic_round=1, restart=0, kkt_every=50)
+    cc = crg.Solver(X, yb, gamma=0.1, stochastic_round=1, restart=0, kkt_every=50, pair_engine=crg.PAIR_CUDA_CORES)
+    conv, _ = tc.solve(1e-3, 200_000)
+    assert conv and tc.kkt_residual()["kkt"] <= 1e-3
+    conv2, _ = cc.solve(1e-3, 200_000)
+    assert conv2
+    # both at KKT 1e-3 of the same problem: fitted values within a few KKT units
+    assert _rel(tc.solution()[0], cc.solution()[0]) <= 1e-2
