@@ -175,9 +175,10 @@ template <typename TS, int NP> struct TcShape {
                   "stage buffers must stay 128-byte aligned");
     static constexpr size_t bytes = off_stage + kStages * stage_bytes + 128;
     // tensor-memory columns: D1 (2 group buffers x {even, odd} x 64 rows), A2 = theta^T
-    // (2 buffers x {even hi, odd hi[, even lo, odd lo]} x 16), D2 ({even, odd} x N2)
+    // (NA2 buffers x {even hi, odd hi[, even lo, odd lo]} x 16), D2 ({even, odd} x N2)
     static constexpr int A2W = SPLIT ? 64 : 32;
-    static constexpr int COL_D1 = 0, COL_A2 = 4 * kGR, COL_D2 = COL_A2 + 2 * A2W;
+    static constexpr int NA2 = SPLIT ? (N2 > 32 ? 2 : 3) : 4;   // theta^T buffers (what fits in 512 columns)
+    static constexpr int COL_D1 = 0, COL_A2 = 4 * kGR, COL_D2 = COL_A2 + NA2 * A2W;
     static constexpr int COLS = COL_D2 + 2 * N2;
     static constexpr uint32_t NCOLS = COLS <= 128 ? 128u : (COLS <= 256 ? 256u : 512u);
     static_assert(COLS <= 512, "tensor memory");
@@ -189,7 +190,7 @@ template <typename TS, int NP> struct TcShape {
 struct TcBars {
     uint64_t xgfull[2];              // X rows of a group landed
     uint64_t d1full[2], d1free[2];   // MMA1 of a group done / its D1 read by all consumer warps
-    uint64_t a2full[2], a2free[2];   // theta^T of a stage written by all consumer warps / MMA2 done with it
+    uint64_t a2full[4], a2free[4];   // theta^T of a stage written by all consumer warps / MMA2 of the stage done
     uint64_t d2done, d2free;         // segment's MMA2 chain done / D2 read by warpgroup 0
     uint64_t xifull;                 // Xi of the segment's stripe landed
     uint64_t drain[2];               // end of pass: every MMA of issuer 1 / issuer 2 done
@@ -204,6 +205,8 @@ __device__ __forceinline__ void tc_init_bars(TcBars &B)
             mbar_init(&B.xgfull[i], 1);
             mbar_init(&B.d1full[i], 1);
             mbar_init(&B.d1free[i], kTcWarps);
+        }
+        for (int i = 0; i < 4; ++i) {
             mbar_init(&B.a2full[i], kTcWarps);
             mbar_init(&B.a2free[i], 1);
         }
@@ -218,8 +221,9 @@ __device__ __forceinline__ void tc_init_bars(TcBars &B)
     }
 }
 
-// Stage ring of the tensor-core pass: the "empty" barrier of a slot also waits for the
-// commit of the MMA2 that read the slot's X blocks.
+// Stage ring of the tensor-core pass: the "empty" barrier of a slot counts the consumer
+// warps and the commit of the MMA2 that read the slot's [X | 1] blocks.  (A per-slot barrier
+// completes once per use of the slot, so the producer's parity wait cannot alias.)
 __device__ __forceinline__ void tc_init_pipeline(uint64_t *full, uint64_t *empty)
 {
     if (threadIdx.x == 0) {
@@ -593,13 +597,14 @@ __device__ __forceinline__ void tc_issue_mma2(const Params &P, long long ubeg, l
         const int slot = mpos.slot;
         const bool first = mc.r == mc.r0;
         const bool last = mc.r + kRS >= mc.r1;
-        ok = mbar_wait(P, &full[slot], mpos.phase) && mbar_wait(P, &B.a2full[k & 1], (uint32_t)((k >> 1) & 1));
+        const int b = (int)(k % Sh::NA2);
+        ok = mbar_wait(P, &full[slot], mpos.phase) && mbar_wait(P, &B.a2full[b], (uint32_t)((k / Sh::NA2) & 1));
         if (ok && first && seg >= 1) ok = mbar_wait(P, &B.d2free, (uint32_t)((seg - 1) & 1));
         if (ok) {
             tc_fence_after();
-            tc_mma2<TS, NP>(tb, D, slot, (int)(k & 1), first);
+            tc_mma2<TS, NP>(tb, D, slot, b, first);
             umma_commit(&empty[slot]);
-            umma_commit(&B.a2free[k & 1]);
+            umma_commit(&B.a2free[b]);
             if (last) umma_commit(&B.d2done);
         }
         if (last) ++seg;
@@ -676,7 +681,7 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
             float *rp = P.rowpart + (s * 4 + q);
             for (long long r = r0; r < r1; r += kRS, ++k, cpos.next()) {
                 const int slot = cpos.slot;
-                const int b = (int)(k & 1);
+                const int b = (int)(k % Sh::NA2);   // theta^T buffer of this stage
                 const int go = (int)((r - r0) % kGR);          // row offset inside the MMA1 group
                 const bool glast = go + kRS == kGR || r + kRS >= r1;
                 const int b1 = (int)(gj & 1);
@@ -697,7 +702,8 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
                     if (lane == 0) mbar_arrive(&B.d1free[b1]);
                     ++gj;
                 }
-                if (ok && k >= 2) ok = mbar_wait(P, &B.a2free[b], (uint32_t)(((k >> 1) - 1) & 1));
+                if (ok && k >= (unsigned long long)Sh::NA2)
+                    ok = mbar_wait(P, &B.a2free[b], (uint32_t)(((k / Sh::NA2) - 1) & 1));
                 ok = __all_sync(0xffffffffu, ok);
                 // --- element-wise Step 2 on 4 rows x 2 columns ---
                 float ae[kTcRPW], ao[kTcRPW], le[kTcRPW], lo[kTcRPW], rs[kTcRPW];
