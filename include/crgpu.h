@@ -65,7 +65,8 @@ enum {
  * columns, the residual dot products xi_l2 . x_l1 and the adjoint sums sum_l1 theta x_l1,
  * sum_l1 theta: two rank-n products. */
 enum {
-    CR_PAIR_AUTO = 0,         /* tensor cores for n >= 8 unless record_every > 0; CUDA cores otherwise */
+    CR_PAIR_AUTO = 0,         /* tensor cores for a 16-bit theta with n >= 8 or an FP32 theta with n >= 16,
+                                 unless record_every > 0 or the persistent driver; CUDA cores otherwise */
     CR_PAIR_CUDA_CORES = 1,   /* packed FP32 FMA on the CUDA cores (bitwise reproducible by cr_backward) */
     CR_PAIR_TENSOR_CORES = 2  /* tcgen05 TF32 MMA, three TF32 products per FP32 product (~FP32 accuracy);
                                  not with record_every > 0 and not in a batch */

@@ -72,6 +72,7 @@ struct DevState {
 
 struct Params {
     CUtensorMap tmap[2];    // TMA descriptors of theta[0], theta[1]: N x N, box kRS x kW
+    CUtensorMap tmap32[2];  // the same with a box of 32 rows (tensor-core pass, 16-bit theta)
     // sizes
     long long N;
     int n;
@@ -775,8 +776,8 @@ __device__ __forceinline__ void flush_row_sums(float (&v)[8], int nb, long long 
     }
 }
 
-// Producer cursor: walks the CTA's stages (kRS rows of one stripe) in consumption order.
-struct StageCursor {
+// Producer cursor: walks the CTA's stages (RS rows of one stripe) in consumption order.
+template <int RS> struct StageCursorT {
     long long u, uend, s, r0, r1, r;
     __device__ __forceinline__ void begin(long long u0, long long ue, long long N)
     {
@@ -795,13 +796,14 @@ struct StageCursor {
     }
     __device__ __forceinline__ void advance(long long N)
     {
-        r += kRS;
+        r += RS;
         if (r >= r1) {
             u += r1 - r0;
             next_segment(N);
         }
     }
 };
+using StageCursor = StageCursorT<kRS>;
 
 // Position of stage k in the ring of S slots: slot = k mod S and the parity of k / S,
 // advanced one stage at a time without a division.

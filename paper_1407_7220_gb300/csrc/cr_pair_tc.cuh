@@ -14,7 +14,8 @@
 // CUDA cores keep the element-wise part: theta^(2), the projection, stochastic rounding, the
 // store of theta^(1)_l, and the row sums (A_1^T, + part).  Consumer thread (warp w < 16,
 // lane t) owns the tensor-memory lane m = 32 (w & 3) + t, i.e. columns 2m and 2m + 1 of the
-// stripe, and the rows 4 (w >> 2) .. 4 (w >> 2) + 3 of every stage.  Warp 16 loads (TMA),
+// stripe, and RPW = RS/4 consecutive rows of every stage of RS rows (RS = 32 for a 16-bit
+// theta, 16 for FP32, where two 32-row stages would not fit).  Warp 16 loads (TMA),
 // warp 17 issues MMA1, warp 18 issues MMA2; each of the three runs on its own lane 0.
 //
 // Operand layouts (tcgen05 canonical K-major, no swizzle: an 8-row x 16-byte core matrix is
@@ -36,9 +37,7 @@ namespace crk {
 
 constexpr int kTcWG = 4;                        // consumer warpgroups
 constexpr int kTcWarps = 4 * kTcWG;             // consumer warps
-constexpr int kTcRPW = kRS / kTcWG;             // rows of a stage per consumer warp
 constexpr int kTcThreads = (kTcWarps + 3) * 32; // + producer, MMA1 and MMA2 issuer warps
-static_assert(kRS % kTcWG == 0 && kTcRPW == 4, "row split of a tensor-core stage");
 
 // ---------------------------------------------------------------------------
 // tcgen05 / tensor-memory wrappers
@@ -134,6 +133,10 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8])
                  : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_ldv(uint32_t t, float (&v)[4]) { tmem_ld4(t, v); }
+__device__ __forceinline__ void tmem_ldv(uint32_t t, float (&v)[8]) { tmem_ld8(t, v); }
+__device__ __forceinline__ void tmem_stv(uint32_t t, const float (&v)[4]) { tmem_st4(t, v); }
+__device__ __forceinline__ void tmem_stv(uint32_t t, const float (&v)[8]) { tmem_st8(t, v); }
 __device__ __forceinline__ float tf32_rna(float x)
 {
     uint32_t r;
@@ -150,20 +153,23 @@ __host__ __device__ constexpr size_t tc_xi_floats(int NP) { return (size_t)2 * 2
 __host__ __device__ constexpr size_t tc_xr_floats(int NP) { return (size_t)2 * tc_kp(NP) * 8; }          // per 8-row block
 __host__ __device__ constexpr size_t tc_xt_floats(int NP) { return (size_t)2 * tc_n2(NP) * 8; }          // per 8-row block
 
-constexpr int kGR = 64;   // rows of one MMA1 group (kGR / kRS stages)
+constexpr int kGR = 64;   // rows of one MMA1 group (kGR / RS stages)
 
 template <typename TS, int NP> struct TcShape {
     static constexpr int KP = tc_kp(NP);
     static constexpr int N2 = tc_n2(NP);
     static constexpr bool SPLIT = std::is_same<TS, float>::value;   // FP32 theta needs a hi/lo split
+    static constexpr int RS = SPLIT ? 16 : 32;                        // rows of a stage
+    static constexpr int RPW = RS / kTcWG;                            // rows of a stage per consumer warp
+    static_assert(kGR % RS == 0 && RS % 8 == 0 && (RPW == 4 || RPW == 8), "stage split");
     static constexpr int REC = RecLayout<NP>::REC;
-    static constexpr size_t tile_bytes = (size_t)kRS * kW * sizeof(TS);
-    static constexpr size_t rec_bytes = (size_t)kRS * REC * sizeof(float);
+    static constexpr size_t tile_bytes = (size_t)RS * kW * sizeof(TS);
+    static constexpr size_t rec_bytes = (size_t)RS * REC * sizeof(float);
     static constexpr size_t xr_block = tc_xr_floats(NP) * 4;   // bytes of one 8-row block
     static constexpr size_t xt_block = tc_xt_floats(NP) * 4;
     static constexpr size_t off_rec = 2 * tile_bytes;
     static constexpr size_t off_xt = off_rec + rec_bytes;
-    static constexpr size_t stage_bytes = off_xt + 2 * xt_block;
+    static constexpr size_t stage_bytes = off_xt + (RS / 8) * xt_block;
     static constexpr size_t xi_bytes = tc_xi_floats(NP) * 4;
     static constexpr size_t xg_bytes = (kGR / 8) * xr_block;   // X rows of one group
     static constexpr size_t off_xg = xi_bytes;                  // 2 group buffers
@@ -175,10 +181,13 @@ template <typename TS, int NP> struct TcShape {
                   "stage buffers must stay 128-byte aligned");
     static constexpr size_t bytes = off_stage + kStages * stage_bytes + 128;
     // tensor-memory columns: D1 (2 group buffers x {even, odd} x 64 rows), A2 = theta^T
-    // (NA2 buffers x {even hi, odd hi[, even lo, odd lo]} x 16), D2 ({even, odd} x N2)
-    static constexpr int A2W = SPLIT ? 64 : 32;
-    static constexpr int NA2 = SPLIT ? (N2 > 32 ? 2 : 3) : 4;   // theta^T buffers (what fits in 512 columns)
-    static constexpr int COL_D1 = 0, COL_A2 = 4 * kGR, COL_D2 = COL_A2 + NA2 * A2W;
+    // (NA2 buffers x {even hi, odd hi[, even lo, odd lo]} x RS), D2 ({even, odd} x N2)
+    static constexpr int A2W = (SPLIT ? 4 : 2) * RS;
+    static constexpr int COL_A2 = 4 * kGR;
+    static constexpr int NA2_FIT = (512 - COL_A2 - 2 * N2) / A2W;
+    static constexpr int NA2 = NA2_FIT > 4 ? 4 : NA2_FIT;   // theta^T buffers (what fits in 512 columns)
+    static_assert(NA2 >= 2, "tensor memory");
+    static constexpr int COL_D1 = 0, COL_D2 = COL_A2 + NA2 * A2W;
     static constexpr int COLS = COL_D2 + 2 * N2;
     static constexpr uint32_t NCOLS = COLS <= 128 ? 128u : (COLS <= 256 ? 256u : 512u);
     static_assert(COLS <= 512, "tensor memory");
@@ -284,8 +293,37 @@ template <> struct Pair2<__half> {
     }
 };
 
-// Row sums of one stage (4 rows per warp) reduced across the warp with a transposing
-// butterfly (6 shuffles); entry e = 2*bit4 + bit3 of the lane id is row r4 + e.
+// Row sums of one stage (8 rows per warp) reduced across the warp with a transposing
+// butterfly (9 shuffles); entry e = 4*bit4 + 2*bit3 + bit2 of the lane id is row r8 + e.
+__device__ __forceinline__ void tc_flush_rows(float (&v)[8], long long r8, long long r1, float *rp, int Q, int lane)
+{
+    const unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool hi = lane & 16;
+        const float send = hi ? v[i] : v[i + 4], keep = hi ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(full, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool hi = lane & 8;
+        const float send = hi ? v[i] : v[i + 2], keep = hi ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(full, send, 8);
+    }
+    {
+        const bool hi = lane & 4;
+        const float send = hi ? v[0] : v[1], keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(full, send, 4);
+    }
+    v[0] += __shfl_xor_sync(full, v[0], 2);
+    v[0] += __shfl_xor_sync(full, v[0], 1);
+    if ((lane & 3) == 0) {
+        const long long row = r8 + ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        if (row < r1) rp[row * Q] = v[0];
+    }
+}
+
+// The same for 4 rows per warp (6 shuffles); entry e = 2*bit4 + bit3 is row r4 + e.
 __device__ __forceinline__ void tc_flush_rows(float (&v)[4], long long r4, long long r1, float *rp, int Q, int lane)
 {
     const unsigned full = 0xffffffffu;
@@ -309,22 +347,23 @@ __device__ __forceinline__ void tc_flush_rows(float (&v)[4], long long r4, long 
     }
 }
 
-// Step 2 on the 4 rows x 2 columns of one consumer thread in one stage.  MASK handles the
+// Step 2 on the RPW rows x 2 columns of one consumer thread in one stage.  MASK handles the
 // diagonal, columns >= N and rows past the segment; SR: stochastic rounding.  nrow points at
 // theta^(1)_l[first row][col0].  Outputs: theta^T for MMA2 (TF32 hi/lo when SPLIT), row sums.
 template <typename TS, int NP, bool SR, bool MASK>
 __device__ __forceinline__ void tc_rows(const TS *tcur, const TS *tprv, const float *rec, int rb, int m, long long r,
                                         long long r1, long long col0, bool va, bool vb, f2 ccol,
-                                        const float (&de)[kTcRPW], const float (&dd)[kTcRPW], f2 beta2, f2 ninvL2,
-                                        float invL, uint32_t hcol, float scl, float iscl, f2 iscl2, TS *nrow,
-                                        long long ld, float (&ae)[kTcRPW], float (&ao)[kTcRPW],
-                                        float (&le)[kTcRPW], float (&lo)[kTcRPW], float (&rs)[kTcRPW])
+                                        const float (&de)[TcShape<TS, NP>::RPW], const float (&dd)[TcShape<TS, NP>::RPW],
+                                        f2 beta2, f2 ninvL2, float invL, uint32_t hcol, float scl, float iscl,
+                                        f2 iscl2, TS *nrow, long long ld, float (&ae)[TcShape<TS, NP>::RPW],
+                                        float (&ao)[TcShape<TS, NP>::RPW], float (&le)[TcShape<TS, NP>::RPW],
+                                        float (&lo)[TcShape<TS, NP>::RPW], float (&rs)[TcShape<TS, NP>::RPW])
 {
     using St = Store<TS>;
     using Sh = TcShape<TS, NP>;
     constexpr int REC = Sh::REC;
 #pragma unroll
-    for (int i = 0; i < kTcRPW; ++i) {
+    for (int i = 0; i < Sh::RPW; ++i) {
         const int rl = rb + i;
         const long long rr = r + rl;
         const float y = rec[rl * REC];
@@ -366,7 +405,8 @@ __device__ __forceinline__ void tc_rows(const TS *tcur, const TS *tprv, const fl
 template <typename TS, int NP>
 __device__ __forceinline__ bool tc_produce(const Params &P, unsigned char *stage0, uint64_t *full, uint64_t *empty,
                                            const RingPos<TcShape<TS, NP>::kStages> &pos, bool reuse,
-                                           const StageCursor &cur, int c, int p, bool blocking, bool &issued)
+                                           const StageCursorT<TcShape<TS, NP>::RS> &cur, int c, int p, bool blocking,
+                                           bool &issued)
 {
     using Sh = TcShape<TS, NP>;
     issued = false;
@@ -378,14 +418,16 @@ __device__ __forceinline__ bool tc_produce(const Params &P, unsigned char *stage
             return true;
         }
     }
-    const int nrows = (int)min((long long)kRS, cur.r1 - cur.r);
+    const int nrows = (int)min((long long)Sh::RS, cur.r1 - cur.r);
     unsigned char *st = stage0 + slot * Sh::stage_bytes;
     const long long blk = cur.r >> 3;
-    mbar_arrive_expect_tx(&full[slot], (uint32_t)(2 * Sh::tile_bytes + (size_t)nrows * Sh::REC * 4 + 2 * Sh::xt_block));
-    tma_load_2d(st, &P.tmap[c], (int)(cur.s * kW), (int)cur.r, &full[slot]);
-    tma_load_2d(st + Sh::tile_bytes, &P.tmap[p], (int)(cur.s * kW), (int)cur.r, &full[slot]);
+    const CUtensorMap *tm = Sh::RS == kRS ? P.tmap : P.tmap32;
+    mbar_arrive_expect_tx(&full[slot], (uint32_t)(2 * Sh::tile_bytes + (size_t)nrows * Sh::REC * 4 +
+                                                  (Sh::RS / 8) * Sh::xt_block));
+    tma_load_2d(st, &tm[c], (int)(cur.s * kW), (int)cur.r, &full[slot]);
+    tma_load_2d(st + Sh::tile_bytes, &tm[p], (int)(cur.s * kW), (int)cur.r, &full[slot]);
     bulk_load(st + Sh::off_rec, P.rowrec + cur.r * Sh::REC, (uint32_t)(nrows * Sh::REC * 4), &full[slot]);
-    bulk_load(st + Sh::off_xt, P.xt_tc + blk * tc_xt_floats(NP), (uint32_t)(2 * Sh::xt_block), &full[slot]);
+    bulk_load(st + Sh::off_xt, P.xt_tc + blk * tc_xt_floats(NP), (uint32_t)((Sh::RS / 8) * Sh::xt_block), &full[slot]);
     issued = true;
     return true;
 }
@@ -436,8 +478,8 @@ __device__ __forceinline__ void tc_mma1(uint32_t tb, const TcDesc &D, int xb, in
     umma_commit(done);
 }
 
-// MMA2 of one stage: D2 (+)= Theta^T [X | 1] for the even and the odd columns, K = 16 rows
-// (two 8-row blocks); theta^T comes from tensor memory (A2 buffer b).
+// MMA2 of one stage: D2 (+)= Theta^T [X | 1] for the even and the odd columns, K = RS rows
+// (RS/8 blocks of 8); theta^T comes from tensor memory (A2 buffer b).
 template <typename TS, int NP>
 __device__ __forceinline__ void tc_mma2(uint32_t tb, const TcDesc &D, int slot, int b, bool first)
 {
@@ -447,13 +489,13 @@ __device__ __forceinline__ void tc_mma2(uint32_t tb, const TcDesc &D, int slot, 
 #pragma unroll
     for (int eo = 0; eo < 2; ++eo) {
         const uint32_t d = tb + Sh::COL_D2 + N2 * eo;
-        const uint32_t a = tb + Sh::COL_A2 + Sh::A2W * b + 16 * eo;
+        const uint32_t a = tb + Sh::COL_A2 + Sh::A2W * b + Sh::RS * eo;
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < Sh::RS / 8; ++s) {
             const uint64_t bh = D.xt[0] + so + s * (Sh::xt_block >> 4), bl = D.xt[1] + so + s * (Sh::xt_block >> 4);
             umma_ts(d, a + 8 * s, bh, Sh::IDESC2, (first && s == 0) ? 0u : 1u);
             umma_ts(d, a + 8 * s, bl, Sh::IDESC2, 1u);
-            if (Sh::SPLIT) umma_ts(d, a + 32 + 8 * s, bh, Sh::IDESC2, 1u);
+            if (Sh::SPLIT) umma_ts(d, a + 2 * Sh::RS + 8 * s, bh, Sh::IDESC2, 1u);
         }
     }
 }
@@ -499,7 +541,7 @@ __device__ __forceinline__ void tc_producer(const Params &P, long long ubeg, lon
     const long long N = P.N;
     unsigned char *stage0 = smem + Sh::off_stage;
     fence_proxy_async();
-    StageCursor pc;
+    StageCursorT<Sh::RS> pc;
     pc.begin(ubeg, uend, N);
     RingPos<S> ppos;
     ppos.init(k0);
@@ -587,7 +629,7 @@ __device__ __forceinline__ void tc_issue_mma2(const Params &P, long long ubeg, l
     const long long N = P.N;
     const uint32_t tb = B.tmem;
     const TcDesc D = tc_descs<TS, NP>(smem);
-    StageCursor mc;
+    StageCursorT<Sh::RS> mc;
     mc.begin(ubeg, uend, N);
     RingPos<S> mpos;
     mpos.init(k0);
@@ -596,7 +638,7 @@ __device__ __forceinline__ void tc_issue_mma2(const Params &P, long long ubeg, l
     for (unsigned long long k = k0; k < kend && ok; ++k) {
         const int slot = mpos.slot;
         const bool first = mc.r == mc.r0;
-        const bool last = mc.r + kRS >= mc.r1;
+        const bool last = mc.r + Sh::RS >= mc.r1;
         const int b = (int)(k % Sh::NA2);
         ok = mbar_wait(P, &full[slot], mpos.phase) && mbar_wait(P, &B.a2full[b], (uint32_t)((k / Sh::NA2) & 1));
         if (ok && first && seg >= 1) ok = mbar_wait(P, &B.d2free, (uint32_t)((seg - 1) & 1));
@@ -641,7 +683,7 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
     unsigned long long nst = 0, nseg = 0, ngrp = 0;
     for (long long u = ubeg; u < uend;) {
         const long long s = u / N, r0 = u - s * N, r1 = min(N, r0 + (uend - u));
-        nst += (unsigned long long)((r1 - r0 + kRS - 1) / kRS);
+        nst += (unsigned long long)((r1 - r0 + Sh::RS - 1) / Sh::RS);
         ngrp += (unsigned long long)((r1 - r0 + kGR - 1) / kGR);
         ++nseg;
         u += r1 - r0;
@@ -666,7 +708,8 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
         const uint32_t rseed = P.seed ^ (uint32_t)ell * 0x632BE5ABu;
         TS *__restrict__ nxt = (TS *)P.theta[p];
         const long long first_stripe = ubeg / N;
-        const int rb = kTcRPW * wg;   // first stage row of this warp
+        constexpr int RS = Sh::RS, RPW = Sh::RPW;
+        const int rb = RPW * wg;   // first stage row of this warp
         RingPos<S> cpos;
         cpos.init(k0);
         unsigned long long k = k0, seg = kseg, gj = kgrp;
@@ -679,21 +722,21 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
             const uint32_t hcol = hash_col((uint32_t)(col0 >> 1), rseed);
             const bool ragged = (s * kW + kW) > N;
             float *rp = P.rowpart + (s * 4 + q);
-            for (long long r = r0; r < r1; r += kRS, ++k, cpos.next()) {
+            for (long long r = r0; r < r1; r += RS, ++k, cpos.next()) {
                 const int slot = cpos.slot;
                 const int b = (int)(k % Sh::NA2);   // theta^T buffer of this stage
                 const int go = (int)((r - r0) % kGR);          // row offset inside the MMA1 group
-                const bool glast = go + kRS == kGR || r + kRS >= r1;
+                const bool glast = go + RS == kGR || r + RS >= r1;
                 const int b1 = (int)(gj & 1);
                 // --- residual dot products from tensor memory (MMA1 of the group) ---
                 if (ok) ok = mbar_wait(P, &full[slot], cpos.phase);
                 if (ok && go == 0) ok = mbar_wait(P, &B.d1full[b1], (uint32_t)((gj >> 1) & 1));
                 ok = __all_sync(0xffffffffu, ok);   // tensor-memory loads and stores are warp-collective
-                float de[kTcRPW], dd[kTcRPW];
+                float de[RPW], dd[RPW];
                 if (ok) {
                     tc_fence_after();
-                    tmem_ld4(tq + Sh::COL_D1 + 2 * kGR * b1 + go + rb, de);
-                    tmem_ld4(tq + Sh::COL_D1 + 2 * kGR * b1 + kGR + go + rb, dd);
+                    tmem_ldv(tq + Sh::COL_D1 + 2 * kGR * b1 + go + rb, de);
+                    tmem_ldv(tq + Sh::COL_D1 + 2 * kGR * b1 + kGR + go + rb, dd);
                     tmem_wait_ld();
                 }
                 if (glast) {
@@ -706,14 +749,14 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
                     ok = mbar_wait(P, &B.a2free[b], (uint32_t)(((k / Sh::NA2) - 1) & 1));
                 ok = __all_sync(0xffffffffu, ok);
                 // --- element-wise Step 2 on 4 rows x 2 columns ---
-                float ae[kTcRPW], ao[kTcRPW], le[kTcRPW], lo[kTcRPW], rs[kTcRPW];
+                float ae[RPW], ao[RPW], le[RPW], lo[RPW], rs[RPW];
                 if (ok) {
                     const unsigned char *st = stage0 + slot * Sh::stage_bytes;
                     const TS *tcur = reinterpret_cast<const TS *>(st);
                     const TS *tprv = reinterpret_cast<const TS *>(st + Sh::tile_bytes);
                     const float *rec = reinterpret_cast<const float *>(st + Sh::off_rec);
                     TS *nrow = nxt + (r + rb) * ld + col0;
-                    const bool fast = !ragged && (r + kRS <= r1) && !(r < s * kW + kW && s * kW < r + kRS);
+                    const bool fast = !ragged && (r + RS <= r1) && !(r < s * kW + kW && s * kW < r + RS);
                     if (sr) {
                         if (fast)
                             tc_rows<TS, NP, true, false>(tcur, tprv, rec, rb, m, r, r1, col0, va, vb, ccol, de, dd,
@@ -735,16 +778,16 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
                     }
                     // theta^T for MMA2 (column k of A = stage row)
                     const uint32_t a2 = tq + Sh::COL_A2 + Sh::A2W * b + rb;
-                    tmem_st4(a2, ae);
-                    tmem_st4(a2 + 16, ao);
+                    tmem_stv(a2, ae);
+                    tmem_stv(a2 + RS, ao);
                     if (Sh::SPLIT) {
-                        tmem_st4(a2 + 32, le);
-                        tmem_st4(a2 + 48, lo);
+                        tmem_stv(a2 + 2 * RS, le);
+                        tmem_stv(a2 + 3 * RS, lo);
                     }
                     tmem_wait_st();
                 } else {
 #pragma unroll
-                    for (int i = 0; i < kTcRPW; ++i) rs[i] = 0.0f;
+                    for (int i = 0; i < RPW; ++i) rs[i] = 0.0f;
                 }
                 tc_fence_before();
                 __syncwarp();

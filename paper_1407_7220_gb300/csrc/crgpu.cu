@@ -633,8 +633,11 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     if (o.pair_engine == CR_PAIR_TENSOR_CORES &&
         (o.record_every > 0 || batch_member || o.driver == CR_DRIVER_PERSISTENT))
         return fail(h, CR_EINVAL, "pair_engine tensor cores: not with record_every > 0, the persistent driver or a batch");
+    // auto: where the tensor-core pass measured faster on a GB300 (16-bit theta from n = 8,
+    // FP32 theta from n = 16; at FP32, n = 10 both run at the same ~70% of HBM)
+    const int tc_from = o.theta_dtype == CR_THETA_F32 ? 16 : 8;
     P.tc = (o.pair_engine == CR_PAIR_TENSOR_CORES ||
-            (o.pair_engine == CR_PAIR_AUTO && h->NP >= 8 && o.record_every <= 0 && !batch_member &&
+            (o.pair_engine == CR_PAIR_AUTO && h->NP >= tc_from && o.record_every <= 0 && !batch_member &&
              o.driver != CR_DRIVER_PERSISTENT))
                ? 1
                : 0;
@@ -689,6 +692,11 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
         CUresult r = encode(&P.tmap[b], tdt, 2, P.theta[b], gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(h, CR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        // 32-row boxes for the tensor-core pass with a 16-bit theta (its stages are 32 rows)
+        cuuint32_t box32[2] = {(cuuint32_t)crk::kW, 32u};
+        r = encode(&P.tmap32[b], tdt, 2, P.theta[b], gdim, gstride, box32, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(h, CR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     }
     const int REC = rec_floats(h->NP);

@@ -33,12 +33,17 @@ def _recipe(n):
 
 def test_engine_selection(crg):
     X, yb, _ = datagen.make("maxaff", N=300, n=10)
-    assert crg.Solver(X, yb).info()["engine"] == "tensor_cores"
+    assert crg.Solver(X, yb, theta_dtype="bf16").info()["engine"] == "tensor_cores"
+    assert crg.Solver(X, yb).info()["engine"] == "cuda_cores"          # FP32, n = 10
+    X16, y16, _ = datagen.make("lse", N=300, n=16)
+    assert crg.Solver(X16, y16).info()["engine"] == "tensor_cores"     # FP32, n = 16
+    assert crg.Solver(X, yb, pair_engine=crg.PAIR_TENSOR_CORES).info()["engine"] == "tensor_cores"
     assert crg.Solver(X, yb, pair_engine=crg.PAIR_CUDA_CORES).info()["engine"] == "cuda_cores"
+    assert crg.Solver(X, yb, theta_dtype="bf16", driver=crg.DRIVER_PERSISTENT).info()["engine"] == "cuda_cores"
     assert crg.Solver(X, yb, record_every=10).info()["engine"] == "cuda_cores"
-    assert crg.Solver(X, yb, driver=crg.DRIVER_PERSISTENT).info()["engine"] == "cuda_cores"
-    with pytest.raises(crg.CrError):
-        crg.Solver(X, yb, driver=crg.DRIVER_PERSISTENT, pair_engine=crg.PAIR_TENSOR_CORES)
+    for bad in (dict(driver=crg.DRIVER_PERSISTENT), dict(record_every=10)):
+        with pytest.raises(crg.CrError):
+            crg.Solver(X, yb, pair_engine=crg.PAIR_TENSOR_CORES, **bad)
     X5, y5, _ = datagen.make("sumexp", N=300, n=5)
     assert crg.Solver(X5, y5).info()["engine"] == "cuda_cores"
     assert crg.Solver(X5, y5, pair_engine=crg.PAIR_TENSOR_CORES).info()["engine"] == "tensor_cores"
@@ -86,8 +91,9 @@ def test_16bit_storage_matches_oracle(crg, dtype, tol):
 def test_partitions_give_same_iterates(crg, grid):
     # one CTA walks every stripe (Xi reloaded at each segment); more CTAs split stripes
     X, yb, _ = datagen.make("maxaff", N=1201, n=10)
-    ref = crg.Solver(X, yb, stochastic_round=0, restart=0, grid=64)
-    s = crg.Solver(X, yb, stochastic_round=0, restart=0, grid=grid)
+    tc = crg.PAIR_TENSOR_CORES
+    ref = crg.Solver(X, yb, stochastic_round=0, restart=0, grid=64, pair_engine=tc)
+    s = crg.Solver(X, yb, stochastic_round=0, restart=0, grid=grid, pair_engine=tc)
     assert s.info()["engine"] == "tensor_cores"
     ref.iterate(15)
     s.iterate(15)
@@ -106,7 +112,7 @@ def test_deterministic_with_stochastic_rounding(crg):
 
 def test_solve_reaches_fp64_confirmed_kkt(crg):
     X, yb, _ = datagen.make("maxaff", N=800, n=10)
-    tc = crg.Solver(X, yb, gamma=0.1, stochastic_round=1, restart=0, kkt_every=50)
+    tc = crg.Solver(X, yb, gamma=0.1, stochastic_round=1, restart=0, kkt_every=50, pair_engine=crg.PAIR_TENSOR_CORES)
     cc = crg.Solver(X, yb, gamma=0.1, stochastic_round=1, restart=0, kkt_every=50, pair_engine=crg.PAIR_CUDA_CORES)
     conv, _ = tc.solve(1e-3, 200_000)
     assert conv and tc.kkt_residual()["kkt"] <= 1e-3
