@@ -160,6 +160,22 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+# DRAM bytes per pair update of the pair pass, dram__bytes_read.sum + dram__bytes_write.sum from
+# one ncu capture of the same kernel on a smaller case of the same recipe, divided by its
+# N(N-1) pair updates (the per-stage vectors make the excess over 3 b proportional to the
+# pairs); keyed by (engine, theta dtype, padded n).  A kernel change invalidates an entry.
+TRAFFIC_BYTES_PER_PAIR = {
+    ("cuda_cores", "f32", 10): (519.277056e6 + 225.008896e6) / (8000 * 7999),
+    ("tensor_cores", "bf16", 20): (752.8384e6 + 280.665344e6) / (12000 * 11999),
+}
+
+
+def traffic_per_launch(engine: str, dtype: str, n: int, pairs: int):
+    npad = next(p for p in (2, 4, 5, 8, 10, 16, 20, 32) if p >= n)
+    per = TRAFFIC_BYTES_PER_PAIR.get((engine, dtype, npad))
+    return None if per is None else per * pairs
+
+
 def run_ours(args):
     import torch
     import paper_1407_7220_gb300 as crg
@@ -198,6 +214,7 @@ def run_ours(args):
     ms = dist_max(ev0.elapsed_time(ev1), dev)
     pair_ms, pair_n = s.profile(crg.PROFILE_PAIR)
     fold_ms, fold_n = s.profile(crg.PROFILE_FOLD)
+    engine = s.info()["engine"]
     pers_ms, pers_n = s.profile(crg.PROFILE_PERSISTENT)
     kkt_ms, kkt_n = s.profile(crg.PROFILE_KKT)
     launches = pair_n + fold_n + pers_n + kkt_n
@@ -249,9 +266,10 @@ def run_ours(args):
                                    f"gamma={GAMMA}, stochastic rounding, plain P-APG momentum",
                        "N": N, "n": n, "gamma": GAMMA, "theta_bytes": b, "driver": info and args.driver,
                        "l2": "inputs larger than L2 (2 theta arrays of %.2f GB)" % (pairs * b / 1e9),
-                       "parallelism": f"replicas x{ws}"},
+                       "parallelism": f"replicas x{ws}", "pair_engine": engine},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / peak, "traffic": traffic_per_launch(engine, args.dtype, n, pairs),
+                         "peak_kind": peak_kind,
                          "kernel": dom_name, "algorithmic_bytes_per_launch": alg_bytes},
             "hbm_frac_whole_step": (3 * b * pairs * args.steps / (ms / 1e3) / 1e9) / peak,
             "e2e": {"value": ws * pairs * args.steps / e2e_s, "unit": "pair-updates/s",
@@ -323,15 +341,18 @@ def run_lse(args):
     with Clocks(0) as clk:
         _, dt = _sync_time(lambda: s.iterate(args.steps))
     pair_ms, pair_n = s.profile(crg.PROFILE_PAIR)
+    engine = s.info()["engine"]
     y16, _ = s.solution()
     s.close()
     pairs = N * (N - 1)
     line = {"metric": "pair-updates/s", "value": pairs * args.steps / dt, "unit": "pair-updates/s",
             "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "dtype": dt_, "data": "synthetic",
-            "config": {"workload": f"lse recipe N={N} n={n} gamma={GAMMA}, {dt_} theta (2 x {pairs * 2 / 1e9:.0f} GB)"},
+            "config": {"workload": f"lse recipe N={N} n={n} gamma={GAMMA}, {dt_} theta (2 x {pairs * 2 / 1e9:.0f} GB)",
+                       "pair_engine": engine},
             "roofline": {"bound": "hbm", "achieved": 3 * 2 * pairs / (pair_ms / pair_n / 1e3) / 1e9,
-                         "peak": peaks()[0], "unit": "GB/s"},
+                         "peak": peaks()[0], "unit": "GB/s",
+                         "traffic": traffic_per_launch(engine, dt_, n, pairs)},
             "clocks": clk.summary()}
     line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
     if not args.no_cpu_baseline:
