@@ -153,15 +153,19 @@ __host__ __device__ constexpr size_t tc_xi_floats(int NP) { return (size_t)2 * 2
 __host__ __device__ constexpr size_t tc_xr_floats(int NP) { return (size_t)2 * tc_kp(NP) * 8; }          // per 8-row block
 __host__ __device__ constexpr size_t tc_xt_floats(int NP) { return (size_t)2 * tc_n2(NP) * 8; }          // per 8-row block
 
-constexpr int kGR = 64;   // rows of one MMA1 group (kGR / RS stages)
+constexpr int kGR = 64;   // largest MMA1 group (rows); the X arrays carry kGR rows of padding
 
 template <typename TS, int NP> struct TcShape {
     static constexpr int KP = tc_kp(NP);
     static constexpr int N2 = tc_n2(NP);
     static constexpr bool SPLIT = std::is_same<TS, float>::value;   // FP32 theta needs a hi/lo split
-    static constexpr int RS = SPLIT ? 16 : 32;                        // rows of a stage
+    // rows of a stage: 32 for a 16-bit theta; 16 for FP32 (two 32-row FP32 stages left too
+    // shallow a ring: 1.07 vs 1.05 ms per pass at N = 20,000, n = 10)
+    static constexpr int RS = SPLIT ? 16 : 32;
     static constexpr int RPW = RS / kTcWG;                            // rows of a stage per consumer warp
-    static_assert(kGR % RS == 0 && RS % 8 == 0 && (RPW == 4 || RPW == 8), "stage split");
+    // rows of one MMA1 group (N of MMA1): an MMA with N = 64 costs about what N = 16 does
+    static constexpr int GR = kGR;
+    static_assert(GR % RS == 0 && GR <= kGR && RS % 8 == 0 && (RPW == 4 || RPW == 8), "stage split");
     static constexpr int REC = RecLayout<NP>::REC;
     static constexpr size_t tile_bytes = (size_t)RS * kW * sizeof(TS);
     static constexpr size_t rec_bytes = (size_t)RS * REC * sizeof(float);
@@ -171,7 +175,7 @@ template <typename TS, int NP> struct TcShape {
     static constexpr size_t off_xt = off_rec + rec_bytes;
     static constexpr size_t stage_bytes = off_xt + (RS / 8) * xt_block;
     static constexpr size_t xi_bytes = tc_xi_floats(NP) * 4;
-    static constexpr size_t xg_bytes = (kGR / 8) * xr_block;   // X rows of one group
+    static constexpr size_t xg_bytes = (GR / 8) * xr_block;    // X rows of one group
     static constexpr size_t off_xg = xi_bytes;                  // 2 group buffers
     static constexpr size_t off_stage = xi_bytes + 2 * xg_bytes;
     static constexpr int kFit = (int)((kSmemBudget - 128 - off_stage) / stage_bytes);
@@ -183,7 +187,7 @@ template <typename TS, int NP> struct TcShape {
     // tensor-memory columns: D1 (2 group buffers x {even, odd} x 64 rows), A2 = theta^T
     // (NA2 buffers x {even hi, odd hi[, even lo, odd lo]} x RS), D2 ({even, odd} x N2)
     static constexpr int A2W = (SPLIT ? 4 : 2) * RS;
-    static constexpr int COL_A2 = 4 * kGR;
+    static constexpr int COL_A2 = 4 * GR;
     static constexpr int NA2_FIT = (512 - COL_A2 - 2 * N2) / A2W;
     static constexpr int NA2 = NA2_FIT > 4 ? 4 : NA2_FIT;   // theta^T buffers (what fits in 512 columns)
     static_assert(NA2 >= 2, "tensor memory");
@@ -191,7 +195,7 @@ template <typename TS, int NP> struct TcShape {
     static constexpr int COLS = COL_D2 + 2 * N2;
     static constexpr uint32_t NCOLS = COLS <= 128 ? 128u : (COLS <= 256 ? 256u : 512u);
     static_assert(COLS <= 512, "tensor memory");
-    static constexpr uint32_t IDESC1 = umma_idesc_tf32(128, kGR);
+    static constexpr uint32_t IDESC1 = umma_idesc_tf32(128, GR);
     static constexpr uint32_t IDESC2 = umma_idesc_tf32(128, N2);
 };
 
@@ -421,13 +425,15 @@ __device__ __forceinline__ bool tc_produce(const Params &P, unsigned char *stage
     const int nrows = (int)min((long long)Sh::RS, cur.r1 - cur.r);
     unsigned char *st = stage0 + slot * Sh::stage_bytes;
     const long long blk = cur.r >> 3;
-    const CUtensorMap *tm = Sh::RS == kRS ? P.tmap : P.tmap32;
+    const CUtensorMap *tm = Sh::RS == kRS ? P.tmap : P.tmap32;   // box of RS rows
     mbar_arrive_expect_tx(&full[slot], (uint32_t)(2 * Sh::tile_bytes + (size_t)nrows * Sh::REC * 4 +
                                                   (Sh::RS / 8) * Sh::xt_block));
+    const uint64_t keep = l2_evict_last();
     tma_load_2d(st, &tm[c], (int)(cur.s * kW), (int)cur.r, &full[slot]);
     tma_load_2d(st + Sh::tile_bytes, &tm[p], (int)(cur.s * kW), (int)cur.r, &full[slot]);
-    bulk_load(st + Sh::off_rec, P.rowrec + cur.r * Sh::REC, (uint32_t)(nrows * Sh::REC * 4), &full[slot]);
-    bulk_load(st + Sh::off_xt, P.xt_tc + blk * tc_xt_floats(NP), (uint32_t)((Sh::RS / 8) * Sh::xt_block), &full[slot]);
+    bulk_load_hint(st + Sh::off_rec, P.rowrec + cur.r * Sh::REC, (uint32_t)(nrows * Sh::REC * 4), &full[slot], keep);
+    bulk_load_hint(st + Sh::off_xt, P.xt_tc + blk * tc_xt_floats(NP), (uint32_t)((Sh::RS / 8) * Sh::xt_block),
+                   &full[slot], keep);
     issued = true;
     return true;
 }
@@ -467,7 +473,7 @@ __device__ __forceinline__ void tc_mma1(uint32_t tb, const TcDesc &D, int xb, in
     using Sh = TcShape<TS, NP>;
 #pragma unroll
     for (int eo = 0; eo < 2; ++eo) {
-        const uint32_t d = tb + Sh::COL_D1 + 2 * kGR * b + kGR * eo;
+        const uint32_t d = tb + Sh::COL_D1 + 2 * Sh::GR * b + Sh::GR * eo;
 #pragma unroll
         for (int s = 0; s < Sh::KP / 8; ++s) {
             umma_ss(d, D.xi[eo][0] + 16 * s, D.xg[xb][0] + 16 * s, Sh::IDESC1, s > 0 ? 1u : 0u);
@@ -500,8 +506,8 @@ __device__ __forceinline__ void tc_mma2(uint32_t tb, const TcDesc &D, int slot, 
     }
 }
 
-// Walks the MMA1 groups (kGR rows of one stripe) of a unit range in consumption order.
-struct GroupCursor {
+// Walks the MMA1 groups (GR rows of one stripe) of a unit range in consumption order.
+template <int GR> struct GroupCursor {
     long long u, uend, s, r0, r1, r;
     __device__ __forceinline__ void begin(long long u0, long long ue, long long N)
     {
@@ -520,7 +526,7 @@ struct GroupCursor {
     __device__ __forceinline__ bool valid() const { return u < uend; }
     __device__ __forceinline__ void advance(long long N)
     {
-        r += kGR;
+        r += GR;
         if (r >= r1) {
             u += r1 - r0;
             next_segment(N);
@@ -558,7 +564,7 @@ __device__ __forceinline__ void tc_producer(const Params &P, long long ubeg, lon
                 mbar_arrive_expect_tx(&B.xifull, (uint32_t)Sh::xi_bytes);
                 bulk_load(smem, P.xi_tc + (size_t)pc.s * tc_xi_floats(NP), (uint32_t)Sh::xi_bytes, &B.xifull);
             }
-            gseg += (unsigned long long)((pc.r1 - pc.r0 + kGR - 1) / kGR);
+            gseg += (unsigned long long)((pc.r1 - pc.r0 + Sh::GR - 1) / Sh::GR);
         }
         bool issued;
         if (ok) ok = tc_produce<TS, NP>(P, stage0, full, empty, ppos, k >= (unsigned long long)S, pc, c, p, true, issued);
@@ -578,7 +584,7 @@ __device__ __forceinline__ void tc_issue_mma1(const Params &P, long long ubeg, l
     const uint32_t tb = B.tmem;
     const TcDesc D = tc_descs<TS, NP>(smem);
     fence_proxy_async();
-    GroupCursor gc, xc;   // group to compute, group whose X rows to load
+    GroupCursor<Sh::GR> gc, xc;   // group to compute, group whose X rows to load
     gc.begin(ubeg, uend, N);
     xc.begin(ubeg, uend, N);
     unsigned long long g = g0, gload = g0, seg = seg0;
@@ -590,8 +596,8 @@ __device__ __forceinline__ void tc_issue_mma1(const Params &P, long long ubeg, l
         if (gload >= g0 + 2) ok = mbar_wait(P, &B.d1full[xb], (uint32_t)(((gload >> 1) - 1) & 1));
         if (!ok) return;
         mbar_arrive_expect_tx(&B.xgfull[xb], (uint32_t)Sh::xg_bytes);
-        bulk_load(smem + Sh::off_xg + xb * Sh::xg_bytes, P.xr_tc + (size_t)(xc.r >> 3) * tc_xr_floats(NP),
-                  (uint32_t)Sh::xg_bytes, &B.xgfull[xb]);
+        bulk_load_hint(smem + Sh::off_xg + xb * Sh::xg_bytes, P.xr_tc + (size_t)(xc.r >> 3) * tc_xr_floats(NP),
+                       (uint32_t)Sh::xg_bytes, &B.xgfull[xb], l2_evict_last());
         xc.advance(N);
         ++gload;
     };
@@ -684,7 +690,7 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
     for (long long u = ubeg; u < uend;) {
         const long long s = u / N, r0 = u - s * N, r1 = min(N, r0 + (uend - u));
         nst += (unsigned long long)((r1 - r0 + Sh::RS - 1) / Sh::RS);
-        ngrp += (unsigned long long)((r1 - r0 + kGR - 1) / kGR);
+        ngrp += (unsigned long long)((r1 - r0 + Sh::GR - 1) / Sh::GR);
         ++nseg;
         u += r1 - r0;
     }
@@ -725,8 +731,8 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
             for (long long r = r0; r < r1; r += RS, ++k, cpos.next()) {
                 const int slot = cpos.slot;
                 const int b = (int)(k % Sh::NA2);   // theta^T buffer of this stage
-                const int go = (int)((r - r0) % kGR);          // row offset inside the MMA1 group
-                const bool glast = go + RS == kGR || r + RS >= r1;
+                const int go = (int)((r - r0) % Sh::GR);       // row offset inside the MMA1 group
+                const bool glast = go + RS == Sh::GR || r + RS >= r1;
                 const int b1 = (int)(gj & 1);
                 // --- residual dot products from tensor memory (MMA1 of the group) ---
                 if (ok) ok = mbar_wait(P, &full[slot], cpos.phase);
@@ -735,8 +741,8 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
                 float de[RPW], dd[RPW];
                 if (ok) {
                     tc_fence_after();
-                    tmem_ldv(tq + Sh::COL_D1 + 2 * kGR * b1 + go + rb, de);
-                    tmem_ldv(tq + Sh::COL_D1 + 2 * kGR * b1 + kGR + go + rb, dd);
+                    tmem_ldv(tq + Sh::COL_D1 + 2 * Sh::GR * b1 + go + rb, de);
+                    tmem_ldv(tq + Sh::COL_D1 + 2 * Sh::GR * b1 + Sh::GR + go + rb, dd);
                     tmem_wait_ld();
                 }
                 if (glast) {

@@ -693,7 +693,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(h, CR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-        // 32-row boxes for the tensor-core pass with a 16-bit theta (its stages are 32 rows)
+        // 32-row boxes for the tensor-core pass (its stages are 32 rows)
         cuuint32_t box32[2] = {(cuuint32_t)crk::kW, 32u};
         r = encode(&P.tmap32[b], tdt, 2, P.theta[b], gdim, gstride, box32, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
