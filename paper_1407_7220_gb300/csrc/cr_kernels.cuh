@@ -82,6 +82,7 @@ struct Params {
     int G;              // CTAs of the grid
     int slots;          // column-partial slots per CTA
     long long total;    // S * N units
+    const long long *ubeg;  // G + 1 entries: first unit of every CTA (host-computed partition)
     // constants
     double gamma, inv_gamma, L, invL_d, shift, sigma;
     float invL;
@@ -538,14 +539,10 @@ __device__ __forceinline__ bool grid_barrier(const Params &P, unsigned long long
 }
 
 // CTA c's unit range [u0, u1) of the stripe-major (stripe, row) order.
-// First (stripe, row) unit of CTA c: an even split of the S*N units, each segment starting
-// on an 8-row boundary (whole 8-row blocks for the tensor-core operands).
-__device__ __forceinline__ long long unit_begin(const Params &P, long long c)
-{
-    const long long u = (long long)(((unsigned long long)c * (unsigned long long)P.total) / (unsigned long long)P.G);
-    const long long s = u / P.N;
-    return s * P.N + ((u - s * P.N) & ~7ll);
-}
+// First (stripe, row) unit of CTA c (c <= G): an even split of the S*N units, each segment
+// starting on an 8-row boundary (whole 8-row blocks for the tensor-core operands).  The host
+// computes the table once per partition (no 64-bit division on the device).
+__device__ __forceinline__ long long unit_begin(const Params &P, long long c) { return __ldg(P.ubeg + c); }
 
 // Bounded mbarrier phase wait: gives up (and sets the error word) after the
 // barrier bound, or at once when another CTA already reported an error.
@@ -1002,6 +999,19 @@ __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, 
     __syncthreads();
 }
 
+// Compensated FP32 accumulation: (hi, lo) with hi + lo the running sum; each FP32 term is
+// added exactly to hi by Knuth's TwoSum and its rounding error collected in lo.  About 2^-48
+// relative for the sums of FP32 partials here, on the FP32 pipe (GB300's FP64 pipe is ~30x
+// narrower); read back as (double)hi + (double)lo.
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float b)
+{
+    const float s = hi + b;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (b - bb);
+    hi = s;
+}
+__device__ __forceinline__ double ff_value(float hi, float lo) { return (double)hi + (double)lo; }
+
 // ---------------------------------------------------------------------------
 // foldA(l): reduce partials of theta^(1)_l in FP64; eta(theta^(1)_l); dual terms
 // ---------------------------------------------------------------------------
@@ -1016,21 +1026,25 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red, long lo
     for (long long l = vc * kThreads + threadIdx.x; l < N; l += (long long)P.G * kThreads) {
         // row sum: the Q (>= 2S, zero padded) contiguous partials of row l, independent 16-byte loads
         const float4 *rp4 = reinterpret_cast<const float4 *>(P.rowpart + l * P.Q);
-        double R = 0.0;
+        float rh = 0.0f, rl = 0.0f;
 #pragma unroll 8
         for (int q = 0; q < Q4; ++q) {
             const float4 t = __ldcg(rp4 + q);
-            R += ((double)t.x + (double)t.y) + ((double)t.z + (double)t.w);
+            ff_add(rh, rl, t.x);
+            ff_add(rh, rl, t.y);
+            ff_add(rh, rl, t.z);
+            ff_add(rh, rl, t.w);
         }
+        const double R = ff_value(rh, rl);
         const long long s = l / kW, cl = l - s * kW;
         // CTAs whose unit range intersects stripe s, ascending
         const long long ua = s * N, ub = s * N + N - 1;
         long long c0 = (long long)(((unsigned long long)ua * (unsigned long long)P.G) / (unsigned long long)P.total);
         while (c0 > 0 && unit_begin(P, c0) > ua) --c0;
         while (c0 + 1 < P.G && unit_begin(P, c0 + 1) <= ua) ++c0;
-        double Cc = 0.0, TX[NP];
+        float ch = 0.0f, clo = 0.0f, th[NP], tl[NP];
 #pragma unroll
-        for (int k = 0; k < NP; ++k) TX[k] = 0.0;
+        for (int k = 0; k < NP; ++k) th[k] = tl[k] = 0.0f;
         long long ubg = unit_begin(P, c0);
         for (long long cta = c0; cta < P.G && ubg <= ub; ++cta) {
             const long long unx = unit_begin(P, cta + 1);
@@ -1039,13 +1053,17 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red, long lo
                 const float *cp0 = P.colpart + ((cta * P.slots + (s - fs)) * P.cgroups * (NP + 1)) * kW + cl;
                 for (int g = 0; g < P.cgroups; ++g) {
                     const float *cp = cp0 + g * (NP + 1) * kW;
-                    Cc += (double)__ldcg(cp);
+                    ff_add(ch, clo, __ldcg(cp));
 #pragma unroll
-                    for (int k = 0; k < NP; ++k) TX[k] += (double)__ldcg(cp + (1 + k) * kW);
+                    for (int k = 0; k < NP; ++k) ff_add(th[k], tl[k], __ldcg(cp + (1 + k) * kW));
                 }
             }
             ubg = unx;
         }
+        const double Cc = ff_value(ch, clo);
+        double TX[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) TX[k] = ff_value(th[k], tl[k]);
         const double v = R - Cc;               // (A_1^T theta)_l = row sum - column sum
         P.v[p][l] = v;
         const double hl = __ldg(P.h + l), mu = __ldcg(P.mu[p] + l);

@@ -288,6 +288,16 @@ long long unit_begin_host(long long c, long long total, long long N, int G)
     return s * N + ((u - s * N) & ~7ll);
 }
 
+// The device's partition table: first unit of every CTA (G + 1 entries, capacity cap).
+cr_status upload_partition(cr_ctx *h, long long *dtab)
+{
+    const Params &P = h->P;
+    std::vector<long long> t((size_t)P.G + 1);
+    for (long long c = 0; c <= P.G; ++c) t[c] = unit_begin_host(c, P.total, P.N, P.G);
+    CR_CUDA(h, cudaMemcpy(dtab, t.data(), sizeof(long long) * t.size(), cudaMemcpyHostToDevice));
+    return CR_OK;
+}
+
 // Work partition of the pair pass: the number of column-partial slots per CTA.
 int max_slots(long long total, long long N, int G)
 {
@@ -720,6 +730,12 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     }
     CR_TRY(dev_alloc(h, &P.rowpart, (size_t)P.Q * N));
     CR_TRY(dev_alloc(h, &P.colpart, (size_t)G * P.slots * P.cgroups * (h->NP + 1) * crk::kW));
+    {
+        long long *tab = nullptr;
+        CR_TRY(dev_alloc(h, &tab, (size_t)G + 1));
+        P.ubeg = tab;
+        CR_TRY(upload_partition(h, tab));
+    }
     CR_TRY(dev_alloc(h, &P.foldpart, (size_t)G * 8));
     CR_TRY(dev_alloc(h, &P.kktpart, (size_t)G * 8));
     CR_TRY(dev_alloc(h, &P.st, 1));
@@ -1255,6 +1271,7 @@ cr_status batch_plan(cr_batch_ctx *b, int f)
         const long long G = std::max<long long>(1, b->Gfine[i] / f);
         h->P.G = (int)G;
         h->P.slots = max_slots(h->P.total, h->N, (int)G);
+        CR_TRY(upload_partition(h, const_cast<long long *>(h->P.ubeg)));   // capacity: the finest grid
         hp[i] = h->P;
         const double pairs = (double)h->N * (double)(h->N - 1);
         for (long long v = 0; v < G; ++v) items.push_back({i, (int)v, pairs / (double)G + 2.0e4});
