@@ -28,6 +28,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace crk {
 
 constexpr int kThreads = 256;   // 8 warps per CTA
@@ -1051,12 +1053,28 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red, long lo
             if (unx > ubg) {
                 const long long fs = ubg / N;
                 const float *cp0 = P.colpart + ((cta * P.slots + (s - fs)) * P.cgroups * (NP + 1)) * kW + cl;
-                for (int g = 0; g < P.cgroups; ++g) {
-                    const float *cp = cp0 + g * (NP + 1) * kW;
-                    ff_add(ch, clo, __ldcg(cp));
+                // all (group, component) loads of one segment are independent: issue them together
+                auto add_groups = [&](auto G) {
+                    constexpr int NG = decltype(G)::value;
+                    float cv[NG], tv[NG][NP];
 #pragma unroll
-                    for (int k = 0; k < NP; ++k) ff_add(th[k], tl[k], __ldcg(cp + (1 + k) * kW));
-                }
+                    for (int g = 0; g < NG; ++g) {
+                        const float *cp = cp0 + g * (NP + 1) * kW;
+                        cv[g] = __ldcg(cp);
+#pragma unroll
+                        for (int k = 0; k < NP; ++k) tv[g][k] = __ldcg(cp + (1 + k) * kW);
+                    }
+#pragma unroll
+                    for (int g = 0; g < NG; ++g) {
+                        ff_add(ch, clo, cv[g]);
+#pragma unroll
+                        for (int k = 0; k < NP; ++k) ff_add(th[k], tl[k], tv[g][k]);
+                    }
+                };
+                if (P.cgroups == kWR)
+                    add_groups(std::integral_constant<int, kWR>());
+                else
+                    add_groups(std::integral_constant<int, 1>());
             }
             ubg = unx;
         }
