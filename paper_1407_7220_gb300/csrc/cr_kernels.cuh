@@ -90,6 +90,7 @@ struct Params {
     float invL;
     float st_scale, st_inv_scale;   // theta storage scale (FP16 only; 1 otherwise)
     int momentum, restart, sr;
+    int fuse;           // 1: foldA(l) also performs foldB(l+1) (plain P-APG: beta needs no reduction)
     double restart_tol;
     unsigned int seed;
     unsigned long long bar_timeout_ns;   // bound of every grid-barrier wait
@@ -565,6 +566,76 @@ __device__ __forceinline__ bool mbar_wait(const Params &P, uint64_t *bar, uint32
 // ---------------------------------------------------------------------------
 // foldB(l): Step 1 at theta^(2)_l (by linearity), mu update, Steps 3-4 scalars
 // ---------------------------------------------------------------------------
+// Per-row part of foldB (Step 1 at theta^(2) by linearity, Step 2 on the y >= 0 row): slot c
+// holds the latest iterate's aggregates, slot p the previous one's; writes mu[p] and the
+// column data of theta^(2) that the pair pass reads.
+template <int NP>
+__device__ __forceinline__ void foldB_row(const Params &P, int c, int p, long long l, double beta)
+{
+    const double b1 = 1.0 + beta;
+    const int n = P.n;
+    double v2 = b1 * __ldcg(P.v[c] + l) - beta * __ldcg(P.v[p] + l);
+    double mu2 = b1 * __ldcg(P.mu[c] + l) - beta * __ldcg(P.mu[p] + l);
+    double y2 = __ldg(P.h + l) + v2 + mu2;
+    double mun = mu2 - y2 * P.invL_d;     // Step 2 on the y >= 0 rows of C
+    P.mu[p][l] = mun > 0.0 ? mun : 0.0;
+    double ys = y2 - P.shift;
+    double d = 0.0;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        float xf = 0.0f;
+        if (k < n) {
+            double xi = (b1 * __ldcg(P.w[c] + l * n + k) - beta * __ldcg(P.w[p] + l * n + k)) * P.inv_gamma;
+            d += xi * __ldg(P.X64 + l * n + k);
+            xf = (float)xi;
+        }
+        P.xi2[l * NP + k] = xf;
+    }
+    P.rowrec[l * RecLayout<NP>::REC] = (float)ys;
+    P.ccol2[l] = (float)(d - ys);
+    if (P.tc) {
+        // Xi of column l as the A operand of the residual product: stripe l/256, column pair
+        // (l%256)/2 = lane, even/odd column = MMA; TF32 hi and lo parts
+        constexpr int KP = (NP + 7) / 8 * 8;
+        const long long st = l / kW;
+        const int cl = (int)(l - st * kW), eo = cl & 1, mm = cl >> 1;
+        float *base = P.xi_tc + (size_t)st * (2 * 2 * 128 * KP);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const float xf = P.xi2[l * NP + k];
+            uint32_t hb;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(xf));
+            const float hi = __uint_as_float(hb);
+            uint32_t lb;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"(xf - hi));
+            const size_t o = ((size_t)(mm >> 3) * (KP / 4) + (k >> 2)) * 32 + (mm & 7) * 4 + (k & 3);
+            base[(size_t)(eo * 2 + 0) * 128 * KP + o] = hi;
+            base[(size_t)(eo * 2 + 1) * 128 * KP + o] = __uint_as_float(lb);
+        }
+    }
+}
+
+// Momentum scalars of iteration e without the dual-value test (plain P-APG): Fig. 2 steps 3-4.
+__device__ __forceinline__ Scal next_scal_plain(const Params &P, long long e)
+{
+    Scal old;
+    const int c = (int)((e - 1) & 1);
+    old.t = __ldcg(&P.st->scal[c].t);
+    old.dual = __ldcg(&P.st->scal[c].dual);
+    old.beta = __ldcg(&P.st->scal[c].beta);
+    old.restarts = __ldcg(&P.st->scal[c].restarts);
+    Scal nw = old;
+    double beta = 0.0;
+    if (e >= 2) {
+        const double t = old.t;
+        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));   // Fig. 2 step 3
+        beta = P.momentum ? (t - 1.0) / tn : 0.0;                 // Fig. 2 step 4 weight
+        nw.t = tn;
+    }
+    nw.beta = beta;
+    return nw;
+}
+
 template <int NP>
 __device__ void phase_foldB(const Params &P, long long ell, double *red, long long vc)
 {
@@ -609,50 +680,10 @@ __device__ void phase_foldB(const Params &P, long long ell, double *red, long lo
         }
     }
     __syncthreads();
-    const double beta = s_beta, b1 = 1.0 + beta;
+    const double beta = s_beta;
     const long long N = P.N;
-    const int n = P.n;
-    for (long long l = vc * kThreads + threadIdx.x; l < N; l += (long long)P.G * kThreads) {
-        double v2 = b1 * __ldcg(P.v[c] + l) - beta * __ldcg(P.v[p] + l);
-        double mu2 = b1 * __ldcg(P.mu[c] + l) - beta * __ldcg(P.mu[p] + l);
-        double y2 = __ldg(P.h + l) + v2 + mu2;
-        double mun = mu2 - y2 * P.invL_d;     // Step 2 on the y >= 0 rows of C
-        P.mu[p][l] = mun > 0.0 ? mun : 0.0;
-        double ys = y2 - P.shift;
-        double d = 0.0;
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            float xf = 0.0f;
-            if (k < n) {
-                double xi = (b1 * __ldcg(P.w[c] + l * n + k) - beta * __ldcg(P.w[p] + l * n + k)) * P.inv_gamma;
-                d += xi * __ldg(P.X64 + l * n + k);
-                xf = (float)xi;
-            }
-            P.xi2[l * NP + k] = xf;
-        }
-        P.rowrec[l * RecLayout<NP>::REC] = (float)ys;
-        P.ccol2[l] = (float)(d - ys);
-        if (P.tc) {
-            // Xi of column l as the A operand of the residual product: stripe l/256, column pair
-            // (l%256)/2 = lane, even/odd column = MMA; TF32 hi and lo parts
-            constexpr int KP = (NP + 7) / 8 * 8;
-            const long long st = l / kW;
-            const int cl = (int)(l - st * kW), eo = cl & 1, mm = cl >> 1;
-            float *base = P.xi_tc + (size_t)st * (2 * 2 * 128 * KP);
-#pragma unroll
-            for (int k = 0; k < NP; ++k) {
-                const float xf = P.xi2[l * NP + k];
-                uint32_t hb;
-                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(xf));
-                const float hi = __uint_as_float(hb);
-                uint32_t lb;
-                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"(xf - hi));
-                const size_t o = ((size_t)(mm >> 3) * (KP / 4) + (k >> 2)) * 32 + (mm & 7) * 4 + (k & 3);
-                base[(size_t)(eo * 2 + 0) * 128 * KP + o] = hi;
-                base[(size_t)(eo * 2 + 1) * 128 * KP + o] = __uint_as_float(lb);
-            }
-        }
-    }
+    for (long long l = vc * kThreads + threadIdx.x; l < N; l += (long long)P.G * kThreads)
+        foldB_row<NP>(P, c, p, l, beta);
 }
 
 // ---------------------------------------------------------------------------
@@ -1024,6 +1055,16 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red, long lo
     const long long N = P.N;
     const int n = P.n;
     const int Q4 = P.Q >> 2;   // row partials per row, in float4 units
+    // fused foldB(l+1): its momentum weight needs no reduction in plain P-APG
+    __shared__ double s_nbeta;
+    if (P.fuse) {
+        if (threadIdx.x == 0) {
+            const Scal nw = next_scal_plain(P, ell + 1);
+            s_nbeta = nw.beta;
+            if (vc == 0) P.st->scal[(ell + 1) & 1] = nw;
+        }
+        __syncthreads();
+    }
     double a = 0.0, b = 0.0, cc = 0.0, mviol = 0.0, mcomp = 0.0, sviol = 0.0, smuy = 0.0;
     for (long long l = vc * kThreads + threadIdx.x; l < N; l += (long long)P.G * kThreads) {
         // row sum: the Q (>= 2S, zero padded) contiguous partials of row l, independent 16-byte loads
@@ -1115,6 +1156,7 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red, long lo
         if (y < 0.0) sviol += y * y;
         smuy += mu * y;
         if (!isfinite(y) || !isfinite(d)) atomicCAS(&P.st->error, 0, ERR_NUMERIC);
+        if (P.fuse) foldB_row<NP>(P, p, p ^ 1, l, s_nbeta);   // this row of foldB(l+1)
     }
     double vals[7] = {a, b, cc, mviol, mcomp, sviol, smuy};
     const bool ismax[7] = {false, false, false, true, true, false, false};

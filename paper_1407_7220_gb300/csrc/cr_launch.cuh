@@ -41,12 +41,14 @@ __device__ __forceinline__ void init_pipeline(uint64_t *full, uint64_t *empty)
 // FP64 confirmation) every check_every iterations and at ell1.
 template <typename TS, int NP>
 __device__ __forceinline__ void persistent_body(const Params &P, long long ell0, long long ell1, int check_every,
-                                                double tol, double sigma, unsigned char *sm, double *red, double *s_m,
-                                                uint64_t *full, uint64_t *empty)
+                                                double tol, double sigma, int first_foldB, unsigned char *sm,
+                                                double *red, double *s_m, uint64_t *full, uint64_t *empty)
 {
     unsigned long long bar = 0, kstage = 0;
-    phase_foldB<NP>(P, ell0, red, blockIdx.x);
-    if (!grid_barrier(P, bar)) return;
+    if (first_foldB) {   // 0 when the previous foldA already performed it (P.fuse)
+        phase_foldB<NP>(P, ell0, red, blockIdx.x);
+        if (!grid_barrier(P, bar)) return;
+    }
     for (long long ell = ell0; ell <= ell1; ++ell) {
         phase_pair<TS, NP>(P, ell, sm, full, empty, kstage, blockIdx.x);
         if (!grid_barrier(P, bar)) return;
@@ -89,7 +91,7 @@ __device__ __forceinline__ void persistent_body(const Params &P, long long ell0,
             }
             if (stop) return;
         }
-        if (ell < ell1) {
+        if (ell < ell1 && !P.fuse) {
             phase_foldB<NP>(P, ell + 1, red, blockIdx.x);
             if (!grid_barrier(P, bar)) return;
         }
@@ -100,7 +102,7 @@ __device__ __forceinline__ void persistent_body(const Params &P, long long ell0,
 template <typename TS, int NP>
 __global__ void __launch_bounds__(kThreads, 1)
 k_persistent(const __grid_constant__ Params P, long long ell0, long long ell1, int check_every, double tol,
-             double sigma)
+             double sigma, int first_foldB)
 {
     extern __shared__ unsigned char sm_raw[];
     unsigned char *sm = aligned_smem(sm_raw);
@@ -108,7 +110,7 @@ k_persistent(const __grid_constant__ Params P, long long ell0, long long ell1, i
     __shared__ double s_m[8];
     __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
     init_pipeline(full, empty);
-    persistent_body<TS, NP>(P, ell0, ell1, check_every, tol, sigma, sm, red, s_m, full, empty);
+    persistent_body<TS, NP>(P, ell0, ell1, check_every, tol, sigma, first_foldB, sm, red, s_m, full, empty);
 }
 
 // One phase of one iteration (the CR_DRIVER_PHASES path and the stand-alone metric

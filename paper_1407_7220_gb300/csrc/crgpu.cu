@@ -49,6 +49,7 @@ struct cr_ctx {
     double sigma = 1.0;
     long long iters = 0;     // iterations completed (host view)
     bool persistent_ok = false;
+    bool prepared = false;   // foldB of iteration iters + 1 already performed (fused into foldA)
     KernelSet ks{};
     Params P{};
     std::vector<void *> allocs;
@@ -362,6 +363,8 @@ cr_status launch_phase(cr_ctx *h, int phase, long long ell, double tol, int grid
         return CR_OK;
     }
     CR_CUDA(h, cudaLaunchKernel(h->ks.phase, dim3(g), dim3(crk::kThreads), args, h->ks.smem, h->stream));
+    if (phase == crk::PH_FOLDA) h->prepared = h->P.fuse != 0;
+    else if (phase == crk::PH_FOLDB) h->prepared = false;
     return CR_OK;
 }
 
@@ -369,10 +372,12 @@ cr_status launch_persistent(cr_ctx *h, long long ell0, long long ell1, int check
 {
     CR_CUDA(h, cudaMemsetAsync(&h->P.st->bar_count, 0, sizeof(unsigned long long), h->stream));
     Params P = h->P;
-    void *args[] = {&P, &ell0, &ell1, &check_every, &tol, &h->sigma};
+    int first_foldB = h->prepared ? 0 : 1;
+    void *args[] = {&P, &ell0, &ell1, &check_every, &tol, &h->sigma, &first_foldB};
     ProfScope ps(h, 3);
     CR_CUDA(h, cudaLaunchCooperativeKernel(h->ks.persistent, dim3(h->P.G), dim3(crk::kThreads), args, h->ks.smem,
                                            h->stream));
+    h->prepared = h->P.fuse != 0;   // its last foldA performed the next foldB
     return CR_OK;
 }
 
@@ -380,9 +385,9 @@ cr_status launch_persistent(cr_ctx *h, long long ell0, long long ell1, int check
 cr_status run_phases(cr_ctx *h, long long ell0, long long ell1, int check_every, double tol)
 {
     for (long long ell = ell0; ell <= ell1; ++ell) {
-        CR_TRY(launch_phase(h, crk::PH_FOLDB, ell, tol));
+        if (!h->prepared) CR_TRY(launch_phase(h, crk::PH_FOLDB, ell, tol));
         CR_TRY(launch_phase(h, crk::PH_PAIR, ell, tol));
-        CR_TRY(launch_phase(h, crk::PH_FOLDA, ell, tol));
+        CR_TRY(launch_phase(h, crk::PH_FOLDA, ell, tol));   // with P.fuse also foldB(ell + 1)
         if (check_every > 0 && ((ell % check_every) == 0 || ell == ell1)) {
             CR_TRY(launch_phase(h, crk::PH_KKT32, ell, tol));
             CR_TRY(launch_phase(h, crk::PH_DECIDE32, ell, tol, 1));
@@ -672,6 +677,9 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     }
     P.momentum = o.momentum;
     P.restart = o.restart;
+    // foldB(l+1) fused into foldA(l): plain P-APG (beta from the t-sequence alone), no recording
+    // (cr_backward restores checkpoints and re-runs foldB), not in a batch
+    P.fuse = (o.restart == 0 && o.record_every <= 0 && np_override <= 0) ? 1 : 0;
     P.restart_tol = o.restart_tol > 0.0 ? o.restart_tol : 0.0;
     P.sr = o.stochastic_round;
     P.seed = (unsigned)(o.seed ^ (o.seed >> 32));
