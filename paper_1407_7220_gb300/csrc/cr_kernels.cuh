@@ -547,6 +547,22 @@ __device__ __forceinline__ bool grid_barrier(const Params &P, unsigned long long
 // computes the table once per partition (no 64-bit division on the device).
 __device__ __forceinline__ long long unit_begin(const Params &P, long long c) { return __ldg(P.ubeg + c); }
 
+// Rows of the per-row phases: chunks of 32 consecutive rows (one per warp, coalesced) dealt
+// round-robin over the CTAs first, so that every SM gets a share even when N < G * kThreads.
+struct RowIter {
+    long long q, step, N;
+    int lane;
+    __device__ __forceinline__ RowIter(const Params &P, long long vc)
+        : q((long long)(threadIdx.x >> 5) * P.G + vc), step((long long)P.G * (kThreads >> 5)), N(P.N),
+          lane((int)(threadIdx.x & 31))
+    {
+    }
+    __device__ __forceinline__ bool more() const { return q * 32 < N; }
+    __device__ __forceinline__ long long row() const { return q * 32 + lane; }
+    __device__ __forceinline__ void next() { q += step; }
+};
+
+
 // Bounded mbarrier phase wait: gives up (and sets the error word) after the
 // barrier bound, or at once when another CTA already reported an error.
 __device__ __forceinline__ bool mbar_wait(const Params &P, uint64_t *bar, uint32_t parity)
@@ -682,8 +698,10 @@ __device__ void phase_foldB(const Params &P, long long ell, double *red, long lo
     __syncthreads();
     const double beta = s_beta;
     const long long N = P.N;
-    for (long long l = vc * kThreads + threadIdx.x; l < N; l += (long long)P.G * kThreads)
-        foldB_row<NP>(P, c, p, l, beta);
+    for (RowIter it(P, vc); it.more(); it.next()) {
+        const long long l = it.row();
+        if (l < N) foldB_row<NP>(P, c, p, l, beta);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1066,7 +1084,9 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red, long lo
         __syncthreads();
     }
     double a = 0.0, b = 0.0, cc = 0.0, mviol = 0.0, mcomp = 0.0, sviol = 0.0, smuy = 0.0;
-    for (long long l = vc * kThreads + threadIdx.x; l < N; l += (long long)P.G * kThreads) {
+    for (RowIter it(P, vc); it.more(); it.next()) {
+        const long long l = it.row();
+        if (l >= N) continue;
         // row sum: the Q (>= 2S, zero padded) contiguous partials of row l, independent 16-byte loads
         const float4 *rp4 = reinterpret_cast<const float4 *>(P.rowpart + l * P.Q);
         float rh = 0.0f, rl = 0.0f;
