@@ -476,26 +476,37 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
-// Block reduction of K doubles (sum or max per component) into out[] of thread 0;
-// fixed order, hence deterministic.  red: shared scratch of 8*K doubles.
+// Block reduction of K doubles (sum or max per component) into v[] of thread 0; fixed
+// order, hence deterministic.  red: shared scratch of (warps + 1)*K doubles.  Every component starts
+// at 0 in every thread and maxima are taken over non-negative terms, so 0 is the identity of
+// each component: a warp whose values are all +0 contributes zeros without FP64 work (GB300's
+// FP64 pipe is narrow, and at small N most warps hold no rows), and the final pass over the
+// warps runs one component per thread.
 template <int K>
 __device__ __forceinline__ void block_reduce(double (&v)[K], const bool (&is_max)[K], double *red)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    bool nz = false;
 #pragma unroll
-    for (int i = 0; i < K; ++i) v[i] = is_max[i] ? warp_max(v[i]) : warp_sum(v[i]);
+    for (int i = 0; i < K; ++i) nz |= __double_as_longlong(v[i]) != 0ll;
+    if (__any_sync(0xffffffffu, nz)) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) v[i] = is_max[i] ? warp_max(v[i]) : warp_sum(v[i]);
+    }
     if (lane == 0)
 #pragma unroll
         for (int i = 0; i < K; ++i) red[warp * K + i] = v[i];
     __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int i = 0; i < K; ++i) {
-            double a = red[i];
-            for (int w = 1; w < kThreads / 32; ++w) a = is_max[i] ? fmax(a, red[w * K + i]) : a + red[w * K + i];
-            v[i] = a;
-        }
+    if (threadIdx.x < K) {
+        const int i = threadIdx.x;
+        double a = red[i];
+        for (int w = 1; w < kThreads / 32; ++w) a = is_max[i] ? fmax(a, red[w * K + i]) : a + red[w * K + i];
+        red[(kThreads / 32) * K + i] = a;
     }
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int i = 0; i < K; ++i) v[i] = red[(kThreads / 32) * K + i];
     __syncthreads();
 }
 
