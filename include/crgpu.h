@@ -214,6 +214,75 @@ cr_status cr_kkt_residual_noalloc(int64_t N, int32_t n, const float *dtheta, int
 /* Releases every resource of the handle (NULL is a no-op). */
 void cr_destroy(cr_handle h);
 
+/* ---- ALCC with the MAPG inner solver on the full problem (Sec. II-D) ---------------------
+ * ALCC (Fig. `fig:alcc`) solves (regularize) directly, without the y >= 0 rows and without a
+ * shift.  Outer iteration k:
+ *   1. L^y_k = 1/mu_k + sigma_max^2(A_1), L^xi_k = gamma/mu_k + sigma_max^2(A_2), with
+ *      sigma_max^2(A_1) = 2N and sigma_max^2(A_2) = max_l lambda_max(sum_m (x_m-x_l)(x_m-x_l)^T);
+ *   2. ell^max_k = 4 sqrt((L^y_k Bbar_y^2 + L^xi_k Bbar_xi^2) / tau_k);
+ *   3. (y_k, xi_k) = MAPG on the subproblem P_k of Eq. (eq:subproblem) from (y_{k-1}, xi_{k-1}):
+ *      block steps 1/L^y_k and 1/L^xi_k projected on the balls Q_y = {||y - ybar|| <= Bbar_y} and
+ *      Q_xi = {||xi|| <= Bbar_xi}, momentum, stopped when both step lengths are <= alpha^y_k and
+ *      alpha^xi_k or at ell^max_k.  The pair pass reads FP32 copies of y and xi, so the thresholds
+ *      are taken no smaller than 2^-23 ||y|| and 2^-23 ||xi|| (a shorter step cannot change those
+ *      copies); fixed_inner turns the test off;
+ *   4. theta_{k+1} = (mu_k/mu_{k+1}) (A_1 y_k + A_2 xi_k - theta_k)_-;
+ *   5-6. mu_{k+1} = c mu_k; tau and the alphas are divided by (c k^(1+kappa))^2.
+ * Readings where the paper is silent: theta_1 = 0; (y_0, xi_0) = (ybar, 0); the radii come from
+ * the feasible point (mean(ybar) 1, 0): Bbar = ||ybar - mean(ybar)||, Bbar_y = Bbar,
+ * Bbar_xi = Bbar / sqrt(gamma); mu_1, tau_1 and the alphas are set relative to these scales.
+ *
+ * Device memory: ONE N x ceil16(N) FP32 multiplier array (read once per MAPG iteration, read and
+ * written once per outer iteration) plus O(N n) vectors and O(N^2/32) partial sums.  Each MAPG
+ * iteration is a cooperative launch's pair pass plus two row folds in FP64; a launch runs up to
+ * launch_iters MAPG iterations.  The handle answers cr_get_solution ((y_k, xi_k)),
+ * cr_get_info (iters = outer iterations), cr_get_device_state, cr_reset and cr_destroy; the
+ * P-APG calls (cr_iterate, cr_solve, cr_kkt_residual, cr_objective, cr_backward) return
+ * CR_ESTATE on it. */
+typedef struct {
+    double mu1_scale;      /* mu_1 = mu1_scale / sigma_max^2(A_1); default 1e3 */
+    double tau1_rel;       /* tau_1 = tau1_rel * Bbar^2 / mu_1; default 1e-2 */
+    double alpha1_rel;     /* alpha^y_1 = alpha1_rel * Bbar_y, alpha^xi_1 = alpha1_rel * Bbar_xi; default 1e-2 */
+    double c;              /* > 1; default 2 */
+    double kappa;          /* > 0; default 0.1 */
+    int64_t lmax_cap;      /* > 0: at most this many MAPG iterations per outer iteration; 0: ell^max_k only */
+    int64_t fixed_inner;   /* > 0: every MAPG call runs exactly this many iterations (stopping test off) */
+    int64_t launch_iters;  /* MAPG iterations per cooperative launch; 0 = chosen from N */
+    double reserved[4];
+} cr_alcc_options;
+
+/* Fills *o with the defaults documented above. */
+void cr_alcc_options_default(cr_alcc_options *o);
+
+/* Creates an ALCC solver.  X, ybar as for cr_create; opt (nullable) supplies gamma, grid, stream,
+ * barrier_timeout_ms and profile, and must ask for FP32 theta and not for the tensor-core pass;
+ * aopt may be NULL (defaults).  CR_EINVAL on bad sizes, non-finite inputs or options (c <= 1,
+ * kappa <= 0, mu1_scale/tau1_rel/alpha1_rel <= 0); CR_ECUDA when the cooperative launch does not
+ * fit.  The state is Iteration 0 of Fig. `fig:alcc`. */
+cr_status cr_alcc_create(const double *X, const double *ybar, int64_t N, int32_t n, const cr_options *opt,
+                         const cr_alcc_options *aopt, cr_handle *out);
+
+/* Runs k outer iterations (steps 1-6 each).  inner (nullable, k entries) receives the MAPG
+ * iterations of each.  Blocks. */
+cr_status cr_alcc_iterate(cr_handle h, int64_t k, int64_t *inner);
+
+/* Runs outer iterations until the KKT residual of cr_alcc_metrics is <= tol or max_outer more
+ * outer iterations; *outer_done (nullable) = outer iterations run by this call.  CR_OK on
+ * convergence, CR_NOT_CONVERGED otherwise.  Blocks. */
+cr_status cr_alcc_solve(cr_handle h, double tol, int64_t max_outer, int64_t *outer_done);
+
+/* FP64 KKT residual of (regularize) after the last outer iteration k, at (y_k, xi_k) with the
+ * multiplier estimate lambda = mu_{k+1} theta_{k+1}; with sigma = max(1, max ybar - min ybar):
+ *   stat = max(max_l |y_l - ybar_l - (A_1^T lambda)_l|, max_lk |gamma xi_lk - (A_2^T lambda)_lk|) / sigma
+ *   pri  = max_p (-(A_1 y + A_2 xi)_p)_+ / sigma
+ *   comp = max_p lambda_p |(A_1 y + A_2 xi)_p| / sigma^2,      kkt = max(stat, pri, comp).
+ * CR_ESTATE before the first outer iteration.  Any pointer may be NULL. */
+cr_status cr_alcc_metrics(cr_handle h, double *kkt, double *stat, double *pri, double *comp);
+
+/* Outer iterations run, MAPG iterations run in total, the current mu_k and the ell^max_k of the
+ * next outer iteration.  Any pointer may be NULL. */
+cr_status cr_alcc_info(cr_handle h, int64_t *outer, int64_t *inner_total, double *mu, int64_t *lmax_next);
+
 /* ---- batched solves: many independent fits in one persistent launch ---------------------
  * B independent instances (sizes N[i] x n[i], host FP64 arrays X[i], ybar[i]) advance together:
  * one cooperative launch runs every phase of every instance, separated by bounded grid

@@ -20,7 +20,7 @@ import threading
 import numpy as np
 
 __all__ = [
-    "CrError", "Options", "Solver", "lib", "library_path", "exported_symbols",
+    "CrError", "Options", "Solver", "AlccOptions", "AlccSolver", "lib", "library_path", "exported_symbols",
     "THETA_F32", "THETA_BF16", "THETA_F16", "DRIVER_AUTO", "DRIVER_PERSISTENT", "DRIVER_PHASES",
     "PAIR_AUTO", "PAIR_CUDA_CORES", "PAIR_TENSOR_CORES",
     "CR_OK", "CR_NOT_CONVERGED",
@@ -43,6 +43,8 @@ exported_symbols = (
     "cr_status_str", "cr_last_error", "cr_profile", "cr_get_device_state", "cr_kkt_residual_noalloc",
     "cr_batch_create", "cr_batch_solve", "cr_batch_iterate", "cr_batch_reset", "cr_batch_instance",
     "cr_batch_info", "cr_batch_destroy", "cr_batch_last_error", "cr_backward", "cr_get_engine",
+    "cr_alcc_options_default", "cr_alcc_create", "cr_alcc_iterate", "cr_alcc_solve", "cr_alcc_metrics",
+    "cr_alcc_info",
 )
 PROFILE_PAIR, PROFILE_FOLD, PROFILE_KKT, PROFILE_PERSISTENT = 0, 1, 2, 3
 
@@ -58,6 +60,15 @@ class Options(ctypes.Structure):
         ("test_barrier_extra", ctypes.c_int32), ("profile", ctypes.c_int32), ("record_every", ctypes.c_int32),
         ("pair_engine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
         ("restart_tol", ctypes.c_double),
+    ]
+
+
+class AlccOptions(ctypes.Structure):
+    """Mirror of ``cr_alcc_options``."""
+    _fields_ = [
+        ("mu1_scale", ctypes.c_double), ("tau1_rel", ctypes.c_double), ("alpha1_rel", ctypes.c_double),
+        ("c", ctypes.c_double), ("kappa", ctypes.c_double), ("lmax_cap", ctypes.c_int64),
+        ("fixed_inner", ctypes.c_int64), ("launch_iters", ctypes.c_int64), ("reserved", ctypes.c_double * 4),
     ]
 
 
@@ -121,6 +132,16 @@ def lib():
                 getattr(L, name).restype = ctypes.c_int
             L.cr_backward.argtypes = [H, fp, fp, fp]
             L.cr_backward.restype = ctypes.c_int
+            L.cr_alcc_options_default.argtypes = [ctypes.POINTER(AlccOptions)]
+            L.cr_alcc_options_default.restype = None
+            L.cr_alcc_create.argtypes = [dp, dp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Options),
+                                         ctypes.POINTER(AlccOptions), ctypes.POINTER(H)]
+            L.cr_alcc_iterate.argtypes = [H, ctypes.c_int64, i64p]
+            L.cr_alcc_solve.argtypes = [H, ctypes.c_double, ctypes.c_int64, i64p]
+            L.cr_alcc_metrics.argtypes = [H, dp, dp, dp, dp]
+            L.cr_alcc_info.argtypes = [H, i64p, i64p, dp, i64p]
+            for name in ("cr_alcc_create", "cr_alcc_iterate", "cr_alcc_solve", "cr_alcc_metrics", "cr_alcc_info"):
+                getattr(L, name).restype = ctypes.c_int
             L.cr_profile.argtypes = [H, ctypes.c_int32, dp, i64p]
             L.cr_profile.restype = ctypes.c_int
             L.cr_destroy.argtypes = [H]
@@ -270,6 +291,62 @@ class Solver:
                                               ctypes.byref(y), ctypes.byref(xi), ctypes.byref(mu), ctypes.byref(sg)))
         return {"theta": th.value, "ld": ld.value, "X": X.value, "y": y.value, "xi": xi.value, "mu": mu.value,
                 "sigma": sg.value}
+
+
+class AlccSolver(Solver):
+    """ALCC with the MAPG inner solver on the full problem (Sec. II-D; ``cr_alcc_*``).
+
+    X, ybar: host arrays.  Keyword arguments set ``cr_alcc_options`` fields (``mu1_scale``,
+    ``tau1_rel``, ``alpha1_rel``, ``c``, ``kappa``, ``lmax_cap``, ``fixed_inner``,
+    ``launch_iters``) or ``cr_options`` fields (``gamma``, ``grid``, ``stream``, ``profile`` ...).
+    ``solution()``, ``device_state()``, ``reset()`` and ``profile()`` are those of ``Solver``.
+    """
+
+    def __init__(self, X, ybar, **opts):
+        self._h = ctypes.c_void_p()
+        L = lib()
+        a = AlccOptions()
+        L.cr_alcc_options_default(ctypes.byref(a))
+        rest = {}
+        for k, v in opts.items():
+            if hasattr(a, k) and k != "reserved":
+                setattr(a, k, v)
+            else:
+                rest[k] = v
+        o = default_options(**rest)
+        self.options, self.alcc_options = o, a
+        Xa = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
+        ya = np.ascontiguousarray(np.asarray(ybar, dtype=np.float64))
+        if Xa.ndim != 2 or ya.shape != (Xa.shape[0],):
+            raise ValueError("X must be (N, n) and ybar (N,)")
+        N, n = Xa.shape
+        st = L.cr_alcc_create(_dptr(Xa), _dptr(ya), N, n, ctypes.byref(o), ctypes.byref(a), ctypes.byref(self._h))
+        if st != CR_OK:
+            raise CrError(st, L.cr_last_error(None).decode())
+        self.N, self.n = int(N), int(n)
+
+    def iterate(self, k: int) -> list[int]:
+        """k outer iterations; returns the MAPG iterations of each."""
+        inner = (ctypes.c_int64 * max(int(k), 1))()
+        self._check(lib().cr_alcc_iterate(self._h, int(k), inner))
+        return [int(v) for v in inner[:int(k)]]
+
+    def solve(self, tol: float, max_outer: int) -> tuple[bool, int]:
+        done = ctypes.c_int64()
+        st = self._check(lib().cr_alcc_solve(self._h, float(tol), int(max_outer), ctypes.byref(done)),
+                         (CR_OK, CR_NOT_CONVERGED))
+        return st == CR_OK, int(done.value)
+
+    def metrics(self) -> dict:
+        v = [ctypes.c_double() for _ in range(4)]
+        self._check(lib().cr_alcc_metrics(self._h, *(ctypes.byref(x) for x in v)))
+        return dict(zip(("kkt", "stat", "pri", "comp"), (x.value for x in v)))
+
+    def info(self) -> dict:
+        o, it, lm = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        mu = ctypes.c_double()
+        self._check(lib().cr_alcc_info(self._h, ctypes.byref(o), ctypes.byref(it), ctypes.byref(mu), ctypes.byref(lm)))
+        return {"outer": o.value, "inner_total": it.value, "mu": mu.value, "lmax_next": lm.value}
 
 
 class _Member(Solver):

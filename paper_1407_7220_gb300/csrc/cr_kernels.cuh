@@ -70,6 +70,11 @@ struct DevState {
     int converged;
     int pad[2];
     double kkt[8];      // last reduced KKT terms: 0 kkt,1 pri,2 comp,3 infeas,4 gap,5 screen
+    // ALCC (Sec. II-D): progress of the current MAPG call, written at the end of every launch
+    long long alcc_ell;  // MAPG iterations done
+    int alcc_done;       // 1: MAPG returned and the outer step of Fig. `fig:alcc` was taken
+    int alcc_pad;
+    double alcc_t;       // t of the MAPG figure after alcc_ell iterations
 };
 
 struct Params {
@@ -113,6 +118,9 @@ struct Params {
     int tc;                 // 1: the pair pass runs its two products on the tensor cores
     float *xi_tc;           // tensor-core operands (TF32 hi/lo): Xi per stripe, written by every foldB
     float *xr_tc, *xt_tc;   // X rows and [X | 1] transposed per 8-row block (constant)
+    // ALCC (Sec. II-D) on the full problem; (y_k, xi_k) live in y1 and xi1_64, theta_k in theta[0]
+    double *ay[2], *axi[2]; // (y, xi)^(1) of the two latest MAPG iterations (N, N x n; FP64)
+    double *ay2, *axi2;     // the extrapolated point (y, xi)^(2) of MAPG steps 4-5
     double *foldpart;       // [G][8]
     double *kktpart;        // [G][8]
     DevState *st;
@@ -728,11 +736,16 @@ __device__ void phase_foldB(const Params &P, long long ell, double *red, long lo
 // rows/columns of a tile are zero-filled by the TMA unit.
 // ---------------------------------------------------------------------------
 
-template <typename TS, int NP> struct PairSmem {
+// Pass modes: the P-APG step (two multiplier tiles in, theta^(1)_l out), and the two ALCC passes
+// of Sec. II-D over one multiplier array: m = (A_1 y + A_2 xi - theta_k)_- with its adjoint and
+// nothing stored (MAPG gradient), and theta <- a m stored in place (Fig. `fig:alcc` step 4).
+enum PairMode : int { PM_PAPG = 0, PM_ALCC_GRAD = 1, PM_ALCC_UPDATE = 2 };
+
+template <typename TS, int NP, int TILES = 2> struct PairSmem {
     static constexpr int REC = RecLayout<NP>::REC;
     static constexpr size_t tile_bytes = (size_t)kRS * kW * sizeof(TS);
     static constexpr size_t rec_bytes = (size_t)kRS * REC * sizeof(float);
-    static constexpr size_t stage_bytes = 2 * tile_bytes + rec_bytes;
+    static constexpr size_t stage_bytes = TILES * tile_bytes + rec_bytes;
     // as many stages as fit (more bytes in flight per SM)
     static constexpr int kFit = (int)((kSmemBudget - 128) / stage_bytes);
     static constexpr int kStages = kFit < kMaxStages ? kFit : kMaxStages;
@@ -748,7 +761,7 @@ template <typename TS, int NP> struct PairSmem {
 // The arithmetic of every pair is the scalar expression order of Step 2 (two chains of the
 // xi.x product, even and odd k), so the residual and the projection mask are reproducible
 // by a scalar evaluation.
-template <typename TS, int NP, bool MASK, bool SR>
+template <typename TS, int NP, bool MASK, bool SR, int MODE>
 __device__ __forceinline__ void pair_stage_rows(const TS *tcur, const TS *tprv, const float *rec, int rg, int cofs,
                                                 long long r, long long r1, long long col0, long long N, long long ld,
                                                 const f2 (&ccol)[2], const f2 (&nxi)[2][NP], f2 (&acc)[2][NP],
@@ -777,7 +790,8 @@ __device__ __forceinline__ void pair_stage_rows(const TS *tcur, const TS *tprv, 
         const f2 yb = f2_make(rv[0], rv[0]);
         f2 tc[2], tp[2], outv[2];
         St::unpack2(tcur + rl * kW + cofs, tc, iscl);
-        St::unpack2(tprv + rl * kW + cofs, tp, iscl);
+        if (MODE == PM_PAPG) St::unpack2(tprv + rl * kW + cofs, tp, iscl);
+        else tp[0] = tp[1] = zero2;   // one array: theta^(2) = (1 + beta) theta
         uint32_t hP[2] = {0u, 0u};
         if (SR) {
             hP[0] = hash_row(hcol, (uint32_t)rr);
@@ -810,7 +824,7 @@ __device__ __forceinline__ void pair_stage_rows(const TS *tcur, const TS *tprv, 
 #pragma unroll
             for (int k = 0; k < NP; ++k) acc[P][k] = f2_fma(vv, xb[k], acc[P][k]);   // theta^T X (A_2^T)
         }
-        if (vec_ok && valid) *reinterpret_cast<Vec *>(nxt + rr * ld + col0) = St::pack2(outv);
+        if (MODE != PM_ALCC_GRAD && vec_ok && valid) *reinterpret_cast<Vec *>(nxt + rr * ld + col0) = St::pack2(outv);
         float a, b;
         f2_split(rs2, a, b);
         rsv[i] = a + b;
@@ -903,32 +917,36 @@ template <int S> struct RingPos {
 // Issue the stage at ring position pos: unless this is the slot's first use (reuse false),
 // wait until its previous occupant (S stages earlier) was released by all 8 warps, then
 // two tiled TMA loads and one bulk copy complete on the slot's "full" barrier.
-template <typename TS, int NP>
+template <typename TS, int NP, int MODE>
 __device__ __forceinline__ bool produce_stage(const Params &P, unsigned char *stage0, uint64_t *full, uint64_t *empty,
-                                              const RingPos<PairSmem<TS, NP>::kStages> &pos, bool reuse,
-                                              const StageCursor &cur, int c, int p)
+                                              const RingPos<PairSmem<TS, NP, MODE == PM_PAPG ? 2 : 1>::kStages> &pos,
+                                              bool reuse, const StageCursor &cur, int c, int p)
 {
-    using L = PairSmem<TS, NP>;
+    constexpr int TILES = MODE == PM_PAPG ? 2 : 1;
+    using L = PairSmem<TS, NP, TILES>;
     const int slot = pos.slot;
     if (reuse && !mbar_wait(P, &empty[slot], pos.phase ^ 1u)) return false;
     const int nrows = (int)min((long long)kRS, cur.r1 - cur.r);
     unsigned char *st = stage0 + slot * L::stage_bytes;
-    mbar_arrive_expect_tx(&full[slot], (uint32_t)(2 * L::tile_bytes + (size_t)nrows * L::REC * 4));
+    mbar_arrive_expect_tx(&full[slot], (uint32_t)(TILES * L::tile_bytes + (size_t)nrows * L::REC * 4));
     tma_load_2d(st, &P.tmap[c], (int)(cur.s * kW), (int)cur.r, &full[slot]);
-    tma_load_2d(st + L::tile_bytes, &P.tmap[p], (int)(cur.s * kW), (int)cur.r, &full[slot]);
-    bulk_load(st + 2 * L::tile_bytes, P.rowrec + cur.r * L::REC, (uint32_t)(nrows * L::REC * 4), &full[slot]);
+    if (TILES == 2) tma_load_2d(st + L::tile_bytes, &P.tmap[p], (int)(cur.s * kW), (int)cur.r, &full[slot]);
+    bulk_load(st + TILES * L::tile_bytes, P.rowrec + cur.r * L::REC, (uint32_t)(nrows * L::REC * 4), &full[slot]);
     return true;
 }
 
-template <typename TS, int NP>
+// MODE = PM_PAPG: Step 2 of P-APG at iteration ell.  The ALCC modes read and write array 0 only;
+// a = mu_k / mu_{k+1} scales the stored values of PM_ALCC_UPDATE.
+template <typename TS, int NP, int MODE = PM_PAPG>
 __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, uint64_t *full, uint64_t *empty,
-                           unsigned long long &kstage, long long vc)
+                           unsigned long long &kstage, long long vc, float a = 1.0f)
 {
     using St = Store<TS>;
-    using L = PairSmem<TS, NP>;
+    constexpr int TILES = MODE == PM_PAPG ? 2 : 1;
+    using L = PairSmem<TS, NP, TILES>;
     constexpr int S = L::kStages;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int p = (int)(ell & 1), c = 1 - p;
+    const int p = MODE == PM_PAPG ? (int)(ell & 1) : 0, c = MODE == PM_PAPG ? 1 - p : 0;
     const long long N = P.N, ld = P.ld;
     const long long ubeg = unit_begin(P, vc);
     const long long uend = unit_begin(P, vc + 1);
@@ -954,7 +972,7 @@ __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, 
         pc.begin(ubeg, uend, N);
         ppos.init(kprod);
         for (; kprod < kend && kprod < kstage + S && pok; ++kprod) {
-            pok = produce_stage<TS, NP>(P, stage0, full, empty, ppos, kprod >= (unsigned long long)S, pc, c, p);
+            pok = produce_stage<TS, NP, MODE>(P, stage0, full, empty, ppos, kprod >= (unsigned long long)S, pc, c, p);
             pc.advance(N);
             ppos.next();
         }
@@ -962,11 +980,13 @@ __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, 
     __syncwarp();
 
     const int wc = warp & 1, rg = warp >> 1;
-    const float beta = (float)__ldcg(&P.st->scal[p].beta);
-    const float invL = P.invL;
+    // MAPG gradient: m = max(0, theta - g) (beta 0, step 1); update: a max(0, theta - g) as
+    // max(0, (1 + (a - 1)) theta - a g)
+    const float beta = MODE == PM_PAPG ? (float)__ldcg(&P.st->scal[p].beta) : MODE == PM_ALCC_UPDATE ? a - 1.0f : 0.0f;
+    const float invL = MODE == PM_PAPG ? P.invL : MODE == PM_ALCC_UPDATE ? a : 1.0f;
     const float scl = P.st_scale, iscl = P.st_inv_scale;
     const f2 beta2 = f2_make(beta, beta), ninvL2 = f2_make(-invL, -invL), iscl2 = f2_make(iscl, iscl);
-    const bool sr = P.sr != 0;
+    const bool sr = MODE == PM_PAPG && P.sr != 0;
     const uint32_t rseed = P.seed ^ (uint32_t)ell * 0x632BE5ABu;
     TS *__restrict__ nxt = (TS *)P.theta[p];   // theta^(1)_{l-2} on entry, theta^(1)_l on exit
     const long long first_stripe = ubeg / N;
@@ -1012,25 +1032,25 @@ __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, 
             if (ok) {
                 const unsigned char *st = stage0 + slot * L::stage_bytes;
                 const TS *tcur = reinterpret_cast<const TS *>(st);
-                const TS *tprv = reinterpret_cast<const TS *>(st + L::tile_bytes);
-                const float *rec = reinterpret_cast<const float *>(st + 2 * L::tile_bytes);
+                const TS *tprv = reinterpret_cast<const TS *>(st + (TILES - 1) * L::tile_bytes);   // unused by the ALCC modes
+                const float *rec = reinterpret_cast<const float *>(st + TILES * L::tile_bytes);
                 const bool fast = !ragged && (r + kRS <= r1) && !(r < colw + 128 && colw < r + kRS);
                 if (sr) {
                     if (fast)
-                        pair_stage_rows<TS, NP, false, true>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn);
+                        pair_stage_rows<TS, NP, false, true, MODE>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn);
                     else
-                        pair_stage_rows<TS, NP, true, true>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn);
+                        pair_stage_rows<TS, NP, true, true, MODE>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn);
                 } else {
                     if (fast)
-                        pair_stage_rows<TS, NP, false, false>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn);
+                        pair_stage_rows<TS, NP, false, false, MODE>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn);
                     else
-                        pair_stage_rows<TS, NP, true, false>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn);
+                        pair_stage_rows<TS, NP, true, false, MODE>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn);
                 }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[slot]);
             if (producer && pok && kprod < kend) {   // refill this slot with the stage S ahead
-                pok = produce_stage<TS, NP>(P, stage0, full, empty, ppos, kprod >= (unsigned long long)S, pc, c, p);
+                pok = produce_stage<TS, NP, MODE>(P, stage0, full, empty, ppos, kprod >= (unsigned long long)S, pc, c, p);
                 pc.advance(N);
                 ppos.next();
                 ++kprod;
@@ -1074,6 +1094,71 @@ __device__ __forceinline__ void ff_add(float &hi, float &lo, float b)
 }
 __device__ __forceinline__ double ff_value(float hi, float lo) { return (double)hi + (double)lo; }
 
+// Aggregates of the values the pair pass accumulated for row and column l, reduced from its
+// partials in a fixed order (deterministic): R = row sum, Cc = column sum, TX = (Theta^T X)_l,
+// with Theta the array of values the pass produced (theta^(1), or m in the ALCC passes).
+template <int NP>
+__device__ __forceinline__ void gather_adjoint(const Params &P, long long l, double &R, double &Cc, double (&TX)[NP])
+{
+    const long long N = P.N;
+    const int Q4 = P.Q >> 2;   // row partials per row, in float4 units
+    // row sum: the Q (>= 2S, zero padded) contiguous partials of row l, independent 16-byte loads
+    const float4 *rp4 = reinterpret_cast<const float4 *>(P.rowpart + l * P.Q);
+    float rh = 0.0f, rl = 0.0f;
+#pragma unroll 8
+    for (int q = 0; q < Q4; ++q) {
+        const float4 t = __ldcg(rp4 + q);
+        ff_add(rh, rl, t.x);
+        ff_add(rh, rl, t.y);
+        ff_add(rh, rl, t.z);
+        ff_add(rh, rl, t.w);
+    }
+    R = ff_value(rh, rl);
+    const long long s = l / kW, cl = l - s * kW;
+    // CTAs whose unit range intersects stripe s, ascending
+    const long long ua = s * N, ub = s * N + N - 1;
+    long long c0 = (long long)(((unsigned long long)ua * (unsigned long long)P.G) / (unsigned long long)P.total);
+    while (c0 > 0 && unit_begin(P, c0) > ua) --c0;
+    while (c0 + 1 < P.G && unit_begin(P, c0 + 1) <= ua) ++c0;
+    float ch = 0.0f, clo = 0.0f, th[NP], tl[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) th[k] = tl[k] = 0.0f;
+    long long ubg = unit_begin(P, c0);
+    for (long long cta = c0; cta < P.G && ubg <= ub; ++cta) {
+        const long long unx = unit_begin(P, cta + 1);
+        if (unx > ubg) {
+            const long long fs = ubg / N;
+            const float *cp0 = P.colpart + ((cta * P.slots + (s - fs)) * P.cgroups * (NP + 1)) * kW + cl;
+            // all (group, component) loads of one segment are independent: issue them together
+            auto add_groups = [&](auto G) {
+                constexpr int NG = decltype(G)::value;
+                float cv[NG], tv[NG][NP];
+#pragma unroll
+                for (int g = 0; g < NG; ++g) {
+                    const float *cp = cp0 + g * (NP + 1) * kW;
+                    cv[g] = __ldcg(cp);
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) tv[g][k] = __ldcg(cp + (1 + k) * kW);
+                }
+#pragma unroll
+                for (int g = 0; g < NG; ++g) {
+                    ff_add(ch, clo, cv[g]);
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) ff_add(th[k], tl[k], tv[g][k]);
+                }
+            };
+            if (P.cgroups == kWR)
+                add_groups(std::integral_constant<int, kWR>());
+            else
+                add_groups(std::integral_constant<int, 1>());
+        }
+        ubg = unx;
+    }
+    Cc = ff_value(ch, clo);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) TX[k] = ff_value(th[k], tl[k]);
+}
+
 // ---------------------------------------------------------------------------
 // foldA(l): reduce partials of theta^(1)_l in FP64; eta(theta^(1)_l); dual terms
 // ---------------------------------------------------------------------------
@@ -1083,7 +1168,6 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red, long lo
     const int p = (int)(ell & 1);
     const long long N = P.N;
     const int n = P.n;
-    const int Q4 = P.Q >> 2;   // row partials per row, in float4 units
     // fused foldB(l+1): its momentum weight needs no reduction in plain P-APG
     __shared__ double s_nbeta;
     if (P.fuse) {
@@ -1098,62 +1182,8 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red, long lo
     for (RowIter it(P, vc); it.more(); it.next()) {
         const long long l = it.row();
         if (l >= N) continue;
-        // row sum: the Q (>= 2S, zero padded) contiguous partials of row l, independent 16-byte loads
-        const float4 *rp4 = reinterpret_cast<const float4 *>(P.rowpart + l * P.Q);
-        float rh = 0.0f, rl = 0.0f;
-#pragma unroll 8
-        for (int q = 0; q < Q4; ++q) {
-            const float4 t = __ldcg(rp4 + q);
-            ff_add(rh, rl, t.x);
-            ff_add(rh, rl, t.y);
-            ff_add(rh, rl, t.z);
-            ff_add(rh, rl, t.w);
-        }
-        const double R = ff_value(rh, rl);
-        const long long s = l / kW, cl = l - s * kW;
-        // CTAs whose unit range intersects stripe s, ascending
-        const long long ua = s * N, ub = s * N + N - 1;
-        long long c0 = (long long)(((unsigned long long)ua * (unsigned long long)P.G) / (unsigned long long)P.total);
-        while (c0 > 0 && unit_begin(P, c0) > ua) --c0;
-        while (c0 + 1 < P.G && unit_begin(P, c0 + 1) <= ua) ++c0;
-        float ch = 0.0f, clo = 0.0f, th[NP], tl[NP];
-#pragma unroll
-        for (int k = 0; k < NP; ++k) th[k] = tl[k] = 0.0f;
-        long long ubg = unit_begin(P, c0);
-        for (long long cta = c0; cta < P.G && ubg <= ub; ++cta) {
-            const long long unx = unit_begin(P, cta + 1);
-            if (unx > ubg) {
-                const long long fs = ubg / N;
-                const float *cp0 = P.colpart + ((cta * P.slots + (s - fs)) * P.cgroups * (NP + 1)) * kW + cl;
-                // all (group, component) loads of one segment are independent: issue them together
-                auto add_groups = [&](auto G) {
-                    constexpr int NG = decltype(G)::value;
-                    float cv[NG], tv[NG][NP];
-#pragma unroll
-                    for (int g = 0; g < NG; ++g) {
-                        const float *cp = cp0 + g * (NP + 1) * kW;
-                        cv[g] = __ldcg(cp);
-#pragma unroll
-                        for (int k = 0; k < NP; ++k) tv[g][k] = __ldcg(cp + (1 + k) * kW);
-                    }
-#pragma unroll
-                    for (int g = 0; g < NG; ++g) {
-                        ff_add(ch, clo, cv[g]);
-#pragma unroll
-                        for (int k = 0; k < NP; ++k) ff_add(th[k], tl[k], tv[g][k]);
-                    }
-                };
-                if (P.cgroups == kWR)
-                    add_groups(std::integral_constant<int, kWR>());
-                else
-                    add_groups(std::integral_constant<int, 1>());
-            }
-            ubg = unx;
-        }
-        const double Cc = ff_value(ch, clo);
-        double TX[NP];
-#pragma unroll
-        for (int k = 0; k < NP; ++k) TX[k] = ff_value(th[k], tl[k]);
+        double R, Cc, TX[NP];
+        gather_adjoint<NP>(P, l, R, Cc, TX);
         const double v = R - Cc;               // (A_1^T theta)_l = row sum - column sum
         P.v[p][l] = v;
         const double hl = __ldg(P.h + l), mu = __ldcg(P.mu[p] + l);

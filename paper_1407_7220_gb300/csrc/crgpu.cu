@@ -18,6 +18,7 @@
 #include <string>
 #include <vector>
 
+#include "cr_alcc.cuh"
 #include "cr_launch.cuh"
 #include "crgpu.h"
 
@@ -79,6 +80,16 @@ struct cr_ctx {
     std::vector<Checkpoint> ckpt;       // at iterations 0, k, 2k, ...
     std::vector<void *> ckpt_allocs;
     std::vector<void *> bwd_allocs;     // reverse-mode workspace (lazily allocated)
+    // ALCC handles (cr_alcc_create): kernel, constants and the schedule of Fig. `fig:alcc`
+    bool alcc = false;
+    cr_alcc_options aopt{};
+    crk::AlccKernel ak{};
+    double a_s2a1 = 0.0, a_s2a2 = 0.0, a_By = 0.0, a_Bxi = 0.0;
+    double a_mu = 0.0, a_tau = 0.0, a_alpha_y = 0.0, a_alpha_xi = 0.0;
+    long long a_inner_total = 0;
+    bool a_have_metrics = false;
+    double a_metrics[4] = {0, 0, 0, 0};
+    std::vector<float> a_rec0, a_ccol0;   // column data of (y_0, xi_0) = (ybar, 0)
 };
 
 namespace {
@@ -571,8 +582,10 @@ void ckpt_clear(cr_ctx *h)
     h->ckpt.clear();
 }
 
+cr_status alcc_init(cr_ctx *h);
+
 cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long N, int n, const cr_options *opt,
-                      cr_handle *out, int np_override = 0)
+                      cr_handle *out, int np_override = 0, const cr_alcc_options *aopt = nullptr)
 {
     cr_ctx *h = new (std::nothrow) cr_ctx();
     if (!h) return CR_ENOMEM;
@@ -588,6 +601,20 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     h->NP = np_override > 0 ? np_override : padded_n(n);
     h->ks = kernels_for(o.theta_dtype, h->NP);
     if (!h->ks.phase) return fail(h, CR_EINVAL, "no kernel for n = %d", n);
+    h->alcc = aopt != nullptr;
+    if (h->alcc) {
+        h->aopt = *aopt;
+        if (o.theta_dtype != CR_THETA_F32) return fail(h, CR_EINVAL, "ALCC keeps theta in FP32");
+        if (o.pair_engine == CR_PAIR_TENSOR_CORES) return fail(h, CR_EINVAL, "ALCC runs the CUDA-core pair pass");
+        if (!(aopt->c > 1.0) || !(aopt->kappa > 0.0) || !(aopt->mu1_scale > 0.0) || !(aopt->tau1_rel > 0.0) ||
+            !(aopt->alpha1_rel > 0.0) || aopt->lmax_cap < 0 || aopt->fixed_inner < 0 || aopt->launch_iters < 0)
+            return fail(h, CR_EINVAL, "ALCC options: need c > 1, kappa > 0, positive scales, counts >= 0");
+        o.record_every = 0;
+        o.pair_engine = CR_PAIR_CUDA_CORES;
+        o.shift = 0.0;
+        h->ak = crk::alcc_kernel(h->NP);
+        if (!h->ak.fn) return fail(h, CR_EINVAL, "no ALCC kernel for n = %d", n);
+    }
 
     CR_CUDA(h, cudaGetDevice(&h->device));
     cudaDeviceProp prop;
@@ -604,8 +631,11 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     CR_CUDA(h, cudaFuncSetAttribute(h->ks.persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem));
     CR_CUDA(h, cudaFuncSetAttribute(h->ks.phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem));
     CR_CUDA(h, cudaFuncSetAttribute(h->ks.pair_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem));
+    if (h->alcc)
+        CR_CUDA(h, cudaFuncSetAttribute(h->ak.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ak.smem));
     int per_sm = 0;
-    CR_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, h->ks.persistent, crk::kThreads, h->ks.smem));
+    CR_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, h->alcc ? h->ak.fn : h->ks.persistent,
+                                                             crk::kThreads, h->alcc ? h->ak.smem : h->ks.smem));
     int coop = 0;
     CR_CUDA(h, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
     const int max_coresident = per_sm * h->num_sms;
@@ -620,6 +650,9 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     if (np_override > 0) h->persistent_ok = false;   // batch member: driven by the batch kernel only
     if (o.driver == CR_DRIVER_PERSISTENT && !h->persistent_ok)
         return fail(h, CR_EINVAL, "persistent driver: grid %d exceeds %d co-resident CTAs", G, max_coresident);
+    if (h->alcc && !h->persistent_ok)
+        return fail(h, CR_ECUDA, "ALCC: grid %d exceeds %d co-resident CTAs (or no cooperative launch)", G,
+                    max_coresident);
 
     // host constants
     double s = o.shift >= 0.0 ? o.shift : default_shift(yb);
@@ -629,7 +662,8 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
         hi = std::max(hi, v);
     }
     h->sigma = std::max(1.0, hi - lo);
-    double L = o.L > 0.0 ? o.L : (1.0 + 2.0 * (double)N + max_block_eig(X, N, n)) / o.gamma;
+    const double s2a2 = max_block_eig(X, N, n);   // sigma_max^2(A_2)
+    double L = o.L > 0.0 ? o.L : (1.0 + 2.0 * (double)N + s2a2) / o.gamma;
     o.shift = s;
     o.L = L;
 
@@ -679,7 +713,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     P.restart = o.restart;
     // foldB(l+1) fused into foldA(l): plain P-APG (beta from the t-sequence alone), no recording
     // (cr_backward restores checkpoints and re-runs foldB), not in a batch
-    P.fuse = (o.restart == 0 && o.record_every <= 0 && np_override <= 0) ? 1 : 0;
+    P.fuse = (o.restart == 0 && o.record_every <= 0 && np_override <= 0 && !h->alcc) ? 1 : 0;
     P.restart_tol = o.restart_tol > 0.0 ? o.restart_tol : 0.0;
     P.sr = o.stochastic_round;
     P.seed = (unsigned)(o.seed ^ (o.seed >> 32));
@@ -690,11 +724,12 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
         return fail(h, CR_EINVAL, "record_every needs FP32 theta and n <= 10");
 
     const size_t es = theta_elem_size(o.theta_dtype);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < (h->alcc ? 1 : 2); ++b) {   // ALCC keeps one multiplier array
         void *t = nullptr;
         CR_TRY(dev_alloc(h, (char **)&t, (size_t)N * h->ld * es));
         P.theta[b] = t;
     }
+    if (h->alcc) P.theta[1] = P.theta[0];
     // TMA descriptors of the two multiplier arrays: N x N elements, row pitch ld, box kRS x kW;
     // out-of-range rows/columns read as zero
     auto encode = tensor_map_encoder();
@@ -747,6 +782,25 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     CR_TRY(dev_alloc(h, &P.foldpart, (size_t)G * 8));
     CR_TRY(dev_alloc(h, &P.kktpart, (size_t)G * 8));
     CR_TRY(dev_alloc(h, &P.st, 1));
+    if (h->alcc) {
+        for (int b = 0; b < 2; ++b) {
+            CR_TRY(dev_alloc(h, &P.ay[b], N));
+            CR_TRY(dev_alloc(h, &P.axi[b], (size_t)N * n));
+        }
+        CR_TRY(dev_alloc(h, &P.ay2, N));
+        CR_TRY(dev_alloc(h, &P.axi2, (size_t)N * n));
+        // sigma_max^2(A_1) = 2N (A_1^T A_1 = 2(N I - 1 1^T)); radii from the feasible point
+        // (mean(ybar) 1, 0): Bbar = ||ybar - mean||, Bbar_y = Bbar, Bbar_xi = Bbar / sqrt(gamma)
+        double mean = 0.0;
+        for (double v : yb) mean += v;
+        mean /= (double)N;
+        double B2 = 0.0;
+        for (double v : yb) B2 += (v - mean) * (v - mean);
+        h->a_s2a1 = 2.0 * (double)N;
+        h->a_s2a2 = s2a2;
+        h->a_By = std::sqrt(B2);
+        h->a_Bxi = h->a_By / std::sqrt(o.gamma);
+    }
 
     // row records {y - s (set by every fold), x_1..x_n, 0 ...}
     std::vector<float> rec((size_t)N * REC, 0.0f);
@@ -759,7 +813,128 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     CR_CUDA(h, cudaMemcpyAsync(P.rowrec, rec.data(), sizeof(float) * rec.size(), cudaMemcpyHostToDevice, h->stream));
     CR_CUDA(h, cudaMemcpyAsync(hh, hv.data(), sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
     if (P.tc) CR_TRY(setup_tc_operands(h, X));
+    if (h->alcc) {
+        // column data of (y_0, xi_0) = (ybar, 0): row records y = ybar, xi^T x - y = -ybar
+        h->a_rec0 = rec;
+        h->a_ccol0.resize(N);
+        for (long long l = 0; l < N; ++l) {
+            h->a_rec0[(size_t)l * REC] = (float)yb[l];
+            h->a_ccol0[l] = (float)(-yb[l]);
+        }
+        return alcc_init(h);
+    }
     return init_state(h);
+}
+
+// ---- ALCC (Sec. II-D) ----------------------------------------------------------
+
+// Iteration 0 of Fig. `fig:alcc`: theta_1 = 0, (y_0, xi_0) = (ybar, 0), mu_1, tau_1, alpha_1.
+cr_status alcc_init(cr_ctx *h)
+{
+    const Params &P = h->P;
+    const long long N = h->N;
+    const int n = h->n;
+    CR_CUDA(h, cudaMemsetAsync(P.theta[0], 0, (size_t)N * h->ld * sizeof(float), h->stream));
+    for (int b = 0; b < 2; ++b) {
+        CR_CUDA(h, cudaMemcpyAsync(P.ay[b], P.h, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemsetAsync(P.axi[b], 0, sizeof(double) * N * n, h->stream));
+    }
+    CR_CUDA(h, cudaMemcpyAsync(P.ay2, P.h, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+    CR_CUDA(h, cudaMemcpyAsync(P.y1, P.h, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+    CR_CUDA(h, cudaMemsetAsync(P.axi2, 0, sizeof(double) * N * n, h->stream));
+    CR_CUDA(h, cudaMemsetAsync(P.xi1_64, 0, sizeof(double) * N * n, h->stream));
+    CR_CUDA(h, cudaMemsetAsync(P.xi2, 0, sizeof(float) * N * h->NP, h->stream));
+    CR_CUDA(h, cudaMemcpyAsync(P.rowrec, h->a_rec0.data(), sizeof(float) * h->a_rec0.size(), cudaMemcpyHostToDevice,
+                               h->stream));
+    CR_CUDA(h, cudaMemcpyAsync(P.ccol2, h->a_ccol0.data(), sizeof(float) * N, cudaMemcpyHostToDevice, h->stream));
+    CR_CUDA(h, cudaMemsetAsync(P.rowpart, 0, sizeof(float) * (size_t)P.Q * N, h->stream));
+    CR_CUDA(h, cudaMemsetAsync(P.colpart, 0, sizeof(float) * (size_t)P.G * P.slots * P.cgroups * (h->NP + 1) * crk::kW,
+                               h->stream));
+    DevState st;
+    std::memset(&st, 0, sizeof st);
+    CR_CUDA(h, cudaMemcpyAsync(P.st, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
+    CR_CUDA(h, cudaStreamSynchronize(h->stream));
+    const cr_alcc_options &A = h->aopt;
+    h->a_mu = A.mu1_scale / h->a_s2a1;
+    h->a_tau = A.tau1_rel * h->a_By * h->a_By / h->a_mu;
+    h->a_alpha_y = A.alpha1_rel * h->a_By;
+    h->a_alpha_xi = A.alpha1_rel * h->a_Bxi;
+    h->a_inner_total = 0;
+    h->a_have_metrics = false;
+    h->iters = 0;
+    h->broken = false;
+    return CR_OK;
+}
+
+// ell^max_k of Fig. `fig:alcc` step 2 at the current schedule (at least 1, at most lmax_cap).
+long long alcc_lmax(const cr_ctx *h)
+{
+    if (h->aopt.fixed_inner > 0) return h->aopt.fixed_inner;
+    const double Ly = 1.0 / h->a_mu + h->a_s2a1, Lxi = h->opt.gamma / h->a_mu + h->a_s2a2;
+    double v = 4.0 * std::sqrt((Ly * h->a_By * h->a_By + Lxi * h->a_Bxi * h->a_Bxi) / h->a_tau);
+    v = std::max(1.0, std::ceil(v));
+    if (h->aopt.lmax_cap > 0) v = std::min(v, (double)h->aopt.lmax_cap);
+    return v >= 4.0e18 ? (long long)4e18 : (long long)v;
+}
+
+// One outer iteration (steps 1-6).  MAPG runs in launches of at most launch_iters iterations;
+// the kernel of the launch in which MAPG returns also takes the outer step and the KKT terms.
+cr_status alcc_outer(cr_ctx *h, long long *inner)
+{
+    const cr_alcc_options &A = h->aopt;
+    const double gamma = h->opt.gamma;
+    const double Ly = 1.0 / h->a_mu + h->a_s2a1;        // step 1
+    const double Lxi = gamma / h->a_mu + h->a_s2a2;
+    const long long lmax = alcc_lmax(h);                // step 2
+    const double mu_next = A.c * h->a_mu;               // step 5
+    crk::AlccStep S{};
+    S.inv_mu = 1.0 / h->a_mu;
+    S.gamma_inv_mu = gamma / h->a_mu;
+    S.mu_next = mu_next;
+    S.inv_Ly = 1.0 / Ly;
+    S.inv_Lxi = 1.0 / Lxi;
+    S.By = h->a_By;
+    S.Bxi = h->a_Bxi;
+    S.alpha_y = A.fixed_inner > 0 ? 0.0 : h->a_alpha_y;
+    S.alpha_xi = A.fixed_inner > 0 ? 0.0 : h->a_alpha_xi;
+    S.res_rel = A.fixed_inner > 0 ? 0.0 : std::ldexp(1.0, -23);   // resolution of the FP32 column data
+    S.lmax = lmax;
+    S.a = (float)(h->a_mu / mu_next);
+    const double pairs = (double)h->N * (double)h->N;
+    const long long chunk = A.launch_iters > 0 ? A.launch_iters
+                                               : (long long)std::min(20000.0, std::max(16.0, 2e11 / pairs));
+    long long ell0 = 1;
+    double t0 = 1.0;
+    DevState st;
+    for (;;) {
+        S.ell0 = ell0;
+        S.ell1 = std::min(lmax, ell0 + chunk - 1);
+        S.t0 = t0;
+        CR_CUDA(h, cudaMemsetAsync(&h->P.st->bar_count, 0, sizeof(unsigned long long), h->stream));
+        Params P = h->P;
+        void *args[] = {&P, &S};
+        {
+            ProfScope ps(h, 3);
+            CR_CUDA(h, cudaLaunchCooperativeKernel(h->ak.fn, dim3(h->P.G), dim3(crk::kThreads), args, h->ak.smem,
+                                                   h->stream));
+        }
+        CR_TRY(read_state(h, &st));
+        if (st.alcc_done) break;
+        ell0 = S.ell1 + 1;
+        t0 = st.alcc_t;
+    }
+    if (inner) *inner = st.alcc_ell;
+    h->a_inner_total += st.alcc_ell;
+    for (int i = 0; i < 4; ++i) h->a_metrics[i] = st.kkt[i];
+    h->a_have_metrics = true;
+    const double k = (double)(h->iters + 1);
+    const double shrink = std::pow(A.c * std::pow(k, 1.0 + A.kappa), 2.0);   // steps 5-6
+    h->a_tau /= shrink;
+    h->a_alpha_y /= shrink;
+    h->a_alpha_xi /= shrink;
+    h->a_mu = mu_next;
+    h->iters += 1;
+    return CR_OK;
 }
 
 cr_status check_inputs(const double *X, const double *ybar, long long N, int n)
@@ -795,6 +970,20 @@ cr_status usable(cr_ctx *h)
 {
     if (!h) return CR_EINVAL;
     if (h->broken) return fail(h, CR_ESTATE, "handle failed a bounded wait; call cr_reset");
+    return CR_OK;
+}
+
+cr_status alcc_only(cr_ctx *h)
+{
+    CR_TRY(usable(h));
+    if (!h->alcc) return fail(h, CR_ESTATE, "not an ALCC handle (cr_alcc_create)");
+    return CR_OK;
+}
+
+cr_status papg_only(cr_ctx *h)
+{
+    CR_TRY(usable(h));
+    if (h->alcc) return fail(h, CR_ESTATE, "an ALCC handle: use the cr_alcc_* calls");
     return CR_OK;
 }
 
@@ -859,6 +1048,7 @@ cr_status cr_create_device(const float *dX, const float *dybar, int64_t N, int32
 cr_status cr_reset(cr_handle h)
 {
     if (!h) return CR_EINVAL;
+    if (h->alcc) return alcc_init(h);
     ckpt_clear(h);
     return init_state(h);
 }
@@ -876,7 +1066,7 @@ static cr_status run_iters(cr_handle h, long long k)
 
 cr_status cr_iterate(cr_handle h, int64_t k)
 {
-    CR_TRY(usable(h));
+    CR_TRY(papg_only(h));
     if (k < 0) return fail(h, CR_EINVAL, "k < 0");
     if (k == 0) return CR_OK;
     if (h->record_every <= 0) return run_iters(h, k);
@@ -903,7 +1093,7 @@ cr_status cr_iterate(cr_handle h, int64_t k)
 
 cr_status cr_solve(cr_handle h, double tol, int64_t max_iter, int64_t *iters_done)
 {
-    CR_TRY(usable(h));
+    CR_TRY(papg_only(h));
     if (iters_done) *iters_done = 0;
     if (max_iter < 0 || !(tol >= 0.0)) return fail(h, CR_EINVAL, "bad tol/max_iter");
     CR_CUDA(h, cudaMemsetAsync(&h->P.st->converged, 0, sizeof(int), h->stream));
@@ -933,7 +1123,7 @@ cr_status cr_solve(cr_handle h, double tol, int64_t max_iter, int64_t *iters_don
 
 cr_status cr_kkt_residual(cr_handle h, double *kkt, double *infeas_norm, double *gap_norm)
 {
-    CR_TRY(usable(h));
+    CR_TRY(papg_only(h));
     CR_CUDA(h, cudaMemsetAsync(&h->P.st->converged, 0, sizeof(int), h->stream));
     CR_TRY(launch_phase(h, crk::PH_KKT64, h->iters, -1.0));
     CR_TRY(launch_phase(h, crk::PH_DECIDE64, h->iters, -1.0, 1));
@@ -947,7 +1137,7 @@ cr_status cr_kkt_residual(cr_handle h, double *kkt, double *infeas_norm, double 
 
 cr_status cr_objective(cr_handle h, double *primal, double *dual, double *gap)
 {
-    CR_TRY(usable(h));
+    CR_TRY(papg_only(h));
     std::vector<double> fp((size_t)h->P.G * 8);
     CR_CUDA(h, cudaMemcpyAsync(fp.data(), h->P.foldpart, sizeof(double) * fp.size(), cudaMemcpyDeviceToHost,
                                h->stream));
@@ -1027,7 +1217,7 @@ cr_status cr_profile(cr_handle h, int32_t kind, double *ms, int64_t *launches)
 
 cr_status cr_backward(cr_handle h, const float *dL_dyhat, float *dL_dybar, float *dL_dX)
 {
-    CR_TRY(usable(h));
+    CR_TRY(papg_only(h));
     if (!dL_dyhat || !dL_dybar || !dL_dX) return fail(h, CR_EINVAL, "NULL buffer");
     if (h->record_every <= 0 || h->ckpt.empty() || h->opt.theta_dtype != CR_THETA_F32)
         return fail(h, CR_ESTATE, "cr_backward needs iterations run with record_every > 0 (FP32 theta)");
@@ -1186,6 +1376,77 @@ cr_status cr_get_device_state(cr_handle h, const void **dtheta, int64_t *ld, con
     if (dxi) *dxi = h->P.xi1_64;
     if (dmu) *dmu = h->P.mu[b];
     if (sigma) *sigma = h->sigma;
+    return CR_OK;
+}
+
+void cr_alcc_options_default(cr_alcc_options *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->mu1_scale = 1e3;
+    o->tau1_rel = 1e-2;
+    o->alpha1_rel = 1e-2;
+    o->c = 2.0;
+    o->kappa = 0.1;
+}
+
+cr_status cr_alcc_create(const double *X, const double *ybar, int64_t N, int32_t n, const cr_options *opt,
+                         const cr_alcc_options *aopt, cr_handle *out)
+{
+    if (!out) return create_error(CR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (check_inputs(X, ybar, N, n) != CR_OK)
+        return create_error(CR_EINVAL, "need X, ybar finite, 1 <= n <= 32 and N >= n + 1");
+    cr_alcc_options a;
+    if (aopt) a = *aopt;
+    else cr_alcc_options_default(&a);
+    std::vector<double> Xv(X, X + (size_t)N * n), yv(ybar, ybar + N);
+    return finish_create(create_impl(Xv, yv, N, n, opt, out, 0, &a), out);
+}
+
+cr_status cr_alcc_iterate(cr_handle h, int64_t k, int64_t *inner)
+{
+    CR_TRY(alcc_only(h));
+    if (k < 0) return fail(h, CR_EINVAL, "k < 0");
+    for (int64_t i = 0; i < k; ++i) {
+        long long it = 0;
+        CR_TRY(alcc_outer(h, &it));
+        if (inner) inner[i] = it;
+    }
+    return CR_OK;
+}
+
+cr_status cr_alcc_solve(cr_handle h, double tol, int64_t max_outer, int64_t *outer_done)
+{
+    CR_TRY(alcc_only(h));
+    if (outer_done) *outer_done = 0;
+    if (max_outer < 0 || !(tol >= 0.0)) return fail(h, CR_EINVAL, "bad tol/max_outer");
+    for (int64_t i = 0; i < max_outer; ++i) {
+        CR_TRY(alcc_outer(h, nullptr));
+        if (outer_done) *outer_done = i + 1;
+        if (h->a_metrics[0] <= tol) return CR_OK;
+    }
+    return CR_NOT_CONVERGED;
+}
+
+cr_status cr_alcc_metrics(cr_handle h, double *kkt, double *stat, double *pri, double *comp)
+{
+    CR_TRY(alcc_only(h));
+    if (!h->a_have_metrics) return fail(h, CR_ESTATE, "no outer iteration has run");
+    if (kkt) *kkt = h->a_metrics[0];
+    if (stat) *stat = h->a_metrics[1];
+    if (pri) *pri = h->a_metrics[2];
+    if (comp) *comp = h->a_metrics[3];
+    return CR_OK;
+}
+
+cr_status cr_alcc_info(cr_handle h, int64_t *outer, int64_t *inner_total, double *mu, int64_t *lmax_next)
+{
+    CR_TRY(alcc_only(h));
+    if (outer) *outer = h->iters;
+    if (inner_total) *inner_total = h->a_inner_total;
+    if (mu) *mu = h->a_mu;
+    if (lmax_next) *lmax_next = alcc_lmax(h);
     return CR_OK;
 }
 
