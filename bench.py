@@ -426,6 +426,90 @@ def run_sumexp(args):
     print(json.dumps(line))
 
 
+def run_alcc(args):
+    """ALCC with the MAPG inner solver on the full problem (Sec. II-D), recipe (2) at N=20,000.
+
+    One MAPG iteration reads the multiplier array once (4 bytes per pair, nothing written) and
+    runs two FP64 row folds.  Its device time is the difference of two outer iterations with
+    fixed MAPG counts K1 < K2 divided by K2 - K1, so the once-per-outer passes (theta update, KKT)
+    cancel.  Also: time to ALCC KKT 5e-3 on recipe (1) (FP32 ALCC floors near 3e-3 there), and the FP64 oracle's MAPG rate on a sample."""
+    import torch
+    import paper_1407_7220_gb300 as crg
+    torch.cuda.set_device(0)
+    N, n = args.N, args.n
+    X, yb, _ = datagen.make(RECIPE, N=N, n=n)
+    K1, K2 = args.warmup, args.warmup + args.steps
+    dev = {}
+    with Clocks(0) as clk:
+        for K in (K1, K2):
+            s = crg.AlccSolver(X, yb, gamma=GAMMA, fixed_inner=K, launch_iters=K, profile=1)
+            s.iterate(1)                       # warm-up outer iteration
+            s.profile(crg.PROFILE_PERSISTENT)
+            _, dt = _sync_time(lambda: s.iterate(1))
+            ms, nl = s.profile(crg.PROFILE_PERSISTENT)
+            dev[K] = (ms, dt)
+            s.close()
+    pairs = N * (N - 1)
+    ms_iter = (dev[K2][0] - dev[K1][0]) / (K2 - K1)
+    wall_iter = (dev[K2][1] - dev[K1][1]) / (K2 - K1)
+    hbm, src = peaks()
+    achieved = 4.0 * pairs / (ms_iter / 1e3) / 1e9
+    line = {"metric": "MAPG pair evaluations/s", "value": pairs / (ms_iter / 1e3), "unit": "pair-evaluations/s",
+            "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_iter, "wall_ms_per_step": 1e3 * wall_iter, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"ALCC+MAPG, {RECIPE} recipe N={N} n={n} gamma={GAMMA}, one FP32 theta array "
+                                   f"({4 * N * N / 1e9:.1f} GB); step = one MAPG iteration"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "peak_source": src, "traffic": None},
+            "clocks": clk.summary()}
+    # time to KKT 3e-3 on recipe (1)
+    Xs, ys, _ = datagen.make("sq2", N=500)
+    a = crg.AlccSolver(Xs, ys, gamma=0.1)
+    (conv, outer), t = _sync_time(lambda: a.solve(5e-3, 12))
+    line["sq2_N500_time_to_kkt_5e-3"] = {"seconds": t, "converged": conv, "outer": outer,
+                                         "mapg_iterations": a.info()["inner_total"], "kkt": a.metrics()["kkt"]}
+    a.close()
+    if not args.no_cpu_baseline:
+        from oracle import alcc as A
+        Ns, Ks = 400, 300
+        Xo, yo, _ = datagen.make(RECIPE, N=Ns, n=n)
+        o = A.Alcc(Xo, yo, GAMMA, A.AlccParams(fixed_inner=Ks))
+        t0 = time.perf_counter()
+        o.outer()
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": Ns * (Ns - 1) * Ks / dt, "unit": "pair-evaluations/s", "cores": 1,
+                                "kind": "oracle", "sample": f"one outer iteration of {Ks} MAPG iterations at "
+                                                            f"N={Ns}, n={n} (FP64 numpy)"}
+    print(json.dumps(line))
+
+
+def run_traces(args):
+    """The small experiment of Sec. III (Figs. Gap_All, Gap_APG, Distance_All): N = 100, n = 5,
+    f0 = 1/2 x^T Q x; duality gap theta^T C eta and infeasibility ||(A_1 y + A_2 xi)_-||_2 (both
+    divided by the N^2 - N pairs, in FP64) of P-APG and of dual gradient ascent along the
+    iterations (every pair its own block, K = N)."""
+    import torch
+    import paper_1407_7220_gb300 as crg
+    torch.cuda.set_device(0)
+    X, yb, _ = datagen.make("xqx")
+    marks = [1, 2, 5, 10, 20, 50, 100, 200, 500, 1000, 2000, 5000]
+    tr = {}
+    for name, mom in (("papg", 1), ("dual_ascent", 0)):
+        s = crg.Solver(X, yb, gamma=0.1, momentum=mom, stochastic_round=1, restart=0)
+        done, rows = 0, []
+        for k in marks:
+            s.iterate(k - done)
+            done = k
+            kk = s.kkt_residual()
+            rows.append({"iter": k, "gap_norm": kk["gap_norm"], "infeas_norm": kk["infeas_norm"], "kkt": kk["kkt"]})
+        tr[name] = rows
+        s.close()
+    line = {"metric": "duality gap and infeasibility traces", "unit": "normalized by N^2 - N", "n_gpus": 1,
+            "dtype": "f32", "data": "synthetic", "traces": tr,
+            "config": {"workload": "xqx recipe N=100 n=5 gamma=0.1 (Sec. III small experiment), FP32 theta"}}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -437,7 +521,7 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--driver", type=int, default=2, help="1 persistent, 2 phase kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="maxaff", choices=["maxaff", "sq2", "lse", "batch", "sumexp"],
+    ap.add_argument("--config", default="maxaff", choices=["maxaff", "sq2", "lse", "batch", "sumexp", "alcc", "traces"],
                     help="workload (default: the headline workload, recipe (2))")
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--batch-iters", type=int, default=20000)
@@ -446,7 +530,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.config != "maxaff":
-        return {"sq2": run_sq2, "lse": run_lse, "batch": run_batch, "sumexp": run_sumexp}[args.config](args)
+        return {"sq2": run_sq2, "lse": run_lse, "batch": run_batch, "sumexp": run_sumexp,
+                "alcc": run_alcc, "traces": run_traces}[args.config](args)
     return run_ours(args)
 
 

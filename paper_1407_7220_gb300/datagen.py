@@ -14,6 +14,8 @@ Recipes (NumPy ``default_rng``; default seed = 1000 + recipe index):
   ``batch``    (4) per fit: N_i log-uniform in [64, 4096], n_i in {1, 2, 5},
                    x ~ N(0, I), f0 = ||x||^2 + |x_1|, eps ~ N(0, 0.1^2)      1024 fits
   ``sumexp``   (5) x ~ U[-1,1]^n, f0 = sum_j exp(x_j / 2), eps ~ N(0, 0.1^2) N=5000, n=5
+  ``xqx``      (6) the small experiment of Sec. III: Lambda (n x n), x and eps with i.i.d.
+                   N(0, 1) entries, f0 = 1/2 x^T Q x with Q = Lambda^T Lambda  N=100, n=5
 """
 from __future__ import annotations
 
@@ -25,6 +27,7 @@ RECIPES = {
     "lse": dict(index=3, N=100000, n=20),
     "batch": dict(index=4, B=1024),
     "sumexp": dict(index=5, N=5000, n=5),
+    "xqx": dict(index=6, N=100, n=5),
 }
 
 
@@ -59,6 +62,11 @@ def make(recipe: str, N: int | None = None, n: int | None = None, seed: int | No
         X = rng.uniform(-1.0, 1.0, size=(N, n))
         f0 = np.exp(0.5 * X).sum(axis=1)
         eps = rng.normal(0.0, 0.1, size=N)
+    elif recipe == "xqx":
+        Lam = rng.normal(0.0, 1.0, size=(n, n))
+        X = rng.normal(0.0, 1.0, size=(N, n))
+        f0 = 0.5 * np.einsum("lj,jk,lk->l", X, Lam.T @ Lam, X)
+        eps = rng.normal(0.0, 1.0, size=N)
     else:
         raise ValueError(f"recipe {recipe!r} has no single instance; use make_batch")
     return np.ascontiguousarray(X), f0 + eps, f0

