@@ -250,7 +250,10 @@ template <> struct Store<float> {
             r0 = __uint_as_float(b0 + __float_as_uint(fl0) - 0x4B400001u);
             r1 = __uint_as_float(b1 + __float_as_uint(fl1) - 0x4B400001u);
         }
-        return f2_make(v0 > 0.0f ? r0 : 0.0f, v1 > 0.0f ? r1 : 0.0f);
+        // projection on theta >= 0 as max(r, 0): for v > 0 the rounded r is >= 0; for v < 0 it is
+        // negative, and for v = -0 or +0 it is 0, a NaN pattern (max gives 0) or, with SR, the
+        // smallest denormal (a > 0 rounded up, as unbiased rounding asks)
+        return f2_make(fmaxf(r0, 0.0f), fmaxf(r1, 0.0f));
     }
     __device__ static __forceinline__ Vec pack2(const f2 (&s)[2])
     {

@@ -5,8 +5,9 @@ the same seeded inputs.  With a fixed number of MAPG iterations per outer iterat
 take the same steps, so the iterates are compared element by element: the GPU's pair pass is
 FP32 (one rounding per residual and compensated FP32 partial sums), its folds FP64, which keeps
 the fitted values within 1e-6 relative and the multiplier array within 1e-6 of the data scale
-(the FP32 rounding of the residuals it is formed from); the KKT terms agree within 1e-3 relative.  With the paper's stopping rule the inner counts of the first outer iterations match the
-oracle's; converged runs are compared with the exact solution of (regularize).
+(the FP32 rounding of the residuals it is formed from); the KKT terms agree within 1e-3
+relative.  With the paper's stopping rule the inner counts of the first outer iterations match
+the oracle's; converged runs are compared with the exact solution of (regularize).
 """
 import numpy as np
 import pytest
