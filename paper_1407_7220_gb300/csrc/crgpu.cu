@@ -644,7 +644,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     long long S = (N + crk::kW - 1) / crk::kW;
     long long total = S * N;
     int G = o.grid > 0 ? o.grid : std::max(1, max_coresident);
-    const long long min_units = 64;   // keep at least 64 (stripe,row) units per CTA
+    const long long min_units = 40;   // keep at least 40 (stripe,row) units per CTA (N = 500: 25 CTAs, measured best)
     if (o.grid <= 0) G = (int)std::max<long long>(1, std::min<long long>(G, total / min_units));
     h->persistent_ok = coop && per_sm > 0 && G <= max_coresident;
     if (np_override > 0) h->persistent_ok = false;   // batch member: driven by the batch kernel only
