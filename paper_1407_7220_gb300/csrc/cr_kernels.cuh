@@ -282,7 +282,7 @@ template <> struct Store<__nv_bfloat16> {
         if (SR) b += rnd16;                                        // stochastic: add uniform 16-bit noise, truncate
         else b += 0x7FFFu + ((b >> 16) & 1u);                      // round to nearest even
         b &= 0xFFFF0000u;
-        return v > 0.0f ? __uint_as_float(b) : 0.0f;
+        return fmaxf(__uint_as_float(b), 0.0f);   // the rounding keeps the sign: v <= 0 gives 0
     }
     __device__ static __forceinline__ Vec pack(const float (&s)[4])
     {
@@ -343,7 +343,7 @@ template <> struct Store<__half> {
         } else {
             r = __half2float(__float2half_rn(sv));
         }
-        return v > 0.0f ? r : 0.0f;
+        return r;   // sv = 0 for v <= 0, and both roundings keep 0
     }
     __device__ static __forceinline__ Vec pack(const float (&s)[4])
     {
@@ -787,6 +787,11 @@ __device__ __forceinline__ void pair_stage_rows(const TS *tcur, const TS *tprv, 
             const float4 t4 = *reinterpret_cast<const float4 *>(rec + rl * REC + q);
             rv[q] = t4.x; rv[q + 1] = t4.y; rv[q + 2] = t4.z; rv[q + 3] = t4.w;
         }
+        // a row past the segment has no record in the stage (the copy moves the segment's rows
+        // only): whatever the slot holds must not reach the accumulators as 0 * x
+        if (MASK && !valid)
+#pragma unroll
+            for (int q = 0; q < REC; ++q) rv[q] = 0.0f;
         f2 xb[NP];   // (x_k, x_k) of this row
 #pragma unroll
         for (int k = 0; k < NP; ++k) xb[k] = f2_make(rv[1 + k], rv[1 + k]);

@@ -191,3 +191,15 @@ def test_bounded_barrier_wait_reports_timeout_and_context_survives(crg):
     t = crg.Solver(X, yb)
     t.iterate(2)
     assert np.isfinite(t.solution()[0]).all()
+
+
+@pytest.mark.parametrize("N,n,grid,driver", [(300, 5, 40, 1), (300, 5, 75, 2), (800, 10, 80, 1), (97, 2, 24, 1)])
+def test_segments_shorter_than_the_ring(crg, N, n, grid, driver):
+    # every CTA owns a few rows (often one partial stage): the stage slots past the segment hold
+    # no row records, and the iterates must not depend on what those slots contain
+    X, yb, _ = datagen.make("sumexp" if n == 5 else ("maxaff" if n == 10 else "sq2"), N=N, n=n)
+    g, o = _pair(crg, X, yb, 6, stochastic_round=0, restart=0, grid=grid, driver=driver)
+    y, xi = g.solution()
+    assert np.isfinite(y).all() and np.isfinite(xi).all()
+    assert _rel(y, o.y_hat) <= 2e-6
+    assert np.abs(xi - o.xi).max() <= 2e-4 * max(1.0, np.abs(o.xi).max())
