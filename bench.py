@@ -166,7 +166,7 @@ def run_reference(args):
 # pairs); keyed by (engine, theta dtype, padded n).  A kernel change invalidates an entry.
 TRAFFIC_BYTES_PER_PAIR = {
     ("cuda_cores", "f32", 10): (519.218859e6 + 222.125824e6) / (8000 * 7999),
-    # ("tensor_cores", "bf16", 20): re-capture pending after the 16-bit projection change
+    ("tensor_cores", "bf16", 20): (742.873728e6 + 278.586368e6) / (12000 * 11999),
 }
 
 
