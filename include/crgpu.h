@@ -248,7 +248,10 @@ typedef struct {
     int64_t lmax_cap;      /* > 0: at most this many MAPG iterations per outer iteration; 0: ell^max_k only */
     int64_t fixed_inner;   /* > 0: every MAPG call runs exactly this many iterations (stopping test off) */
     int64_t launch_iters;  /* MAPG iterations per cooperative launch; 0 = chosen from N */
-    double reserved[4];
+    double mu_max_scale;   /* NOT IN THE PAPER.  > 0: mu_k stops growing at mu_max_scale / sigma_max^2(A_1)
+                              (the multiplier update alone then drives feasibility); 0 = the paper's
+                              unbounded mu_{k+1} = c mu_k */
+    double reserved[3];
 } cr_alcc_options;
 
 /* Fills *o with the defaults documented above. */

@@ -157,6 +157,7 @@ class AlccParams:
     kappa: float = 0.1
     lmax_cap: int = 1 << 62          # optional bound on MAPG iterations per call (none in the paper)
     fixed_inner: int = 0             # > 0: every MAPG call runs exactly this many iterations
+    mu_max_scale: float = 0.0        # NOT IN THE PAPER: > 0 caps mu_k at mu_max_scale / sigma_max^2(A_1)
 
 
 @dataclass
@@ -208,6 +209,8 @@ class Alcc:
         m = np.maximum(self.theta - G, 0.0)                             # (A_1 y + A_2 xi - theta_k)_-
         np.fill_diagonal(m, 0.0)
         mu_next = p.c * self.mu                                         # step 5
+        if p.mu_max_scale > 0.0:                                        # optional cap (not in the paper)
+            mu_next = min(mu_next, max(self.mu, p.mu_max_scale / self.s2a1))
         self.theta = (self.mu / mu_next) * m                            # step 4
         lam = mu_next * self.theta                                      # multiplier estimate
         shrink = (p.c * float(self.k) ** (1.0 + p.kappa)) ** 2

@@ -68,7 +68,8 @@ class AlccOptions(ctypes.Structure):
     _fields_ = [
         ("mu1_scale", ctypes.c_double), ("tau1_rel", ctypes.c_double), ("alpha1_rel", ctypes.c_double),
         ("c", ctypes.c_double), ("kappa", ctypes.c_double), ("lmax_cap", ctypes.c_int64),
-        ("fixed_inner", ctypes.c_int64), ("launch_iters", ctypes.c_int64), ("reserved", ctypes.c_double * 4),
+        ("fixed_inner", ctypes.c_int64), ("launch_iters", ctypes.c_int64), ("mu_max_scale", ctypes.c_double),
+        ("reserved", ctypes.c_double * 3),
     ]
 
 

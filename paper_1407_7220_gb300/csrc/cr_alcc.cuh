@@ -152,9 +152,9 @@ __device__ void phase_mapg_step(const Params &P, const AlccStep &S, long long el
     }
 }
 
-// MAPG steps 6-9: the same decision in every CTA.  The pair pass reads y and xi as FP32 copies,
-// so a step shorter than their resolution (res_rel = 2^-23 times the norm) cannot change the next
-// gradient: the thresholds are taken at least that large.
+// MAPG steps 6-9: the same decision in every CTA.  The thresholds are taken no smaller than
+// res_rel times the norms of y and xi: a shorter step cannot change the next gradient, whose
+// active terms the pair pass evaluates from the FP64 point.
 __device__ __forceinline__ bool mapg_returns(const Params &P, const AlccStep &S, long long ell, int *s_flag)
 {
     if (threadIdx.x < 32) {

@@ -94,6 +94,8 @@ struct Params {
     double gamma, inv_gamma, L, invL_d, shift, sigma;
     float invL;
     float st_scale, st_inv_scale;   // theta storage scale (FP16 only; 1 otherwise)
+    float xmax;                     // max |x_lk| over the data
+    float alcc_delta;               // ALCC passes: relative bound of the FP32 residual's error, (n + 4) 2^-23
     int momentum, restart, sr;
     int fuse;           // 1: foldA(l) also performs foldB(l+1) (plain P-APG: beta needs no reduction)
     double restart_tol;
@@ -757,6 +759,18 @@ template <typename TS, int NP, int TILES = 2> struct PairSmem {
     static_assert(tile_bytes % 128 == 0 && rec_bytes % 128 == 0, "stage buffers must stay 128-byte aligned");
 };
 
+// theta - g_p in FP64 for pair (l1, l2) from the folds' FP64 point (y, xi)^(2) and X: the ALCC
+// passes take it for the pairs whose FP32 estimate of theta - g is close to 0, since the
+// multiplier estimate mu_k (g - theta)_- multiplies any absolute error in it by mu_k.
+static __device__ __noinline__ double alcc_exact_margin(const Params &P, long long l1, long long l2, float theta)
+{
+    const int n = P.n;
+    double g = __ldcg(P.ay2 + l1) - __ldcg(P.ay2 + l2);
+    for (int k = 0; k < n; ++k)
+        g -= __ldcg(P.axi2 + l2 * n + k) * (__ldg(P.X64 + l1 * n + k) - __ldg(P.X64 + l2 * n + k));
+    return (double)theta - g;
+}
+
 // The kRPW rows (rg, rg + kWR, ...) of one pipeline stage for one consumer warp, 4 columns per
 // lane held as two f32x2 column pairs.  MASK handles the diagonal (l1 == l2), columns >= N
 // and rows past the segment; stages without any of these take the unmasked instantiation.
@@ -770,7 +784,7 @@ __device__ __forceinline__ void pair_stage_rows(const TS *tcur, const TS *tprv, 
                                                 const f2 (&ccol)[2], const f2 (&nxi)[2][NP], f2 (&acc)[2][NP],
                                                 f2 (&csum)[2], f2 beta2, f2 ninvL2, float invL, uint32_t hcol,
                                                 float scl, float iscl, f2 iscl2, TS *__restrict__ nxt, bool vec_ok,
-                                                float (&rsv)[kRPW])
+                                                float (&rsv)[kRPW], const Params &Pm, const f2 (&cbnd)[2])
 {
     using St = Store<TS>;
     using Vec = typename St::Vec;
@@ -816,7 +830,28 @@ __device__ __forceinline__ void pair_stage_rows(const TS *tcur, const TS *tprv, 
                 if (k & 1) g1 = f2_fma(nxi[P][k], xb[k], g1);
                 else g0 = f2_fma(nxi[P][k], xb[k], g0);
             }
-            f2 sv = St::template round2<SR>(th2, f2_add(g0, g1), ninvL2, invL, hP[P], scl);   // Pi_{>=0}(theta^(2) - g/L)
+            f2 sv;
+            if (MODE == PM_PAPG) {
+                sv = St::template round2<SR>(th2, f2_add(g0, g1), ninvL2, invL, hP[P], scl);   // Pi_{>=0}(theta^(2) - g/L)
+            } else {
+                // ALCC: invL * max(0, theta - g).  Where the FP32 estimate e = theta - g lies within
+                // kNear error bounds of 0 (every active pair near the solution, where e ~ lambda/mu_k),
+                // theta - g is taken in FP64; farther out e keeps at least 10 correct bits
+                constexpr float kNear = 1024.0f;
+                float t0, t1, q0, q1, b0, b1;
+                f2_split(tc[P], t0, t1);
+                f2_split(f2_add(g0, g1), q0, q1);
+                f2_split(cbnd[P], b0, b1);
+                const float ay = fabsf(rv[0]);
+                const long long c = col0 + 2 * P;
+                const float e0 = t0 - q0, e1 = t1 - q1;
+                float s0 = fmaxf(e0, 0.0f) * invL, s1 = fmaxf(e1, 0.0f) * invL;
+                if ((!MASK || (valid && c < N && c != rr)) && fabsf(e0) <= kNear * Pm.alcc_delta * (ay + b0))
+                    s0 = (float)fmax(0.0, (double)invL * alcc_exact_margin(Pm, rr, c, t0));
+                if ((!MASK || (valid && c + 1 < N && c + 1 != rr)) && fabsf(e1) <= kNear * Pm.alcc_delta * (ay + b1))
+                    s1 = (float)fmax(0.0, (double)invL * alcc_exact_margin(Pm, rr, c + 1, t1));
+                sv = f2_make(s0, s1);
+            }
             if (MASK) {
                 float s0, s1;
                 f2_split(sv, s0, s1);
@@ -1017,6 +1052,24 @@ __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, 
             for (int q = 0; q < NP; ++q)
                 nxi[P2][q] = f2_make(va ? -__ldcg(P.xi2 + ca * NP + q) : 0.0f, vb ? -__ldcg(P.xi2 + cb * NP + q) : 0.0f);
         }
+        // ALCC passes: |ccol| + max|x| ||xi||_1 of each column (with |y_l1|, the size of the terms of g)
+        f2 cbnd[2];
+#pragma unroll
+        for (int P2 = 0; P2 < 2; ++P2) {
+            cbnd[P2] = 0ull;
+            if (MODE != PM_PAPG) {
+                float ca, cb, sa = 0.0f, sb = 0.0f;
+                f2_split(ccol[P2], ca, cb);
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    float xa, xb2;
+                    f2_split(nxi[P2][q], xa, xb2);
+                    sa += fabsf(xa);
+                    sb += fabsf(xb2);
+                }
+                cbnd[P2] = f2_make(fabsf(ca) + P.xmax * sa, fabsf(cb) + P.xmax * sb);
+            }
+        }
         f2 acc[2][NP], csum[2];
 #pragma unroll
         for (int P2 = 0; P2 < 2; ++P2) {
@@ -1045,14 +1098,14 @@ __device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, 
                 const bool fast = !ragged && (r + kRS <= r1) && !(r < colw + 128 && colw < r + kRS);
                 if (sr) {
                     if (fast)
-                        pair_stage_rows<TS, NP, false, true, MODE>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn);
+                        pair_stage_rows<TS, NP, false, true, MODE>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn, P, cbnd);
                     else
-                        pair_stage_rows<TS, NP, true, true, MODE>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn);
+                        pair_stage_rows<TS, NP, true, true, MODE>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn, P, cbnd);
                 } else {
                     if (fast)
-                        pair_stage_rows<TS, NP, false, false, MODE>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn);
+                        pair_stage_rows<TS, NP, false, false, MODE>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn, P, cbnd);
                     else
-                        pair_stage_rows<TS, NP, true, false, MODE>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn);
+                        pair_stage_rows<TS, NP, true, false, MODE>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn, P, cbnd);
                 }
             }
             __syncwarp();

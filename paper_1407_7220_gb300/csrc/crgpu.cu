@@ -607,7 +607,8 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
         if (o.theta_dtype != CR_THETA_F32) return fail(h, CR_EINVAL, "ALCC keeps theta in FP32");
         if (o.pair_engine == CR_PAIR_TENSOR_CORES) return fail(h, CR_EINVAL, "ALCC runs the CUDA-core pair pass");
         if (!(aopt->c > 1.0) || !(aopt->kappa > 0.0) || !(aopt->mu1_scale > 0.0) || !(aopt->tau1_rel > 0.0) ||
-            !(aopt->alpha1_rel > 0.0) || aopt->lmax_cap < 0 || aopt->fixed_inner < 0 || aopt->launch_iters < 0)
+            !(aopt->alpha1_rel > 0.0) || aopt->lmax_cap < 0 || aopt->fixed_inner < 0 || aopt->launch_iters < 0 ||
+            !(aopt->mu_max_scale >= 0.0))
             return fail(h, CR_EINVAL, "ALCC options: need c > 1, kappa > 0, positive scales, counts >= 0");
         o.record_every = 0;
         o.pair_engine = CR_PAIR_CUDA_CORES;
@@ -705,6 +706,12 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     P.sigma = h->sigma;
     P.st_scale = 1.0f;
     P.st_inv_scale = 1.0f;
+    {
+        double xm = 0.0;
+        for (double v : X) xm = std::max(xm, std::fabs(v));
+        P.xmax = (float)(xm * (1.0 + 1e-6));   // rounded up
+        P.alcc_delta = (float)((n + 4) * std::ldexp(1.0, -23));
+    }
     if (o.theta_dtype == CR_THETA_F16) {
         P.st_scale = std::ldexp(1.0f, o.fp16_exponent);
         P.st_inv_scale = std::ldexp(1.0f, -o.fp16_exponent);
@@ -886,7 +893,8 @@ cr_status alcc_outer(cr_ctx *h, long long *inner)
     const double Ly = 1.0 / h->a_mu + h->a_s2a1;        // step 1
     const double Lxi = gamma / h->a_mu + h->a_s2a2;
     const long long lmax = alcc_lmax(h);                // step 2
-    const double mu_next = A.c * h->a_mu;               // step 5
+    double mu_next = A.c * h->a_mu;                     // step 5
+    if (A.mu_max_scale > 0.0) mu_next = std::min(mu_next, std::max(h->a_mu, A.mu_max_scale / h->a_s2a1));
     crk::AlccStep S{};
     S.inv_mu = 1.0 / h->a_mu;
     S.gamma_inv_mu = gamma / h->a_mu;
@@ -897,7 +905,8 @@ cr_status alcc_outer(cr_ctx *h, long long *inner)
     S.Bxi = h->a_Bxi;
     S.alpha_y = A.fixed_inner > 0 ? 0.0 : h->a_alpha_y;
     S.alpha_xi = A.fixed_inner > 0 ? 0.0 : h->a_alpha_xi;
-    S.res_rel = A.fixed_inner > 0 ? 0.0 : std::ldexp(1.0, -23);   // resolution of the FP32 column data
+    // steps far below the FP64 resolution of (y, xi) cannot change the FP64 margins of the active pairs
+    S.res_rel = A.fixed_inner > 0 ? 0.0 : std::ldexp(1.0, -40);
     S.lmax = lmax;
     S.a = (float)(h->a_mu / mu_next);
     const double pairs = (double)h->N * (double)h->N;

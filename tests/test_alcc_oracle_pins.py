@@ -192,3 +192,22 @@ def test_planted_adjoint_sign_error_is_caught(monkeypatch):
     fd = (_explicit_value(y, xi + e, tv, y + 0.3, 0.3, 0.05, A1, A2)
           - _explicit_value(y, xi - e, tv, y + 0.3, 0.3, 0.05, A1, A2)) / (2 * eps)
     assert abs(gxi[2, 1] - fd) > 1e-3
+
+
+def test_optional_mu_cap_schedule():
+    # not in the paper: mu_{k+1} = min(c mu_k, mu_max), mu_max = mu_max_scale / sigma_max^2(A_1)
+    X, yb, _ = datagen.make("sq2", N=10, n=2, seed=3)
+    prm = A.AlccParams(fixed_inner=3, mu_max_scale=3e3)
+    s = A.Alcc(X, yb, 0.1, prm)
+    mus = [s.mu]
+    for _ in range(4):
+        s.outer()
+        mus.append(s.mu)
+    mu_max = 3e3 / A.sigma2_A1(10)
+    assert mus == pytest.approx([1e3 / 20, 2e3 / 20, mu_max, mu_max, mu_max], rel=1e-14)
+    # with mu fixed, theta_{k+1} = (A_1 y_k + A_2 xi_k - theta_k)_- (step 4 with mu_k / mu_{k+1} = 1)
+    y, xi, th = s.y.copy(), s.xi.copy(), s.theta.copy()
+    s.outer()
+    m = np.maximum(th - A.constraint_values(s.y, s.xi, X), 0.0)
+    np.fill_diagonal(m, 0.0)
+    np.testing.assert_allclose(s.theta, m, rtol=0, atol=1e-15)
