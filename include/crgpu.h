@@ -170,6 +170,16 @@ cr_status cr_get_info(cr_handle h, int64_t *iters, int64_t *restarts, double *L,
  * CR_PAIR_TENSOR_CORES (CR_PAIR_AUTO is decided by n and record_every). */
 cr_status cr_get_engine(cr_handle h, int32_t *engine);
 
+/* The problem constants the solvers derive on the host, without a device: the step constant
+ * bound L = (1 + sigma_max^2(A_1) + sigma_max^2(A_2)) / gamma of cr_options.L (Eq. (eq:lischitz)
+ * with sigma_max^2(C) <= 1 + ||A_1||^2 + ||A_2||^2), the default shift s (after Eq.
+ * (omega_primal)), sigma_max^2(A_1) = 2N and sigma_max^2(A_2) = max_l lambda_max(sum_m (x_m - x_l)
+ * (x_m - x_l)^T) (Fig. `fig:alcc` step 1).  X, ybar: host arrays as for cr_create.  Any output
+ * pointer may be NULL.  CR_EINVAL (message in cr_last_error(NULL)) on bad sizes, non-finite
+ * inputs or gamma <= 0. */
+cr_status cr_problem_constants(const double *X, const double *ybar, int64_t N, int32_t n, double gamma, double *L,
+                               double *shift, double *sigma2_A1, double *sigma2_A2);
+
 /* Kernel timing collected since the last call when cr_options.profile = 1 (CUDA events on the
  * handle's stream around each launch).  kind: 0 = pair pass (Step 2 + fused adjoint, the
  * multiplier-array stream), 1 = folds (Step 1 and reductions), 2 = KKT passes, 3 = persistent

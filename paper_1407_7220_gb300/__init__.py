@@ -20,7 +20,8 @@ import threading
 import numpy as np
 
 __all__ = [
-    "CrError", "Options", "Solver", "AlccOptions", "AlccSolver", "lib", "library_path", "exported_symbols",
+    "CrError", "Options", "Solver", "AlccOptions", "AlccSolver", "problem_constants", "lib", "library_path",
+    "exported_symbols",
     "THETA_F32", "THETA_BF16", "THETA_F16", "DRIVER_AUTO", "DRIVER_PERSISTENT", "DRIVER_PHASES",
     "PAIR_AUTO", "PAIR_CUDA_CORES", "PAIR_TENSOR_CORES",
     "CR_OK", "CR_NOT_CONVERGED",
@@ -44,7 +45,7 @@ exported_symbols = (
     "cr_batch_create", "cr_batch_solve", "cr_batch_iterate", "cr_batch_reset", "cr_batch_instance",
     "cr_batch_info", "cr_batch_destroy", "cr_batch_last_error", "cr_backward", "cr_get_engine",
     "cr_alcc_options_default", "cr_alcc_create", "cr_alcc_iterate", "cr_alcc_solve", "cr_alcc_metrics",
-    "cr_alcc_info",
+    "cr_alcc_info", "cr_problem_constants",
 )
 PROFILE_PAIR, PROFILE_FOLD, PROFILE_KKT, PROFILE_PERSISTENT = 0, 1, 2, 3
 
@@ -143,6 +144,8 @@ def lib():
             L.cr_alcc_info.argtypes = [H, i64p, i64p, dp, i64p]
             for name in ("cr_alcc_create", "cr_alcc_iterate", "cr_alcc_solve", "cr_alcc_metrics", "cr_alcc_info"):
                 getattr(L, name).restype = ctypes.c_int
+            L.cr_problem_constants.argtypes = [dp, dp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, dp, dp, dp, dp]
+            L.cr_problem_constants.restype = ctypes.c_int
             L.cr_profile.argtypes = [H, ctypes.c_int32, dp, i64p]
             L.cr_profile.restype = ctypes.c_int
             L.cr_destroy.argtypes = [H]
@@ -292,6 +295,20 @@ class Solver:
                                               ctypes.byref(y), ctypes.byref(xi), ctypes.byref(mu), ctypes.byref(sg)))
         return {"theta": th.value, "ld": ld.value, "X": X.value, "y": y.value, "xi": xi.value, "mu": mu.value,
                 "sigma": sg.value}
+
+
+def problem_constants(X, ybar, gamma: float) -> dict:
+    """cr_problem_constants: L, shift, sigma_max^2(A_1), sigma_max^2(A_2) computed on the host."""
+    Xa = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
+    ya = np.ascontiguousarray(np.asarray(ybar, dtype=np.float64))
+    if Xa.ndim != 2 or ya.shape != (Xa.shape[0],):
+        raise ValueError("X must be (N, n) and ybar (N,)")
+    out = [ctypes.c_double() for _ in range(4)]
+    st = lib().cr_problem_constants(_dptr(Xa), _dptr(ya), Xa.shape[0], Xa.shape[1], float(gamma),
+                                    *(ctypes.byref(v) for v in out))
+    if st != CR_OK:
+        raise CrError(st, lib().cr_last_error(None).decode())
+    return dict(zip(("L", "shift", "sigma2_A1", "sigma2_A2"), (v.value for v in out)))
 
 
 class AlccSolver(Solver):

@@ -1196,6 +1196,20 @@ cr_status cr_get_info(cr_handle h, int64_t *iters, int64_t *restarts, double *L,
     return CR_OK;
 }
 
+cr_status cr_problem_constants(const double *X, const double *ybar, int64_t N, int32_t n, double gamma, double *L,
+                               double *shift, double *sigma2_A1, double *sigma2_A2)
+{
+    if (check_inputs(X, ybar, N, n) != CR_OK || !(gamma > 0.0) || !std::isfinite(gamma))
+        return create_error(CR_EINVAL, "need X, ybar finite, 1 <= n <= 32, N >= n + 1 and gamma > 0");
+    std::vector<double> Xv(X, X + (size_t)N * n), yv(ybar, ybar + N);
+    const double s2a2 = max_block_eig(Xv, N, n);
+    if (L) *L = (1.0 + 2.0 * (double)N + s2a2) / gamma;
+    if (shift) *shift = default_shift(yv);
+    if (sigma2_A1) *sigma2_A1 = 2.0 * (double)N;
+    if (sigma2_A2) *sigma2_A2 = s2a2;
+    return CR_OK;
+}
+
 cr_status cr_get_engine(cr_handle h, int32_t *engine)
 {
     if (!h || !engine) return CR_EINVAL;
