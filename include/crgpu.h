@@ -14,7 +14,8 @@
  * Step 2 is the projected update of the N x N multiplier array, and Steps 3-4
  * are the momentum of Fig. 2.  The y >= 0 rows of C (Eq. (eq:C)) are kept and
  * made inactive by the shift of the observations described after
- * Eq. (omega_primal).
+ * Eq. (omega_primal).  The same multiplier-array machinery also runs ALCC with
+ * its MAPG inner solver (Sec. II-D) on (regularize) directly (cr_alcc_*).
  *
  * Conventions for every entry point:
  *  - Host pointers are plain C arrays; "device" pointers are CUDA device

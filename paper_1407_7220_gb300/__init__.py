@@ -9,7 +9,10 @@ GPU is present, the calls raise.
 
 Names mirror the C ABI (``cr_create``, ``cr_iterate``, ``cr_solve``,
 ``cr_objective``, ``cr_kkt_residual``, ``cr_get_solution``, ...).  The
-``Solver`` class wraps one handle.
+``Solver`` class wraps one handle; ``BatchSolver`` many independent fits;
+``AlccSolver`` the ALCC method with its MAPG inner solver (Sec. II-D) on the
+full problem; ``convex_fit`` the differentiable fit (autograd);
+``problem_constants`` the host-side constants.
 """
 from __future__ import annotations
 
