@@ -52,8 +52,12 @@ typedef enum {
     CR_ESTATE = -6        /* call not valid in the handle's current state */
 } cr_status;
 
-/* Storage type of the multiplier array theta (math is FP32 in every case). */
-enum { CR_THETA_F32 = 0, CR_THETA_BF16 = 1, CR_THETA_F16 = 2 };
+/* Storage type of the multiplier array theta.  F32, BF16, F16: the per-pair math is FP32.
+ * F64: the multipliers and the whole per-pair step (residual, projection, adjoint sums) are
+ * FP64, for problems that must be solved below the KKT floor of FP32 multipliers (measured
+ * near 5e-5 at N = 500, n = 2 with stochastic rounding); n <= 10, CUDA-core pass, single
+ * instances, no record_every.  GB300's FP64 rate makes it the mode for small problems (both arrays in L2). */
+enum { CR_THETA_F32 = 0, CR_THETA_BF16 = 1, CR_THETA_F16 = 2, CR_THETA_F64 = 3 };
 
 /* Iteration driver. */
 enum {
@@ -78,7 +82,7 @@ typedef struct {
     double L;       /* step constant L_g of Eq. (eq:lischitz); <= 0: the closed-form bound
                        (1 + 2N + max_l lambda_max(sum_m (x_m-x_l)(x_m-x_l)^T)) / gamma */
     double shift;   /* observation shift s (after Eq. (omega_primal)); < 0: max(0,-min ybar) + range(ybar) */
-    int32_t theta_dtype;      /* CR_THETA_F32 / _BF16 / _F16 */
+    int32_t theta_dtype;      /* CR_THETA_F32 / _BF16 / _F16 / _F64 */
     int32_t stochastic_round; /* 1: unbiased stochastic rounding of every theta store (counter-based hash) */
     int32_t kkt_every;        /* cr_solve evaluates the KKT residual every this many iterations (>= 1) */
     int32_t momentum;         /* 1: P-APG (Fig. 2); 0: dual gradient ascent (the paper's comparator, Sec. III) */
@@ -213,11 +217,17 @@ cr_status cr_get_device_state(cr_handle h, const void **dtheta, int64_t *ld, con
  *
  * Scratch: a fixed array of 65,536 x 4 doubles (2 MiB) inside the library, held by every
  * device that loads the library until the process exits.  N > 65,536 is rejected with
- * CR_EINVAL (message in cr_last_error(NULL)).  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the array, so calls that overlap on the
- * GPU (for example on two streams at once) race and must be ordered by the caller.  The
- * call allocates nothing: no cudaMalloc, cudaFree or allocating library routine. */
+ * CR_EINVAL (message in cr_last_error(NULL)).  The first call on a device is its set-up: with
+ * that device current it looks up the array's device address (cudaGetSymbolAddress).  Under
+ * CUDA's lazy module loading (the default) that first call is also when the driver loads the
+ * library's module, reserves the 2 MiB and loads the two kernels, so a caller with a fixed
+ * memory budget makes one warm-up call at start-up; later calls on that device change no
+ * device-memory figure.  Make the first call before any stream capture.  The address is kept
+ * per device together with the current context; a device reset (cudaDeviceReset) destroys
+ * that context, and the next call, made in the new context, repeats the set-up.  All calls
+ * share the array, so calls that overlap on the GPU (for example on two streams at once) race
+ * and must be ordered by the caller.  The call allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine. */
 cr_status cr_kkt_residual_noalloc(int64_t N, int32_t n, const float *dtheta, int64_t ld, const double *dX,
                                   const double *dy, const double *dxi, const double *dmu, double sigma, void *stream,
                                   double *dout);

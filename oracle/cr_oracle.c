@@ -49,6 +49,12 @@
 
 #define ORC_API __attribute__((visibility("default")))
 
+/* Loops over rows run on several threads only from this many points on: at smaller N a
+ * parallel region costs more than the loop (the pins run millions of iterations at N = 20).
+ * Scheduling only: every sum below walks its terms in the same order whatever the thread
+ * count, except the reduction clauses of orc_metrics (FP64 sums, order of the partials). */
+#define ORC_PAR_MIN 256
+
 /* ------------------------------------------------------------------------ */
 /* Problem constants                                                         */
 /* ------------------------------------------------------------------------ */
@@ -116,7 +122,7 @@ static double jacobi_max_eig(double *a, int n)
 ORC_API double orc_lipschitz(const double *X, int64_t N, int32_t n, double gamma)
 {
     double lam2 = 0.0;
-#pragma omp parallel
+#pragma omp parallel if (N >= ORC_PAR_MIN)
     {
         double *M = (double *)malloc(sizeof(double) * n * n);
         double local = 0.0;
@@ -151,7 +157,7 @@ ORC_API void orc_eta(const double *theta, const double *mu, const double *X, con
                      int64_t N, int32_t n, double gamma, double *y, double *xi)
 {
     /* row sums: (A_1^T theta) positive part */
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= ORC_PAR_MIN)
     for (int64_t l = 0; l < N; ++l) {
         double r = 0.0;
         for (int64_t m = 0; m < N; ++m)
@@ -160,7 +166,7 @@ ORC_API void orc_eta(const double *theta, const double *mu, const double *X, con
     }
     /* column sums and A_2^T theta; each thread owns a range of columns l and
      * walks the rows m in increasing order (row-major reads). */
-#pragma omp parallel
+#pragma omp parallel if (N >= ORC_PAR_MIN)
     {
         int nt = 1, tid = 0;
 #ifdef _OPENMP
@@ -204,7 +210,7 @@ static inline double pair_row(const double *y, const double *xi, const double *X
 ORC_API void orc_residual(const double *y, const double *xi, const double *X, int64_t N, int32_t n,
                           double *G)
 {
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= ORC_PAR_MIN)
     for (int64_t l1 = 0; l1 < N; ++l1)
         for (int64_t l2 = 0; l2 < N; ++l2) G[l1 * N + l2] = (l1 == l2) ? 0.0 : pair_row(y, xi, X, n, l1, l2);
 }
@@ -230,7 +236,7 @@ ORC_API void orc_metrics(const double *theta, const double *mu, const double *y,
                          double sigma, double *out)
 {
     double maxviol = 0.0, maxcomp = 0.0, sumviol2 = 0.0, thetaG = 0.0;
-#pragma omp parallel for schedule(static) reduction(max : maxviol, maxcomp) reduction(+ : sumviol2, thetaG)
+#pragma omp parallel for schedule(static) reduction(max : maxviol, maxcomp) reduction(+ : sumviol2, thetaG) if (N >= ORC_PAR_MIN)
     for (int64_t l1 = 0; l1 < N; ++l1) {
         for (int64_t l2 = 0; l2 < N; ++l2) {
             if (l1 == l2) continue;
@@ -342,7 +348,7 @@ ORC_API int64_t orc_papg(const double *X, const double *h, int64_t N, int32_t n,
 
         /* Step 2: theta^(1)_l = Pi_{Q_2}(theta^(2)_l - (1/L) C eta_l), written over T2
          * (theta^(2)_l is not needed afterwards).  Q_2 = {theta >= 0}. */
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= ORC_PAR_MIN)
         for (int64_t l1 = 0; l1 < N; ++l1) {
             for (int64_t l2 = 0; l2 < N; ++l2) {
                 if (l1 == l2) continue;
@@ -382,7 +388,7 @@ ORC_API int64_t orc_papg(const double *X, const double *h, int64_t N, int32_t n,
         scal[1] = ell;
 
         /* Step 4: theta^(2)_{l+1} = theta^(1)_l + beta (theta^(1)_l - theta^(1)_{l-1}). */
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= ORC_PAR_MIN)
         for (int64_t l1 = 0; l1 < N; ++l1) {
             for (int64_t l2 = 0; l2 < N; ++l2) {
                 int64_t q = l1 * N + l2;
@@ -445,7 +451,7 @@ ORC_API void orc_papg_jvp(const double *X, const double *ybar, int64_t N, int32_
          *   y = h + sum_m T2[l][m] - sum_m T2[m][l] + mu2,       dy = dybar + (same with dT2) + dmu2
          *   gamma xi_l = sum_m T2[m][l] (x_l - x_m),
          *   gamma dxi_l = sum_m dT2[m][l] (x_l - x_m) + sum_m T2[m][l] (dx_l - dx_m) */
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= ORC_PAR_MIN)
         for (int64_t l = 0; l < N; ++l) {
             double r = 0.0, dr = 0.0, c = 0.0, dc = 0.0;
             for (int64_t m = 0; m < N; ++m) {
@@ -470,7 +476,7 @@ ORC_API void orc_papg_jvp(const double *X, const double *ybar, int64_t N, int32_
             }
         }
         /* Step 2 and its tangent: new = max(0, T2 - g/L), g = y_l1 - y_l2 - xi_l2 (x_l1 - x_l2) */
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= ORC_PAR_MIN)
         for (int64_t l1 = 0; l1 < N; ++l1) {
             for (int64_t l2 = 0; l2 < N; ++l2) {
                 const size_t q = (size_t)l1 * N + l2;
@@ -499,7 +505,7 @@ ORC_API void orc_papg_jvp(const double *X, const double *ybar, int64_t N, int32_
         const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
         const double beta = (t - 1.0) / tn;
         t = tn;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= ORC_PAR_MIN)
         for (int64_t l1 = 0; l1 < N; ++l1)
             for (int64_t l2 = 0; l2 < N; ++l2) {
                 const size_t q = (size_t)l1 * N + l2;
@@ -516,7 +522,7 @@ ORC_API void orc_papg_jvp(const double *X, const double *ybar, int64_t N, int32_
         }
     }
     /* fitted values at theta^(1)_K = P: yhat = ybar + A_1^T P + muP */
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (N >= ORC_PAR_MIN)
     for (int64_t l = 0; l < N; ++l) {
         double r = 0.0, dr = 0.0;
         for (int64_t m = 0; m < N; ++m) {

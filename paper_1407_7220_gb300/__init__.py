@@ -25,7 +25,7 @@ import numpy as np
 __all__ = [
     "CrError", "Options", "Solver", "AlccOptions", "AlccSolver", "problem_constants", "lib", "library_path",
     "exported_symbols",
-    "THETA_F32", "THETA_BF16", "THETA_F16", "DRIVER_AUTO", "DRIVER_PERSISTENT", "DRIVER_PHASES",
+    "THETA_F32", "THETA_BF16", "THETA_F16", "THETA_F64", "DRIVER_AUTO", "DRIVER_PERSISTENT", "DRIVER_PHASES",
     "PAIR_AUTO", "PAIR_CUDA_CORES", "PAIR_TENSOR_CORES",
     "CR_OK", "CR_NOT_CONVERGED",
 ]
@@ -34,11 +34,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(HERE, "libcrgpu.so")
 
 CR_OK, CR_NOT_CONVERGED, CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ETIMEOUT, CR_ENUMERIC, CR_ESTATE = 0, 1, -1, -2, -3, -4, -5, -6
-THETA_F32, THETA_BF16, THETA_F16 = 0, 1, 2
+THETA_F32, THETA_BF16, THETA_F16, THETA_F64 = 0, 1, 2, 3
 DRIVER_AUTO, DRIVER_PERSISTENT, DRIVER_PHASES = 0, 1, 2
 PAIR_AUTO, PAIR_CUDA_CORES, PAIR_TENSOR_CORES = 0, 1, 2
 _DTYPES = {"f32": THETA_F32, "fp32": THETA_F32, "float32": THETA_F32, "bf16": THETA_BF16,
-           "bfloat16": THETA_BF16, "f16": THETA_F16, "fp16": THETA_F16, "float16": THETA_F16}
+           "bfloat16": THETA_BF16, "f16": THETA_F16, "fp16": THETA_F16, "float16": THETA_F16,
+           "f64": THETA_F64, "fp64": THETA_F64, "float64": THETA_F64}
 
 # the C-ABI entry points declared in include/crgpu.h
 exported_symbols = (

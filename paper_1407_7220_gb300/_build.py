@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libcrgpu.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["crgpu.cu", "cr_kern_f32.cu", "cr_kern_bf16.cu", "cr_kern_f16.cu", "cr_kern_alcc.cu", "cr_noalloc.cu"]
+SOURCES = ["crgpu.cu", "cr_kern_f32.cu", "cr_kern_bf16.cu", "cr_kern_f16.cu", "cr_kern_f64.cu", "cr_kern_alcc.cu",
+           "cr_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,13 @@
+// Instantiation of the solver kernels with the multiplier array stored as double.
+#include "cr_launch.cuh"
+
+namespace crk {
+KernelSet kernels_f64(int NP)
+{
+#define CR_CASE(V) \
+    if (NP == V) return make_set<double, V>();
+    CR_NP_LIST_F64(CR_CASE)
+#undef CR_CASE
+    return KernelSet{nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, {nullptr, nullptr, nullptr, nullptr}};
+}
+}  // namespace crk

@@ -117,6 +117,11 @@ struct Params {
     int Q;
     float *colpart;         // [G][slots][cgroups][NP+1][kW]: column partials per CTA, stripe slot and group
     int cgroups;            // column-partial groups per CTA segment: kWR row groups of warps, or 1
+    // FP64 multipliers (theta_dtype F64): the pair pass runs in FP64 on FP64 copies of its
+    // inputs and writes FP64 partials (same layouts as rowrec, ccol2, xi2, rowpart, colpart)
+    int f64;
+    double *rec64, *ccol2_64, *xi2_64;
+    double *rowpart64, *colpart64;
     int tc;                 // 1: the pair pass runs its two products on the tensor cores
     float *xi_tc;           // tensor-core operands (TF32 hi/lo): Xi per stripe, written by every foldB
     float *xr_tc, *xt_tc;   // X rows and [X | 1] transposed per 8-row block (constant)
@@ -633,6 +638,17 @@ __device__ __forceinline__ void foldB_row(const Params &P, int c, int p, long lo
     }
     P.rowrec[l * RecLayout<NP>::REC] = (float)ys;
     P.ccol2[l] = (float)(d - ys);
+    if (P.f64) {
+        // the FP64 pass reads the same column and row data unrounded
+        P.rec64[l * RecLayout<NP>::REC] = ys;
+        P.ccol2_64[l] = d - ys;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            double xi = 0.0;
+            if (k < n) xi = (b1 * __ldcg(P.w[c] + l * n + k) - beta * __ldcg(P.w[p] + l * n + k)) * P.inv_gamma;
+            P.xi2_64[l * NP + k] = xi;
+        }
+    }
     if (P.tc) {
         // Xi of column l as the A operand of the residual product: stripe l/256, column pair
         // (l%256)/2 = lane, even/odd column = MMA; TF32 hi and lo parts
@@ -978,11 +994,30 @@ __device__ __forceinline__ bool produce_stage(const Params &P, unsigned char *st
     return true;
 }
 
+// Step 2 with FP64 multipliers (cr_pair_f64.cuh).
+template <int NP> __device__ void phase_pair_f64(const Params &P, long long ell, long long vc);
+
 // MODE = PM_PAPG: Step 2 of P-APG at iteration ell.  The ALCC modes read and write array 0 only;
 // a = mu_k / mu_{k+1} scales the stored values of PM_ALCC_UPDATE.
 template <typename TS, int NP, int MODE = PM_PAPG>
-__device__ void phase_pair(const Params &P, long long ell, unsigned char *smem, uint64_t *full, uint64_t *empty,
-                           unsigned long long &kstage, long long vc, float a = 1.0f)
+__device__ void phase_pair_stream(const Params &P, long long ell, unsigned char *smem, uint64_t *full,
+                                  uint64_t *empty, unsigned long long &kstage, long long vc, float a = 1.0f);
+
+template <typename TS, int NP, int MODE = PM_PAPG>
+__device__ __forceinline__ void phase_pair(const Params &P, long long ell, unsigned char *smem, uint64_t *full,
+                                           uint64_t *empty, unsigned long long &kstage, long long vc, float a = 1.0f)
+{
+    if constexpr (std::is_same<TS, double>::value) {
+        static_assert(MODE == PM_PAPG, "FP64 multipliers: P-APG only");
+        phase_pair_f64<NP>(P, ell, vc);
+    } else {
+        phase_pair_stream<TS, NP, MODE>(P, ell, smem, full, empty, kstage, vc, a);
+    }
+}
+
+template <typename TS, int NP, int MODE>
+__device__ void phase_pair_stream(const Params &P, long long ell, unsigned char *smem, uint64_t *full,
+                                  uint64_t *empty, unsigned long long &kstage, long long vc, float a)
 {
     using St = Store<TS>;
     constexpr int TILES = MODE == PM_PAPG ? 2 : 1;
@@ -1159,8 +1194,16 @@ __device__ __forceinline__ double ff_value(float hi, float lo) { return (double)
 // partials in a fixed order (deterministic): R = row sum, Cc = column sum, TX = (Theta^T X)_l,
 // with Theta the array of values the pass produced (theta^(1), or m in the ALCC passes).
 template <int NP>
+__device__ __forceinline__ void gather_adjoint64(const Params &P, long long l, double &R, double &Cc,
+                                                 double (&TX)[NP]);
+
+template <int NP>
 __device__ __forceinline__ void gather_adjoint(const Params &P, long long l, double &R, double &Cc, double (&TX)[NP])
 {
+    if (P.f64) {
+        gather_adjoint64<NP>(P, l, R, Cc, TX);
+        return;
+    }
     const long long N = P.N;
     const int Q4 = P.Q >> 2;   // row partials per row, in float4 units
     // row sum: the Q (>= 2S, zero padded) contiguous partials of row l, independent 16-byte loads
@@ -1218,6 +1261,44 @@ __device__ __forceinline__ void gather_adjoint(const Params &P, long long l, dou
     Cc = ff_value(ch, clo);
 #pragma unroll
     for (int k = 0; k < NP; ++k) TX[k] = ff_value(th[k], tl[k]);
+}
+
+// The same aggregates from the FP64 partials of the FP64 pass, added in FP64 in the same fixed order.
+template <int NP>
+__device__ __forceinline__ void gather_adjoint64(const Params &P, long long l, double &R, double &Cc,
+                                                 double (&TX)[NP])
+{
+    const long long N = P.N;
+    const double *rp = P.rowpart64 + l * P.Q;
+    double r = 0.0;
+    for (int q = 0; q < P.Q; ++q) r += __ldcg(rp + q);
+    R = r;
+    const long long s = l / kW, cl = l - s * kW;
+    const long long ua = s * N, ub = s * N + N - 1;
+    long long c0 = (long long)(((unsigned long long)ua * (unsigned long long)P.G) / (unsigned long long)P.total);
+    while (c0 > 0 && unit_begin(P, c0) > ua) --c0;
+    while (c0 + 1 < P.G && unit_begin(P, c0 + 1) <= ua) ++c0;
+    double cc = 0.0, tx[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) tx[k] = 0.0;
+    long long ubg = unit_begin(P, c0);
+    for (long long cta = c0; cta < P.G && ubg <= ub; ++cta) {
+        const long long unx = unit_begin(P, cta + 1);
+        if (unx > ubg) {
+            const long long fs = ubg / N;
+            const double *cp0 = P.colpart64 + ((cta * P.slots + (s - fs)) * kWR * (NP + 1)) * kW + cl;
+            for (int g = 0; g < kWR; ++g) {
+                const double *cp = cp0 + g * (NP + 1) * kW;
+                cc += __ldcg(cp);
+#pragma unroll
+                for (int k = 0; k < NP; ++k) tx[k] += __ldcg(cp + (1 + k) * kW);
+            }
+        }
+        ubg = unx;
+    }
+    Cc = cc;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) TX[k] = tx[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -1291,11 +1372,28 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red, long lo
 // ---------------------------------------------------------------------------
 // KKT pass at theta^(1)_l: per-pair g = (C eta)_p; FP32 (screen) or FP64
 // ---------------------------------------------------------------------------
+// Four multipliers theta[idx .. idx+3] of the stored array (16-byte aligned), as doubles.
+template <typename TS>
+__device__ __forceinline__ void load_theta4(const TS *th, long long idx, float iscl, double (&o)[4])
+{
+    if constexpr (std::is_same<TS, double>::value) {
+        const double2 a = __ldcg(reinterpret_cast<const double2 *>(th + idx));
+        const double2 b = __ldcg(reinterpret_cast<const double2 *>(th + idx + 2));
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    } else {
+        using St = Store<TS>;
+        float t[4];
+        St::unpack(__ldcg(reinterpret_cast<const typename St::Vec *>(th + idx)), t, iscl);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[j] = (double)t[j];
+    }
+}
+
+// With FP64 multipliers the screen is the FP64 evaluation itself (F64X).
 template <typename TS, int NP, bool F64>
 __device__ void phase_kkt(const Params &P, long long ell, double *red, long long vc)
 {
-    using St = Store<TS>;
-    using Vec = typename St::Vec;
+    constexpr bool F64X = F64 || std::is_same<TS, double>::value;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wc = warp & 1, wr = warp >> 1;
     const int p = (int)(ell & 1);
@@ -1320,9 +1418,9 @@ __device__ void phase_kkt(const Params &P, long long ell, double *red, long long
         float tv_viol = 0.0f, tv_comp = 0.0f, tv_s2 = 0.0f, tv_tg = 0.0f;
         for (long long r = r0 + wr; r < r1; r += kWR) {
             if (!vec_ok) continue;
-            float tc[4];
-            St::unpack(__ldcg((const Vec *)(th + r * ld + col0)), tc, iscl);
-            if (F64) {
+            double tc[4];
+            load_theta4<TS>(th, r * ld + col0, iscl, tc);
+            if (F64X) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const long long l2 = col0 + j;
@@ -1330,9 +1428,9 @@ __device__ void phase_kkt(const Params &P, long long ell, double *red, long long
                     double g = __ldcg(P.y1 + r) - __ldcg(P.y1 + l2);
                     for (int k = 0; k < n; ++k) g -= __ldcg(P.xi1_64 + l2 * n + k) * (__ldg(P.X64 + r * n + k) - __ldg(P.X64 + l2 * n + k));
                     mviol = fmax(mviol, -g);
-                    mcomp = fmax(mcomp, (double)tc[j] * fabs(g));
+                    mcomp = fmax(mcomp, tc[j] * fabs(g));
                     if (g < 0.0) sviol += g * g;
-                    sthg += (double)tc[j] * g;
+                    sthg += tc[j] * g;
                 }
             } else {
                 const float yr = __ldcg(P.yrow1 + r);
@@ -1346,14 +1444,15 @@ __device__ void phase_kkt(const Params &P, long long ell, double *red, long long
                     float g = yr + __ldcg(P.ccol1 + l2);
 #pragma unroll
                     for (int k = 0; k < NP; ++k) g = fmaf(-__ldcg(P.xi1 + l2 * NP + k), xr[k], g);
+                    const float t = (float)tc[j];
                     tv_viol = fmaxf(tv_viol, -g);
-                    tv_comp = fmaxf(tv_comp, tc[j] * fabsf(g));
+                    tv_comp = fmaxf(tv_comp, t * fabsf(g));
                     if (g < 0.0f) tv_s2 = fmaf(g, g, tv_s2);
-                    tv_tg = fmaf(tc[j], g, tv_tg);
+                    tv_tg = fmaf(t, g, tv_tg);
                 }
             }
         }
-        if (!F64) {
+        if (!F64X) {
             mviol = fmax(mviol, (double)tv_viol);
             mcomp = fmax(mcomp, (double)tv_comp);
             sviol += (double)tv_s2;

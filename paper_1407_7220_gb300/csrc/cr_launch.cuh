@@ -4,16 +4,22 @@
 
 #include "cr_kernels.cuh"
 #include "cr_backward.cuh"
+#include "cr_pair_f64.cuh"
 #include "cr_pair_tc.cuh"
 
 namespace crk {
 
 enum Phase : int { PH_FOLDB = 0, PH_PAIR = 1, PH_FOLDA = 2, PH_KKT32 = 3, PH_KKT64 = 4, PH_DECIDE32 = 5, PH_DECIDE64 = 6 };
 
-// Dynamic shared memory of the pair pass (the larger of the CUDA-core and tensor-core layouts).
+// Dynamic shared memory of the pair pass (the larger of the CUDA-core and tensor-core layouts;
+// the FP64 pass stages nothing in shared memory).
 template <typename TS, int NP> constexpr size_t pair_smem_bytes()
 {
-    return PairSmem<TS, NP>::bytes > TcShape<TS, NP>::bytes ? PairSmem<TS, NP>::bytes : TcShape<TS, NP>::bytes;
+    if constexpr (std::is_same<TS, double>::value) {
+        return 0;
+    } else {
+        return PairSmem<TS, NP>::bytes > TcShape<TS, NP>::bytes ? PairSmem<TS, NP>::bytes : TcShape<TS, NP>::bytes;
+    }
 }
 
 // 128-byte aligned base of the dynamic shared memory (TMA destinations).
@@ -285,11 +291,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pair_tc(const __grid_constant
     if (threadIdx.x == 0) s_skip = (__ldcg(&P.st->error) != 0 || __ldcg(&P.st->converged) != 0) ? 1 : 0;
     __syncthreads();
     if (s_skip) return;   // block-uniform
-    unsigned long long kstage = 0, kseg = 0, kgrp = 0;
+    unsigned long long kstage = 0, kseg = 0, kgrp = 0, kch = 0;
     tc_init_pipeline(full, empty);
     tc_init_bars(tcb);
     tc_alloc<TS, NP>(tcb);   // includes a block barrier
-    phase_pair_tc<TS, NP>(P, ell, aligned_smem(sm_raw), full, empty, tcb, kstage, kseg, kgrp, blockIdx.x);
+    phase_pair_tc<TS, NP>(P, ell, aligned_smem(sm_raw), full, empty, tcb, kstage, kseg, kgrp, kch, blockIdx.x);
     tc_free<TS, NP>(tcb);
 }
 
@@ -313,9 +319,14 @@ template <typename TS, int NP> KernelSet make_set()
     KernelSet k;
     k.persistent = (const void *)k_persistent<TS, NP>;
     k.phase = (const void *)k_phase<TS, NP>;
-    k.pair_tc = (const void *)k_pair_tc<TS, NP>;
     k.kkt64_if = (const void *)k_kkt64_if_screened<TS, NP>;
-    k.batch = (const void *)k_batch<TS, NP>;
+    if constexpr (std::is_same<TS, double>::value) {
+        k.pair_tc = nullptr;   // FP64 multipliers: CUDA cores only, single instances only
+        k.batch = nullptr;
+    } else {
+        k.pair_tc = (const void *)k_pair_tc<TS, NP>;
+        k.batch = (const void *)k_batch<TS, NP>;
+    }
     k.smem = pair_smem_bytes<TS, NP>();
     k.NP = NP;
     k.bwd = make_bwd<NP>();
@@ -326,8 +337,13 @@ template <typename TS, int NP> KernelSet make_set()
 #define CR_NP_LIST(X) X(2) X(4) X(5) X(8) X(10) X(16) X(20) X(32)
 constexpr int kMaxN = 32;
 
+// padded n values compiled for FP64 multipliers (n <= 10: its per-lane FP64 accumulators)
+#define CR_NP_LIST_F64(X) X(2) X(4) X(5) X(8) X(10)
+constexpr int kMaxNF64 = 10;
+
 KernelSet kernels_f32(int NP);
 KernelSet kernels_bf16(int NP);
 KernelSet kernels_f16(int NP);
+KernelSet kernels_f64(int NP);
 
 }  // namespace crk

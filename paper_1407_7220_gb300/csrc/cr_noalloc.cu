@@ -7,6 +7,7 @@
 // cr_kkt_residual_noalloc computes the same metrics as cr_kkt_residual from
 // caller-owned device buffers, with its scratch space in a fixed file-scope
 // device array instead of an allocation.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -27,7 +28,29 @@ static __device__ __align__(256) double g_kkt_rows[kMaxRows * kTerms];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-double *g_rows_ptr[kMaxDevices] = {};   // device address of g_kkt_rows, per device
+// Device address of g_kkt_rows per device, with the context it was looked up in.  A host
+// application that resets the device (cudaDeviceReset) destroys that context and the module
+// with it; the next call then runs in a new context and looks the address up again.
+struct RowsAddr {
+    CUcontext ctx;
+    double *ptr;
+};
+RowsAddr g_rows[kMaxDevices] = {};
+
+// cuCtxGetCurrent through the runtime's driver entry point (no link-time libcuda).
+typedef CUresult (*PFN_ctx_get_current)(CUcontext *);
+PFN_ctx_get_current ctx_get_current()
+{
+    static PFN_ctx_get_current fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_ctx_get_current)p;
+    }
+    return fn;
+}
 
 }  // namespace
 
@@ -142,15 +165,25 @@ extern "C" cr_status cr_kkt_residual_noalloc(int64_t N, int32_t n, const float *
     if (dev < 0 || dev >= kMaxDevices) return err(CR_EINVAL, "cr_kkt_residual_noalloc: device index out of range");
     double *rows = nullptr;
     {
-        // first call on this device: look up the device address of the scratch array
+        // set-up, once per device (and again if the device's context was replaced): look up the
+        // device address of the scratch array with this device current.  With lazy module
+        // loading this first lookup also loads the library's module and its 2 MiB array.
+        // Calls from several threads are serialized by the lock.
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_rows_ptr[dev]) {
+        PFN_ctx_get_current get = ctx_get_current();
+        if (!get) return err(CR_ECUDA, "cr_kkt_residual_noalloc: cuCtxGetCurrent is not available from the driver");
+        CUcontext ctx = nullptr;
+        if (get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+        if (!ctx || !g_rows[dev].ptr || g_rows[dev].ctx != ctx) {
             void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_kkt_rows);
+            e = cudaGetSymbolAddress(&p, g_kkt_rows);   // also makes the device's context current
             if (e != cudaSuccess) return err(CR_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            g_rows_ptr[dev] = (double *)p;
+            if (get(&ctx) != CUDA_SUCCESS || !ctx)
+                return err(CR_ECUDA, "cr_kkt_residual_noalloc: no current CUDA context");
+            g_rows[dev].ptr = (double *)p;
+            g_rows[dev].ctx = ctx;
         }
-        rows = g_rows_ptr[dev];
+        rows = g_rows[dev].ptr;
     }
     cudaStream_t s = (cudaStream_t)stream;
     int sms = 0;

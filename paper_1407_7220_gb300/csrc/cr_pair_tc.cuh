@@ -184,15 +184,24 @@ template <typename TS, int NP> struct TcShape {
     static_assert(stage_bytes % 128 == 0 && xi_bytes % 128 == 0 && xg_bytes % 128 == 0 && off_xt % 128 == 0,
                   "stage buffers must stay 128-byte aligned");
     static constexpr size_t bytes = off_stage + kStages * stage_bytes + 128;
+    // D2 (the adjoint product) is accumulated by the tensor cores over chunks of 32 rows only:
+    // their FP32 accumulation truncates (rounds toward zero), so a sum carried over a whole
+    // segment (thousands of MMAs) drifts below the true column sums (measured: the dual value
+    // 2e-4 low at N = 20,000).  Each chunk's D2 is added to FP32 registers (round to nearest)
+    // by the consumer warps, a quarter of the columns per warpgroup.
+    static constexpr int CH = 32 / RS;   // stages per D2 chunk
+    static constexpr int H2 = N2 / 2;    // D2 columns per warpgroup
     // tensor-memory columns: D1 (2 group buffers x {even, odd} x 64 rows), A2 = theta^T
-    // (NA2 buffers x {even hi, odd hi[, even lo, odd lo]} x RS), D2 ({even, odd} x N2)
+    // (NA2 buffers x {even hi, odd hi[, even lo, odd lo]} x RS), D2 (ND2 chunk buffers x {even, odd} x N2)
     static constexpr int A2W = (SPLIT ? 4 : 2) * RS;
     static constexpr int COL_A2 = 4 * GR;
-    static constexpr int NA2_FIT = (512 - COL_A2 - 2 * N2) / A2W;
+    static constexpr int ND2 = (512 - COL_A2 - 4 * N2) / A2W >= 2 ? 2 : 1;
+    static constexpr int NA2_FIT = (512 - COL_A2 - 2 * ND2 * N2) / A2W;
     static constexpr int NA2 = NA2_FIT > 4 ? 4 : NA2_FIT;   // theta^T buffers (what fits in 512 columns)
     static_assert(NA2 >= 2, "tensor memory");
+    static_assert(H2 % 8 == 0 && 32 % RS == 0, "D2 chunk split");
     static constexpr int COL_D1 = 0, COL_D2 = COL_A2 + NA2 * A2W;
-    static constexpr int COLS = COL_D2 + 2 * N2;
+    static constexpr int COLS = COL_D2 + 2 * ND2 * N2;
     static constexpr uint32_t NCOLS = COLS <= 128 ? 128u : (COLS <= 256 ? 256u : 512u);
     static_assert(COLS <= 512, "tensor memory");
     static constexpr uint32_t IDESC1 = umma_idesc_tf32(128, GR);
@@ -204,7 +213,7 @@ struct TcBars {
     uint64_t xgfull[2];              // X rows of a group landed
     uint64_t d1full[2], d1free[2];   // MMA1 of a group done / its D1 read by all consumer warps
     uint64_t a2full[4], a2free[4];   // theta^T of a stage written by all consumer warps / MMA2 of the stage done
-    uint64_t d2done, d2free;         // segment's MMA2 chain done / D2 read by warpgroup 0
+    uint64_t d2done[2], d2free[2];   // a D2 chunk's MMA2 chain done / that D2 buffer read by all consumer warps
     uint64_t xifull;                 // Xi of the segment's stripe landed
     uint64_t drain[2];               // end of pass: every MMA of issuer 1 / issuer 2 done
     uint32_t tmem;
@@ -223,8 +232,10 @@ __device__ __forceinline__ void tc_init_bars(TcBars &B)
             mbar_init(&B.a2full[i], kTcWarps);
             mbar_init(&B.a2free[i], 1);
         }
-        mbar_init(&B.d2done, 1);
-        mbar_init(&B.d2free, 4);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&B.d2done[i], 1);
+            mbar_init(&B.d2free[i], kTcWarps);
+        }
         mbar_init(&B.xifull, 1);
         for (int i = 0; i < 2; ++i) {
             mbar_init(&B.drain[i], 1);
@@ -487,14 +498,14 @@ __device__ __forceinline__ void tc_mma1(uint32_t tb, const TcDesc &D, int xb, in
 // MMA2 of one stage: D2 (+)= Theta^T [X | 1] for the even and the odd columns, K = RS rows
 // (RS/8 blocks of 8); theta^T comes from tensor memory (A2 buffer b).
 template <typename TS, int NP>
-__device__ __forceinline__ void tc_mma2(uint32_t tb, const TcDesc &D, int slot, int b, bool first)
+__device__ __forceinline__ void tc_mma2(uint32_t tb, const TcDesc &D, int slot, int b, bool first, int db)
 {
     using Sh = TcShape<TS, NP>;
     constexpr int N2 = Sh::N2;
     const uint64_t so = (uint64_t)(slot * (uint32_t)(Sh::stage_bytes >> 4));
 #pragma unroll
     for (int eo = 0; eo < 2; ++eo) {
-        const uint32_t d = tb + Sh::COL_D2 + N2 * eo;
+        const uint32_t d = tb + Sh::COL_D2 + 2 * N2 * db + N2 * eo;
         const uint32_t a = tb + Sh::COL_A2 + Sh::A2W * b + Sh::RS * eo;
 #pragma unroll
         for (int s = 0; s < Sh::RS / 8; ++s) {
@@ -625,10 +636,12 @@ __device__ __forceinline__ void tc_issue_mma1(const Params &P, long long ubeg, l
 
 // MMA2 issuer (lane 0 of warp 18): for every stage, once all consumer warps stored their
 // theta^T, D2 += Theta^T [X | 1]; releases the ring slot and the theta^T buffer by commits.
+// D2 restarts at the first stage of every chunk (CH stages of a segment) in buffer
+// chunk % ND2, once the consumers read that buffer's previous chunk.
 template <typename TS, int NP>
 __device__ __forceinline__ void tc_issue_mma2(const Params &P, long long ubeg, long long uend, unsigned char *smem,
                                               uint64_t *full, uint64_t *empty, TcBars &B, unsigned long long k0,
-                                              unsigned long long kend, unsigned long long seg0)
+                                              unsigned long long kend, unsigned long long ch0)
 {
     using Sh = TcShape<TS, NP>;
     constexpr int S = Sh::kStages;
@@ -639,23 +652,26 @@ __device__ __forceinline__ void tc_issue_mma2(const Params &P, long long ubeg, l
     mc.begin(ubeg, uend, N);
     RingPos<S> mpos;
     mpos.init(k0);
-    unsigned long long seg = seg0;
+    unsigned long long ch = ch0;
     bool ok = true;
     for (unsigned long long k = k0; k < kend && ok; ++k) {
         const int slot = mpos.slot;
-        const bool first = mc.r == mc.r0;
-        const bool last = mc.r + Sh::RS >= mc.r1;
+        const long long i = (mc.r - mc.r0) / Sh::RS;   // stage of the segment
+        const bool cfirst = (i % Sh::CH) == 0;
+        const bool clast = (i % Sh::CH) == Sh::CH - 1 || mc.r + Sh::RS >= mc.r1;
         const int b = (int)(k % Sh::NA2);
+        const int db = (int)(ch % Sh::ND2);
         ok = mbar_wait(P, &full[slot], mpos.phase) && mbar_wait(P, &B.a2full[b], (uint32_t)((k / Sh::NA2) & 1));
-        if (ok && first && seg >= 1) ok = mbar_wait(P, &B.d2free, (uint32_t)((seg - 1) & 1));
+        if (ok && cfirst && ch >= (unsigned long long)Sh::ND2)
+            ok = mbar_wait(P, &B.d2free[db], (uint32_t)((ch / Sh::ND2 - 1) & 1));
         if (ok) {
             tc_fence_after();
-            tc_mma2<TS, NP>(tb, D, slot, b, first);
+            tc_mma2<TS, NP>(tb, D, slot, b, cfirst, db);
             umma_commit(&empty[slot]);
             umma_commit(&B.a2free[b]);
-            if (last) umma_commit(&B.d2done);
+            if (clast) umma_commit(&B.d2done[db]);
         }
-        if (last) ++seg;
+        if (clast) ++ch;
         mc.advance(N);
         mpos.next();
     }
@@ -671,7 +687,7 @@ __device__ __forceinline__ void tc_issue_mma2(const Params &P, long long ubeg, l
 template <typename TS, int NP>
 __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *smem, uint64_t *full, uint64_t *empty,
                               TcBars &B, unsigned long long &kstage, unsigned long long &kseg, unsigned long long &kgrp,
-                              long long vc)
+                              unsigned long long &kch, long long vc)
 {
     using Sh = TcShape<TS, NP>;
     constexpr int S = Sh::kStages, N2 = Sh::N2;
@@ -686,10 +702,12 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
     const uint32_t tb = B.tmem;
     const uint32_t tq = tb + ((uint32_t)(32 * q) << 16);   // this warp's lane quarter
 
-    unsigned long long nst = 0, nseg = 0, ngrp = 0;
+    unsigned long long nst = 0, nseg = 0, ngrp = 0, nch = 0;
     for (long long u = ubeg; u < uend;) {
         const long long s = u / N, r0 = u - s * N, r1 = min(N, r0 + (uend - u));
-        nst += (unsigned long long)((r1 - r0 + Sh::RS - 1) / Sh::RS);
+        const long long sst = (r1 - r0 + Sh::RS - 1) / Sh::RS;
+        nst += (unsigned long long)sst;
+        nch += (unsigned long long)((sst + Sh::CH - 1) / Sh::CH);
         ngrp += (unsigned long long)((r1 - r0 + Sh::GR - 1) / Sh::GR);
         ++nseg;
         u += r1 - r0;
@@ -702,7 +720,7 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
             else if (warp == kTcWarps + 1)
                 tc_issue_mma1<TS, NP>(P, ubeg, uend, smem, B, kgrp, kseg);
             else
-                tc_issue_mma2<TS, NP>(P, ubeg, uend, smem, full, empty, B, k0, kend, kseg);
+                tc_issue_mma2<TS, NP>(P, ubeg, uend, smem, full, empty, B, k0, kend, kch);
         }
         __syncwarp();
     } else {
@@ -718,8 +736,34 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
         const int rb = RPW * wg;   // first stage row of this warp
         RingPos<S> cpos;
         cpos.init(k0);
-        unsigned long long k = k0, seg = kseg, gj = kgrp;
+        unsigned long long k = k0, seg = kseg, gj = kgrp, ch = kch;
         bool ok = true;
+        // this warpgroup's share of D2: columns [h0, h0 + H2) of the even (eo = 0) or odd block
+        constexpr int H2 = Sh::H2;
+        const int eo = wg >> 1, h0 = (wg & 1) * H2;
+        float d2acc[H2];
+        bool pending = false;          // a D2 chunk whose MMAs were issued and that is not added yet
+        unsigned long long pch = 0;
+        // adds D2 chunk cc to d2acc (round to nearest) and hands its buffer back to the MMA2 issuer
+        auto flush_d2 = [&](unsigned long long cc) {
+            const int db = (int)(cc % Sh::ND2);
+            if (ok) ok = mbar_wait(P, &B.d2done[db], (uint32_t)((cc / Sh::ND2) & 1));
+            ok = __all_sync(0xffffffffu, ok);
+            if (ok) {
+                tc_fence_after();
+#pragma unroll
+                for (int j = 0; j < H2; j += 8) {
+                    float v[8];
+                    tmem_ld8(tq + Sh::COL_D2 + 2 * N2 * db + N2 * eo + h0 + j, v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) d2acc[j + t] += v[t];
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&B.d2free[db]);
+        };
         for (long long u = ubeg; u < uend;) {
             const long long s = u / N, r0 = u - s * N, r1 = min(N, r0 + (uend - u));
             const long long col0 = s * kW + 2 * m;
@@ -728,6 +772,8 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
             const uint32_t hcol = hash_col((uint32_t)(col0 >> 1), rseed);
             const bool ragged = (s * kW + kW) > N;
             float *rp = P.rowpart + (s * 4 + q);
+#pragma unroll
+            for (int j = 0; j < H2; ++j) d2acc[j] = 0.0f;
             for (long long r = r0; r < r1; r += RS, ++k, cpos.next()) {
                 const int slot = cpos.slot;
                 const int b = (int)(k % Sh::NA2);   // theta^T buffer of this stage
@@ -802,34 +848,33 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
                     mbar_arrive(&empty[slot]);
                 }
                 tc_flush_rows(rs, r + rb, ok ? r1 : r, rp, P.Q, lane);
-            }
-            // --- segment end: column partials from D2 (warpgroup 0) ---
-            if (ok) ok = mbar_wait(P, &B.d2done, (uint32_t)(seg & 1));
-            ok = __all_sync(0xffffffffu, ok);
-            if (wg == 0) {
-                float d2e[N2], d2o[N2];
-                if (ok) {
-                    tc_fence_after();
-#pragma unroll
-                    for (int j = 0; j < N2; j += 16) {
-                        tmem_ld16(tq + Sh::COL_D2 + j, d2e + j);
-                        tmem_ld16(tq + Sh::COL_D2 + N2 + j, d2o + j);
-                    }
-                    tmem_wait_ld();
-                    const int slotc = (int)(s - first_stripe);
-                    float *cp = P.colpart + ((vc * P.slots + slotc) * P.cgroups * (NP + 1)) * kW + 2 * m;
-                    const int n = P.n;
-                    cp[0] = d2e[n];
-                    cp[1] = d2o[n];
-#pragma unroll
-                    for (int kk = 0; kk < NP; ++kk) {
-                        cp[(1 + kk) * kW] = kk < n ? d2e[kk] : 0.0f;
-                        cp[(1 + kk) * kW + 1] = kk < n ? d2o[kk] : 0.0f;
-                    }
+                // the previous D2 chunk (its MMAs had a stage to finish), then mark this one
+                if (pending) {
+                    flush_d2(pch);
+                    pending = false;
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&B.d2free);
+                const long long si = (r - r0) / RS;
+                if ((si % Sh::CH) == Sh::CH - 1 || r + RS >= r1) {
+                    pch = ch++;
+                    pending = true;
+                }
+            }
+            // --- segment end: the last chunk, then this warpgroup's share of the column partials
+            // (D2 column j < n: (Theta^T X)_j, j = n: the column sums; n < j <= NP written as 0) ---
+            if (pending) {
+                flush_d2(pch);
+                pending = false;
+            }
+            if (ok) {
+                const int slotc = (int)(s - first_stripe);
+                float *cp = P.colpart + ((vc * P.slots + slotc) * P.cgroups * (NP + 1)) * kW + 2 * m + eo;
+                const int n = P.n;
+#pragma unroll
+                for (int j = 0; j < H2; ++j) {
+                    const int kk = h0 + j;
+                    if (kk == n) cp[0] = d2acc[j];
+                    else if (kk < NP) cp[(1 + kk) * kW] = kk < n ? d2acc[j] : 0.0f;
+                }
             }
             u += r1 - r0;
             ++seg;
@@ -838,6 +883,7 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
     kstage = kend;
     kseg += nseg;
     kgrp += ngrp;
+    kch += nch;
     __syncthreads();
 }
 

@@ -145,11 +145,12 @@ KernelSet kernels_for(int dtype, int NP)
     case CR_THETA_F32: return crk::kernels_f32(NP);
     case CR_THETA_BF16: return crk::kernels_bf16(NP);
     case CR_THETA_F16: return crk::kernels_f16(NP);
+    case CR_THETA_F64: return crk::kernels_f64(NP);
     default: return KernelSet{nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, {nullptr, nullptr, nullptr, nullptr}};
     }
 }
 
-size_t theta_elem_size(int dtype) { return dtype == CR_THETA_F32 ? 4 : 2; }
+size_t theta_elem_size(int dtype) { return dtype == CR_THETA_F64 ? 8 : dtype == CR_THETA_F32 ? 4 : 2; }
 
 int rec_floats(int NP) { return ((NP + 1 + 3) / 4) * 4; }
 
@@ -487,6 +488,12 @@ cr_status init_state(cr_ctx *h)
     }
     CR_CUDA(h, cudaMemsetAsync(P.rowpart, 0, sizeof(float) * (size_t)P.Q * h->N, h->stream));
     CR_CUDA(h, cudaMemsetAsync(P.colpart, 0, sizeof(float) * (size_t)P.G * P.slots * P.cgroups * (h->NP + 1) * crk::kW, h->stream));
+    if (P.f64) {
+        CR_CUDA(h, cudaMemsetAsync(P.rowpart64, 0, sizeof(double) * (size_t)P.Q * h->N, h->stream));
+        CR_CUDA(h, cudaMemsetAsync(P.colpart64, 0,
+                                   sizeof(double) * (size_t)P.G * P.slots * crk::kWR * (h->NP + 1) * crk::kW,
+                                   h->stream));
+    }
     DevState st;
     std::memset(&st, 0, sizeof st);
     st.scal[0].t = 1.0;   // t_1 = 1 (Iteration 0 of Fig. 2)
@@ -594,7 +601,12 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     else cr_options_default(&h->opt);
     cr_options &o = h->opt;
     if (!(o.gamma > 0.0) || !std::isfinite(o.gamma)) return fail(h, CR_EINVAL, "gamma must be > 0");
-    if (o.theta_dtype < 0 || o.theta_dtype > 2) return fail(h, CR_EINVAL, "unknown theta_dtype %d", o.theta_dtype);
+    if (o.theta_dtype < 0 || o.theta_dtype > 3) return fail(h, CR_EINVAL, "unknown theta_dtype %d", o.theta_dtype);
+    const bool f64 = o.theta_dtype == CR_THETA_F64;
+    if (f64 && n > crk::kMaxNF64)
+        return fail(h, CR_EINVAL, "FP64 multipliers are compiled for n <= %d (n = %d)", crk::kMaxNF64, n);
+    if (f64 && (o.pair_engine == CR_PAIR_TENSOR_CORES || o.record_every > 0 || np_override > 0))
+        return fail(h, CR_EINVAL, "FP64 multipliers: CUDA-core pass only, no record_every, not in a batch");
     if (o.kkt_every < 1) return fail(h, CR_EINVAL, "kkt_every must be >= 1");
     h->N = N;
     h->n = n;
@@ -631,7 +643,8 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     }
     CR_CUDA(h, cudaFuncSetAttribute(h->ks.persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem));
     CR_CUDA(h, cudaFuncSetAttribute(h->ks.phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem));
-    CR_CUDA(h, cudaFuncSetAttribute(h->ks.pair_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem));
+    if (h->ks.pair_tc)
+        CR_CUDA(h, cudaFuncSetAttribute(h->ks.pair_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ks.smem));
     if (h->alcc)
         CR_CUDA(h, cudaFuncSetAttribute(h->ak.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ak.smem));
     int per_sm = 0;
@@ -645,7 +658,9 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     long long S = (N + crk::kW - 1) / crk::kW;
     long long total = S * N;
     int G = o.grid > 0 ? o.grid : std::max(1, max_coresident);
-    const long long min_units = 40;   // keep at least 40 (stripe,row) units per CTA (N = 500: 25 CTAs, measured best)
+    // keep at least 40 (stripe,row) units per CTA (N = 500: 25 CTAs, measured best); the FP64 pass
+    // is bound by GB300's narrow FP64 pipe and spreads over more SMs
+    const long long min_units = f64 ? 4 : 40;
     if (o.grid <= 0) G = (int)std::max<long long>(1, std::min<long long>(G, total / min_units));
     h->persistent_ok = coop && per_sm > 0 && G <= max_coresident;
     if (np_override > 0) h->persistent_ok = false;   // batch member: driven by the batch kernel only
@@ -688,7 +703,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     const int tc_from = o.theta_dtype == CR_THETA_F32 ? 16 : 8;
     P.tc = (o.pair_engine == CR_PAIR_TENSOR_CORES ||
             (o.pair_engine == CR_PAIR_AUTO && h->NP >= tc_from && o.record_every <= 0 && !batch_member &&
-             o.driver != CR_DRIVER_PERSISTENT))
+             o.driver != CR_DRIVER_PERSISTENT && !f64))
                ? 1
                : 0;
     if (P.tc) h->persistent_ok = false;   // the tensor-core pass runs in its own launch (phase driver)
@@ -744,7 +759,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     const CUtensorMapDataType tdt = o.theta_dtype == CR_THETA_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                     : o.theta_dtype == CR_THETA_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < 2 && !f64; ++b) {   // the FP64 pass reads its tiles without TMA
         cuuint64_t gdim[2] = {(cuuint64_t)N, (cuuint64_t)N};
         cuuint64_t gstride[1] = {(cuuint64_t)h->ld * es};
         cuuint32_t box[2] = {(cuuint32_t)crk::kW, (cuuint32_t)crk::kRS};
@@ -789,6 +804,14 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     CR_TRY(dev_alloc(h, &P.foldpart, (size_t)G * 8));
     CR_TRY(dev_alloc(h, &P.kktpart, (size_t)G * 8));
     CR_TRY(dev_alloc(h, &P.st, 1));
+    P.f64 = f64 ? 1 : 0;
+    if (f64) {
+        CR_TRY(dev_alloc(h, &P.rec64, (size_t)N * REC));
+        CR_TRY(dev_alloc(h, &P.ccol2_64, (size_t)N));
+        CR_TRY(dev_alloc(h, &P.xi2_64, (size_t)N * h->NP));
+        CR_TRY(dev_alloc(h, &P.rowpart64, (size_t)P.Q * N));
+        CR_TRY(dev_alloc(h, &P.colpart64, (size_t)G * P.slots * crk::kWR * (h->NP + 1) * crk::kW));
+    }
     if (h->alcc) {
         for (int b = 0; b < 2; ++b) {
             CR_TRY(dev_alloc(h, &P.ay[b], N));
@@ -819,6 +842,16 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     CR_CUDA(h, cudaMemcpyAsync(X64, X.data(), sizeof(double) * N * n, cudaMemcpyHostToDevice, h->stream));
     CR_CUDA(h, cudaMemcpyAsync(P.rowrec, rec.data(), sizeof(float) * rec.size(), cudaMemcpyHostToDevice, h->stream));
     CR_CUDA(h, cudaMemcpyAsync(hh, hv.data(), sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+    std::vector<double> rec64;
+    if (f64) {
+        // FP64 row records {y - s (set by every fold), x_1..x_n, 0 ...}
+        rec64.assign((size_t)N * REC, 0.0);
+        for (long long l = 0; l < N; ++l)
+            for (int k = 0; k < n; ++k) rec64[(size_t)l * REC + 1 + k] = X[(size_t)l * n + k];
+        CR_CUDA(h, cudaMemcpyAsync(P.rec64, rec64.data(), sizeof(double) * rec64.size(), cudaMemcpyHostToDevice,
+                                   h->stream));
+        CR_CUDA(h, cudaMemsetAsync(P.xi2_64, 0, sizeof(double) * (size_t)N * h->NP, h->stream));
+    }
     if (P.tc) CR_TRY(setup_tc_operands(h, X));
     if (h->alcc) {
         // column data of (y_0, xi_0) = (ybar, 0): row records y = ybar, xi^T x - y = -ybar

@@ -31,12 +31,12 @@ def test_backward_matches_oracle_directional_derivatives(N, n, K, k):
     rng = np.random.default_rng(1)
     ubar = rng.normal(size=N)
     s, gyb, gX = _vjp(crg, X, yb, K, k, ubar)
-    info = s.info()
+    L, sh = O.lipschitz(X, 0.1), O.shift(yb)   # the oracle's own constants
     errs = []
     for _ in range(6):
         dy = rng.normal(size=N)
         dX = rng.normal(size=X.shape)
-        _, jv = O.papg_jvp(X, yb, 0.1, info["L"], info["shift"], K, dy, dX)
+        _, jv = O.papg_jvp(X, yb, 0.1, L, sh, K, dy, dX)
         want = float(ubar @ jv)
         got = float(gyb @ dy + (gX * dX).sum())
         errs.append(abs(got - want) / max(abs(want), 1e-12))
@@ -73,13 +73,12 @@ def test_autograd_function_gradient_matches_oracle():
     # the solver works on the FP32-rounded inputs; compare with the oracle on the same data
     Xr = Xt.detach().double().cpu().numpy()
     yr = yt.detach().double().cpu().numpy()
-    s = crg.Solver(Xr, yr, gamma=0.1)
-    info = s.info()
+    L, sh = O.lipschitz(Xr, 0.1), O.shift(yr)
     rng = np.random.default_rng(11)
     for _ in range(4):
         dy = rng.normal(size=yb.shape)
         dX = rng.normal(size=X.shape)
-        yo, jv = O.papg_jvp(Xr, yr, 0.1, info["L"], info["shift"], K, dy, dX)
+        yo, jv = O.papg_jvp(Xr, yr, 0.1, L, sh, K, dy, dX)
         want = float(2.0 * (yo - f0) @ jv)
         got = float((yt.grad.double().cpu().numpy() * dy).sum() + (Xt.grad.double().cpu().numpy() * dX).sum())
         assert abs(got - want) <= 2e-3 * abs(want) + 1e-6, (got, want)

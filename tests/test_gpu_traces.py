@@ -28,7 +28,7 @@ def crg():
 def _traces(crg, momentum):
     X, yb, _ = datagen.make("xqx")
     g = crg.Solver(X, yb, gamma=0.1, momentum=momentum, stochastic_round=0, restart=0)
-    o = O.Solver(X, yb, gamma=0.1, L=g.info()["L"], s=g.info()["shift"], momentum=bool(momentum), restart=False)
+    o = O.Solver(X, yb, gamma=0.1, momentum=bool(momentum), restart=False)
     out, done = [], 0
     for k in CHECKS:
         g.iterate(k - done)
