@@ -105,6 +105,12 @@ typedef struct {
     int32_t reserved[3];
     double restart_tol;       /* restart only when the dual value fell by more than restart_tol * |previous|
                                  (guards the test against rounding noise); default 1e-7 */
+    double B_theta;           /* radius of the ball in Q_2 = {lambda >= 0, ||lambda||_2 <= B_theta} of Eq.
+                                 (lambda_dual), lambda = (theta, mu) all dual variables; <= 0 (default) or
+                                 infinite: no ball.  Finite: Step 2 projects on Q_2 exactly, the clamp at 0
+                                 followed by the radial factor min(1, B_theta / ||clamped lambda||_2), which
+                                 costs a norm pass and, when the ball binds, a scaling pass over the array.
+                                 FP32 or FP64 multipliers, CUDA-core pass, phase driver, no record_every */
 } cr_options;
 
 /* Fills *opt with the defaults documented above. */
@@ -333,6 +339,13 @@ cr_status cr_batch_reset(cr_batch_handle b);
 cr_status cr_batch_instance(cr_batch_handle b, int32_t i, cr_handle *h);
 /* Granularity factor picked by the autotuner, physical CTAs, iterations run. */
 cr_status cr_batch_info(cr_batch_handle b, int32_t *factor, int32_t *grid, int64_t *iters);
+/* How the batch launches ran: *graph_live = 1 when the launch is held as an instantiated CUDA
+ * graph (0 when capture of the cooperative launch was refused and the batch launches directly);
+ * graph_launches / direct_launches count the launches of each kind so far; *tuned = candidates
+ * the autotuner timed, tune_ms (nullable, room for 8) their milliseconds per iteration in the
+ * order of the factors 1, 2, 4, 8, 16.  Any pointer may be NULL. */
+cr_status cr_batch_stats(cr_batch_handle b, int32_t *graph_live, int64_t *graph_launches, int64_t *direct_launches,
+                         int32_t *tuned, double *tune_ms);
 void cr_batch_destroy(cr_batch_handle b);
 const char *cr_batch_last_error(cr_batch_handle b);
 

@@ -325,6 +325,8 @@ typedef struct {
     int32_t check_every; /* evaluate the KKT metric every this many iterations (0 = never) */
     int32_t pad;
     double restart_tol;  /* restart only if the dual value fell by more than restart_tol * |previous| */
+    double B_theta;      /* radius of the ball in Q_2 = {lambda >= 0, ||lambda||_2 <= B_theta} (Eq. (lambda_dual));
+                            <= 0 or infinite: no ball (Q_2 = {lambda >= 0}) */
 } orc_opts;
 
 /* Runs up to max_iter iterations of P-APG from the given state.  After each
@@ -361,6 +363,25 @@ ORC_API int64_t orc_papg(const double *X, const double *h, int64_t N, int32_t n,
         for (int64_t l = 0; l < N; ++l) {
             double v = mu2[l] - yy[l] * invL;
             mun[l] = v > 0.0 ? v : 0.0;
+        }
+        /* Q_2 with a finite ball: the projection onto {lambda >= 0} intersected with the ball
+         * ||lambda||_2 <= B_theta centred at 0 is the projection onto the orthant (the clamp
+         * above) followed by the radial scaling min(1, B_theta / ||lambda||_2), over all dual
+         * variables lambda = (theta, mu) */
+        if (o->B_theta > 0.0 && isfinite(o->B_theta)) {
+            double ss = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : ss) if (N >= ORC_PAR_MIN)
+            for (int64_t l1 = 0; l1 < N; ++l1)
+                for (int64_t l2 = 0; l2 < N; ++l2) ss += T2[l1 * N + l2] * T2[l1 * N + l2];
+            for (int64_t l = 0; l < N; ++l) ss += mun[l] * mun[l];
+            const double nrm = sqrt(ss);
+            if (nrm > o->B_theta) {
+                const double c = o->B_theta / nrm;
+#pragma omp parallel for schedule(static) if (N >= ORC_PAR_MIN)
+                for (int64_t l1 = 0; l1 < N; ++l1)
+                    for (int64_t l2 = 0; l2 < N; ++l2) T2[l1 * N + l2] *= c;
+                for (int64_t l = 0; l < N; ++l) mun[l] *= c;
+            }
         }
 
         double ell = scal[1] + 1.0;
@@ -535,6 +556,160 @@ ORC_API void orc_papg_jvp(const double *X, const double *ybar, int64_t N, int32_
     }
     free(P); free(T2); free(dP); free(dT2); free(muP); free(mu2); free(dmuP); free(dmu2);
     free(h); free(y); free(dy); free(xi); free(dxi); free(nw); free(dnw); free(mun); free(dmun);
+}
+
+/* The same forward-mode derivative for ORC_JD = 8 directions at once (direction index innermost
+ * in every tangent array, a fixed count so that the loops over directions vectorize), for sizes
+ * where separate runs of orc_papg_jvp would be slow.  Each
+ * step and each tangent formula is the one of orc_papg_jvp, evaluated in the same order per
+ * (point, direction); only the loops run row-major (column sums walk the rows m in increasing
+ * order, as in orc_eta).  dybar: N x 8, dX: N x n x 8 (row-major, directions innermost);
+ * dyhat: N x 8. */
+#define ORC_JD 8
+ORC_API void orc_papg_jvp_multi(const double *X, const double *ybar, int64_t N, int32_t n, double gamma,
+                                double L, double s, int64_t K, const double *dybar, const double *dX,
+                                double *yhat, double *dyhat)
+{
+    const size_t NN = (size_t)N * (size_t)N;
+    double *P = (double *)calloc(NN, sizeof(double)), *T2 = (double *)calloc(NN, sizeof(double));
+    double *dP = (double *)calloc(NN * ORC_JD, sizeof(double)), *dT2 = (double *)calloc(NN * ORC_JD, sizeof(double));
+    double *muP = (double *)calloc(N, sizeof(double)), *mu2 = (double *)calloc(N, sizeof(double));
+    double *dmuP = (double *)calloc((size_t)N * ORC_JD, sizeof(double)), *dmu2 = (double *)calloc((size_t)N * ORC_JD, sizeof(double));
+    double *h = (double *)malloc(sizeof(double) * N), *y = (double *)malloc(sizeof(double) * N);
+    double *dy = (double *)malloc(sizeof(double) * N * ORC_JD), *xi = (double *)malloc(sizeof(double) * N * n);
+    double *dxi = (double *)malloc(sizeof(double) * N * n * ORC_JD);
+    double *rs = (double *)malloc(sizeof(double) * N), *drs = (double *)malloc(sizeof(double) * N * ORC_JD);
+    const double invL = 1.0 / L;
+    for (int64_t l = 0; l < N; ++l) h[l] = ybar[l] + s;
+    double t = 1.0;
+    for (int64_t it = 0; it < K; ++it) {
+        /* Step 1: row sums of T2 and of its tangents */
+#pragma omp parallel for schedule(static) if (N >= ORC_PAR_MIN)
+        for (int64_t l = 0; l < N; ++l) {
+            double r = 0.0;
+            double *dr = drs + (size_t)l * ORC_JD;
+            for (int d = 0; d < ORC_JD; ++d) dr[d] = 0.0;
+            for (int64_t m = 0; m < N; ++m) {
+                if (m == l) continue;
+                r += T2[l * N + m];
+                const double *dt = dT2 + ((size_t)l * N + m) * ORC_JD;
+                for (int d = 0; d < ORC_JD; ++d) dr[d] += dt[d];
+            }
+            rs[l] = r;
+        }
+        /* column sums, A_2^T T2 and their tangents: each thread owns a range of columns l and
+         * walks the rows m in increasing order */
+#pragma omp parallel if (N >= ORC_PAR_MIN)
+        {
+            int nt = 1, tid = 0;
+#ifdef _OPENMP
+            nt = omp_get_num_threads();
+            tid = omp_get_thread_num();
+#endif
+            int64_t l0 = N * tid / nt, l1 = N * (tid + 1) / nt;
+            int64_t w = l1 - l0 > 0 ? l1 - l0 : 1;
+            double *c = (double *)calloc((size_t)w, sizeof(double));
+            double *dc = (double *)calloc((size_t)w * ORC_JD, sizeof(double));
+            double *ax = (double *)calloc((size_t)w * n, sizeof(double));
+            double *dax = (double *)calloc((size_t)w * n * ORC_JD, sizeof(double));
+            for (int64_t m = 0; m < N; ++m) {
+                const double *xm = X + m * n, *dxm = dX + (size_t)m * n * ORC_JD;
+                for (int64_t l = l0; l < l1; ++l) {
+                    if (l == m) continue;
+                    const double tm = T2[m * N + l];
+                    const double *dtm = dT2 + ((size_t)m * N + l) * ORC_JD;
+                    const double *xl = X + l * n, *dxl = dX + (size_t)l * n * ORC_JD;
+                    c[l - l0] += tm;
+                    double *dcl = dc + (size_t)(l - l0) * ORC_JD;
+                    for (int d = 0; d < ORC_JD; ++d) dcl[d] += dtm[d];
+                    for (int k = 0; k < n; ++k) {
+                        const double dxk = xl[k] - xm[k];
+                        ax[(l - l0) * n + k] += tm * dxk;
+                        double *da = dax + ((size_t)(l - l0) * n + k) * ORC_JD;
+                        const double *dxlk = dxl + (size_t)k * ORC_JD, *dxmk = dxm + (size_t)k * ORC_JD;
+                        for (int d = 0; d < ORC_JD; ++d) da[d] += dtm[d] * dxk + tm * (dxlk[d] - dxmk[d]);
+                    }
+                }
+            }
+            for (int64_t l = l0; l < l1; ++l) {
+                y[l] = h[l] + (rs[l] - c[l - l0]) + mu2[l];
+                for (int d = 0; d < ORC_JD; ++d)
+                    dy[(size_t)l * ORC_JD + d] = dybar[(size_t)l * ORC_JD + d] + (drs[(size_t)l * ORC_JD + d] - dc[(size_t)(l - l0) * ORC_JD + d]) +
+                                            dmu2[(size_t)l * ORC_JD + d];
+                for (int k = 0; k < n; ++k) {
+                    xi[l * n + k] = ax[(l - l0) * n + k] / gamma;
+                    for (int d = 0; d < ORC_JD; ++d)
+                        dxi[((size_t)l * n + k) * ORC_JD + d] = dax[((size_t)(l - l0) * n + k) * ORC_JD + d] / gamma;
+                }
+            }
+            free(c);
+            free(dc);
+            free(ax);
+            free(dax);
+        }
+        /* Steps 3-4 scalars (the weight is known before Step 2) */
+        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        const double beta = (t - 1.0) / tn;
+        t = tn;
+        /* Step 2 and its tangent, then Step 4 element by element:
+         *   new = max(0, T2 - g/L), dnew = [v > 0] (dT2 - dg/L), T2 <- new + beta (new - P), P <- new */
+#pragma omp parallel for schedule(static) if (N >= ORC_PAR_MIN)
+        for (int64_t l1 = 0; l1 < N; ++l1) {
+            const double *dyl1 = dy + (size_t)l1 * ORC_JD, *dxl1 = dX + (size_t)l1 * n * ORC_JD;
+            for (int64_t l2 = 0; l2 < N; ++l2) {
+                const size_t q = (size_t)l1 * N + l2;
+                double *dt2 = dT2 + q * ORC_JD, *dp = dP + q * ORC_JD;
+                if (l1 == l2) continue;   /* diagonal: stays 0 with zero tangents */
+                const double *dyl2 = dy + (size_t)l2 * ORC_JD, *dxl2 = dX + (size_t)l2 * n * ORC_JD;
+                double g = y[l1] - y[l2];
+                for (int k = 0; k < n; ++k) g -= xi[l2 * n + k] * (X[l1 * n + k] - X[l2 * n + k]);
+                const double v = T2[q] - g * invL;
+                const double nw = v > 0.0 ? v : 0.0;
+                for (int d = 0; d < ORC_JD; ++d) {
+                    double dg = dyl1[d] - dyl2[d];
+                    for (int k = 0; k < n; ++k) {
+                        const double dx = X[l1 * n + k] - X[l2 * n + k];
+                        dg -= dxi[((size_t)l2 * n + k) * ORC_JD + d] * dx +
+                              xi[l2 * n + k] * (dxl1[(size_t)k * ORC_JD + d] - dxl2[(size_t)k * ORC_JD + d]);
+                    }
+                    const double dnw = v > 0.0 ? dt2[d] - dg * invL : 0.0;
+                    dt2[d] = dnw + beta * (dnw - dp[d]);
+                    dp[d] = dnw;
+                }
+                T2[q] = nw + beta * (nw - P[q]);
+                P[q] = nw;
+            }
+        }
+        for (int64_t l = 0; l < N; ++l) {
+            const double v = mu2[l] - y[l] * invL;
+            const double nm = v > 0.0 ? v : 0.0;
+            for (int d = 0; d < ORC_JD; ++d) {
+                const size_t i = (size_t)l * ORC_JD + d;
+                const double dnm = v > 0.0 ? dmu2[i] - dy[i] * invL : 0.0;
+                dmu2[i] = dnm + beta * (dnm - dmuP[i]);
+                dmuP[i] = dnm;
+            }
+            mu2[l] = nm + beta * (nm - muP[l]);
+            muP[l] = nm;
+        }
+    }
+    /* fitted values at theta^(1)_K = P: yhat = ybar + A_1^T P + muP, and their tangents */
+#pragma omp parallel for schedule(static) if (N >= ORC_PAR_MIN)
+    for (int64_t l = 0; l < N; ++l) {
+        double r = 0.0;
+        double *dr = dyhat + (size_t)l * ORC_JD;
+        for (int d = 0; d < ORC_JD; ++d) dr[d] = 0.0;
+        for (int64_t m = 0; m < N; ++m) {
+            if (m == l) continue;
+            r += P[l * N + m] - P[m * N + l];
+            const double *a = dP + ((size_t)l * N + m) * ORC_JD, *b = dP + ((size_t)m * N + l) * ORC_JD;
+            for (int d = 0; d < ORC_JD; ++d) dr[d] += a[d] - b[d];
+        }
+        yhat[l] = ybar[l] + r + muP[l];
+        for (int d = 0; d < ORC_JD; ++d) dr[d] = dybar[(size_t)l * ORC_JD + d] + dr[d] + dmuP[(size_t)l * ORC_JD + d];
+    }
+    free(P); free(T2); free(dP); free(dT2); free(muP); free(mu2); free(dmuP); free(dmu2);
+    free(h); free(y); free(dy); free(xi); free(dxi); free(rs); free(drs);
 }
 
 ORC_API int orc_num_threads(void)

@@ -25,7 +25,7 @@ _lib = None
 
 __all__ = [
     "build_oracle", "shift", "lipschitz", "eta", "residual", "metrics", "Solver",
-    "METRIC_NAMES", "num_threads", "papg_jvp",
+    "METRIC_NAMES", "num_threads", "papg_jvp", "papg_jvp_multi",
 ]
 
 METRIC_NAMES = ("kkt", "pri", "comp", "infeas", "gap", "primal", "dual", "fit", "sum_check")
@@ -34,7 +34,7 @@ METRIC_NAMES = ("kkt", "pri", "comp", "infeas", "gap", "primal", "dual", "fit", 
 def build_oracle(force: bool = False) -> str:
     """Compile cr_oracle.c with gcc (OpenMP, FP64, no FMA contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+        cmd = ["gcc", "-O3", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
                "-o", _LIB + ".tmp", _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(_LIB + ".tmp", _LIB)
@@ -44,7 +44,8 @@ def build_oracle(force: bool = False) -> str:
 class _Opts(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("L", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("tol", ctypes.c_double), ("momentum", ctypes.c_int32), ("restart", ctypes.c_int32),
-                ("check_every", ctypes.c_int32), ("pad", ctypes.c_int32), ("restart_tol", ctypes.c_double)]
+                ("check_every", ctypes.c_int32), ("pad", ctypes.c_int32), ("restart_tol", ctypes.c_double),
+                ("B_theta", ctypes.c_double)]
 
 
 def _load():
@@ -72,6 +73,8 @@ def _load():
             lib.orc_papg.restype = i64
             lib.orc_papg_jvp.argtypes = [dp, dp, i64, i32, d, d, d, i64, dp, dp, dp, dp]
             lib.orc_papg_jvp.restype = None
+            lib.orc_papg_jvp_multi.argtypes = [dp, dp, i64, i32, d, d, d, i64, dp, dp, dp, dp]
+            lib.orc_papg_jvp_multi.restype = None
             lib.orc_num_threads.argtypes = []
             lib.orc_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -143,6 +146,32 @@ def papg_jvp(X, ybar, gamma: float, L: float, s: float, K: int, dybar, dX):
     return yhat, dyhat
 
 
+def papg_jvp_multi(X, ybar, gamma: float, L: float, s: float, K: int, dybar, dX):
+    """papg_jvp for D directions: dybar (D, N), dX (D, N, n).  Returns (yhat (N,), dyhat (D, N)).
+    The C routine takes 8 directions per call (memory: 2 N^2 x 8 doubles); the last group is
+    padded with zero directions."""
+    X, ybar = _f64(X), _f64(ybar)
+    dybar = np.asarray(dybar, dtype=np.float64)
+    dX = np.asarray(dX, dtype=np.float64)
+    N, n = X.shape
+    D = dybar.shape[0]
+    assert dybar.shape == (D, N) and dX.shape == (D, N, n)
+    G = 8
+    out = np.empty((D, N))
+    yhat = np.empty(N)
+    for g0 in range(0, D, G):
+        g1 = min(D, g0 + G)
+        dyb = np.zeros((N, G))
+        dxx = np.zeros((N, n, G))
+        dyb[:, :g1 - g0] = dybar[g0:g1].T
+        dxx[:, :, :g1 - g0] = np.transpose(dX[g0:g1], (1, 2, 0))
+        dyh = np.empty((N, G))
+        _load().orc_papg_jvp_multi(_p(X), _p(ybar), N, n, float(gamma), float(L), float(s), int(K), _p(dyb), _p(dxx),
+                                   _p(yhat), _p(dyh))
+        out[g0:g1] = dyh[:, :g1 - g0].T
+    return yhat, out
+
+
 def data_scale(ybar) -> float:
     yb = np.asarray(ybar, dtype=np.float64)
     return max(1.0, float(yb.max() - yb.min()))
@@ -158,7 +187,7 @@ class Solver:
 
     def __init__(self, X, ybar, gamma: float = 1e-1, L: float | None = None, s: float | None = None,
                  momentum: bool = True, restart: bool = False, check_every: int = 0,
-                 theta0=None, mu0=None, restart_tol: float = 0.0):
+                 theta0=None, mu0=None, restart_tol: float = 0.0, B_theta: float = 0.0):
         self.X = _f64(X)
         self.ybar = _f64(ybar)
         self.N, self.n = self.X.shape
@@ -173,6 +202,7 @@ class Solver:
         self.restart = bool(restart)
         self.check_every = int(check_every)
         self.restart_tol = float(restart_tol)
+        self.B_theta = float(B_theta)   # > 0: Q_2 includes the ball ||lambda||_2 <= B_theta
         N = self.N
         self.P = np.zeros((N, N))
         self.T2 = np.zeros((N, N))
@@ -195,7 +225,7 @@ class Solver:
 
     def _opts(self, tol):
         return _Opts(self.gamma, self.L, self.sigma, float(tol), int(self.momentum), int(self.restart),
-                     int(self.check_every), 0, self.restart_tol)
+                     int(self.check_every), 0, self.restart_tol, self.B_theta)
 
     def iterate(self, k: int, tol: float = -1.0) -> int:
         o = self._opts(tol)

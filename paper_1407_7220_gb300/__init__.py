@@ -49,7 +49,7 @@ exported_symbols = (
     "cr_batch_create", "cr_batch_solve", "cr_batch_iterate", "cr_batch_reset", "cr_batch_instance",
     "cr_batch_info", "cr_batch_destroy", "cr_batch_last_error", "cr_backward", "cr_get_engine",
     "cr_alcc_options_default", "cr_alcc_create", "cr_alcc_iterate", "cr_alcc_solve", "cr_alcc_metrics",
-    "cr_alcc_info", "cr_problem_constants",
+    "cr_alcc_info", "cr_problem_constants", "cr_batch_stats",
 )
 PROFILE_PAIR, PROFILE_FOLD, PROFILE_KKT, PROFILE_PERSISTENT = 0, 1, 2, 3
 
@@ -64,7 +64,7 @@ class Options(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("barrier_timeout_ms", ctypes.c_int32),
         ("test_barrier_extra", ctypes.c_int32), ("profile", ctypes.c_int32), ("record_every", ctypes.c_int32),
         ("pair_engine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
-        ("restart_tol", ctypes.c_double),
+        ("restart_tol", ctypes.c_double), ("B_theta", ctypes.c_double),
     ]
 
 
@@ -129,6 +129,9 @@ def lib():
             L.cr_batch_reset.argtypes = [H]
             L.cr_batch_instance.argtypes = [H, ctypes.c_int32, ctypes.POINTER(H)]
             L.cr_batch_info.argtypes = [H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), i64p]
+            L.cr_batch_stats.argtypes = [H, ctypes.POINTER(ctypes.c_int32), i64p, i64p, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_double)]
+            L.cr_batch_stats.restype = ctypes.c_int
             L.cr_batch_destroy.argtypes = [H]
             L.cr_batch_destroy.restype = None
             L.cr_batch_last_error.argtypes = [H]
@@ -441,6 +444,16 @@ class BatchSolver:
         f, g, it = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
         self._check(lib().cr_batch_info(self._h, ctypes.byref(f), ctypes.byref(g), ctypes.byref(it)))
         return {"factor": f.value, "grid": g.value, "iters": it.value}
+
+    def stats(self) -> dict:
+        """cr_batch_stats: whether the CUDA graph is live, launches of each kind, autotuner timings."""
+        live, nt = ctypes.c_int32(), ctypes.c_int32()
+        gl, dl = ctypes.c_int64(), ctypes.c_int64()
+        ms = (ctypes.c_double * 8)()
+        self._check(lib().cr_batch_stats(self._h, ctypes.byref(live), ctypes.byref(gl), ctypes.byref(dl),
+                                         ctypes.byref(nt), ms))
+        return {"graph_live": bool(live.value), "graph_launches": gl.value, "direct_launches": dl.value,
+                "tune_ms": [ms[i] for i in range(nt.value)]}
 
     def close(self):
         if getattr(self, "_h", None):

@@ -60,6 +60,7 @@ struct Scal {
     double dual;       // g_gamma(theta^(1)) the restart test compares against
     double beta;       // momentum weight used to form theta^(2)_l
     long long restarts;
+    double ball_c;     // finite B_theta: radial factor min(1, B_theta / ||lambda||_2) of this iterate
 };
 
 struct DevState {
@@ -90,6 +91,8 @@ struct Params {
     int slots;          // column-partial slots per CTA
     long long total;    // S * N units
     const long long *ubeg;  // G + 1 entries: first unit of every CTA (host-computed partition)
+    const long long *cfs;   // G entries: first stripe of every CTA (-1: no units)
+    const long long *sc0, *sc1;   // S entries each: CTAs [sc0[s], sc1[s]) meet stripe s
     // constants
     double gamma, inv_gamma, L, invL_d, shift, sigma;
     float invL;
@@ -120,6 +123,11 @@ struct Params {
     // FP64 multipliers (theta_dtype F64): the pair pass runs in FP64 on FP64 copies of its
     // inputs and writes FP64 partials (same layouts as rowrec, ccol2, xi2, rowpart, colpart)
     int f64;
+    // Q_2 with a finite ball ||lambda||_2 <= B_theta (Eq. (lambda_dual)): per-CTA partial sums
+    // of squares of the clamped multipliers (pairs and y >= 0 rows)
+    int ball;
+    double B_theta;
+    double *ballpart;   // [G]
     double *rec64, *ccol2_64, *xi2_64;
     double *rowpart64, *colpart64;
     int tc;                 // 1: the pair pass runs its two products on the tensor cores
@@ -468,6 +476,19 @@ __device__ __forceinline__ void bulk_load_hint(void *dst, const void *src, uint3
                  "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
                  : "memory");
 }
+// Stores of the per-iteration partial sums (read by the next fold) with an L2 evict-last policy:
+// the pair pass streams the multiplier arrays (GBs) through L2 after the first partials are
+// written, and with the default policy the fold found most of them evicted to DRAM.
+__device__ __forceinline__ void st_keep(float *p, float v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_keep(ulonglong2 *p, ulonglong2 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v2.u64 [%0], {%1, %2}, %3;" ::"l"(p), "l"(v.x), "l"(v.y), "l"(pol)
+                 : "memory");
+}
+
 // generic-proxy writes (earlier phases) ordered before async-proxy (TMA) reads
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 __device__ __forceinline__ void named_barrier_sync(int id, int count)
@@ -895,7 +916,7 @@ __device__ __forceinline__ void pair_stage_rows(const TS *tcur, const TS *tprv, 
 // e = 4*bit4 + 2*bit3 + bit2 (of the lane id) in every lane.  Entry e is row
 // r_last - kRS*(kSB - 1 - e/kRPW) + rg + kWR*(e % kRPW); only the nb most recent stages are written.
 __device__ __forceinline__ void flush_row_sums(float (&v)[8], int nb, long long r_last, int rg, long long r1,
-                                               float *rp, int Q, int lane)
+                                               float *rp, int Q, int lane, uint64_t pol)
 {
     const unsigned full = 0xffffffffu;
 #pragma unroll
@@ -921,7 +942,7 @@ __device__ __forceinline__ void flush_row_sums(float (&v)[8], int nb, long long 
         const int e = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
         const int sp = e / kRPW;
         const long long row = r_last - (long long)kRS * (kSB - 1 - sp) + rg + kWR * (e % kRPW);
-        if (sp >= kSB - nb && row < r1) rp[row * Q] = v[0];
+        if (sp >= kSB - nb && row < r1) st_keep(rp + row * Q, v[0], pol);
     }
 }
 
@@ -995,7 +1016,7 @@ __device__ __forceinline__ bool produce_stage(const Params &P, unsigned char *st
 }
 
 // Step 2 with FP64 multipliers (cr_pair_f64.cuh).
-template <int NP> __device__ void phase_pair_f64(const Params &P, long long ell, long long vc);
+template <int NP> __device__ void phase_pair_f64(const Params &P, long long ell, unsigned char *smem, long long vc);
 
 // MODE = PM_PAPG: Step 2 of P-APG at iteration ell.  The ALCC modes read and write array 0 only;
 // a = mu_k / mu_{k+1} scales the stored values of PM_ALCC_UPDATE.
@@ -1009,7 +1030,7 @@ __device__ __forceinline__ void phase_pair(const Params &P, long long ell, unsig
 {
     if constexpr (std::is_same<TS, double>::value) {
         static_assert(MODE == PM_PAPG, "FP64 multipliers: P-APG only");
-        phase_pair_f64<NP>(P, ell, vc);
+        phase_pair_f64<NP>(P, ell, smem, vc);
     } else {
         phase_pair_stream<TS, NP, MODE>(P, ell, smem, full, empty, kstage, vc, a);
     }
@@ -1065,6 +1086,7 @@ __device__ void phase_pair_stream(const Params &P, long long ell, unsigned char 
     const float scl = P.st_scale, iscl = P.st_inv_scale;
     const f2 beta2 = f2_make(beta, beta), ninvL2 = f2_make(-invL, -invL), iscl2 = f2_make(iscl, iscl);
     const bool sr = MODE == PM_PAPG && P.sr != 0;
+    const uint64_t keep = l2_evict_last();   // policy of the partial-sum stores
     const uint32_t rseed = P.seed ^ (uint32_t)ell * 0x632BE5ABu;
     TS *__restrict__ nxt = (TS *)P.theta[p];   // theta^(1)_{l-2} on entry, theta^(1)_l on exit
     const long long first_stripe = ubeg / N;
@@ -1159,7 +1181,7 @@ __device__ void phase_pair_stream(const Params &P, long long ell, unsigned char 
             for (int i = 0; i < kRPW; ++i) rsb[8 - kRPW + i] = rsn[i];
             ++nb;
             if (nb == kSB || r + kRS >= r1) {
-                flush_row_sums(rsb, nb, r, rg, r1, rp, P.Q, lane);
+                flush_row_sums(rsb, nb, r, rg, r1, rp, P.Q, lane, keep);
 #pragma unroll
                 for (int q = 0; q < 8; ++q) rsb[q] = 0.0f;
                 nb = 0;
@@ -1168,9 +1190,10 @@ __device__ void phase_pair_stream(const Params &P, long long ell, unsigned char 
         // column partials of this segment, one block per row group (summed in FP64 by foldA)
         const int slotc = (int)(s - first_stripe);
         float *cp = P.colpart + (((vc * P.slots + slotc) * kWR + rg) * (NP + 1)) * kW + wc * 128 + lane * 4;
-        *reinterpret_cast<ulonglong2 *>(cp) = make_ulonglong2(csum[0], csum[1]);
+        st_keep(reinterpret_cast<ulonglong2 *>(cp), make_ulonglong2(csum[0], csum[1]), keep);
 #pragma unroll
-        for (int q = 0; q < NP; ++q) *reinterpret_cast<ulonglong2 *>(cp + (1 + q) * kW) = make_ulonglong2(acc[0][q], acc[1][q]);
+        for (int q = 0; q < NP; ++q)
+            st_keep(reinterpret_cast<ulonglong2 *>(cp + (1 + q) * kW), make_ulonglong2(acc[0][q], acc[1][q]), keep);
         u += r1 - r0;
     }
     kstage += nst;
@@ -1204,34 +1227,43 @@ __device__ __forceinline__ void gather_adjoint(const Params &P, long long l, dou
         gather_adjoint64<NP>(P, l, R, Cc, TX);
         return;
     }
-    const long long N = P.N;
     const int Q4 = P.Q >> 2;   // row partials per row, in float4 units
     // row sum: the Q (>= 2S, zero padded) contiguous partials of row l, independent 16-byte loads
+    // issued 16 at a time (the fold is bound by the round trips to L2), summed in four
+    // interleaved compensated chains (one per vector component) that are added at the end
     const float4 *rp4 = reinterpret_cast<const float4 *>(P.rowpart + l * P.Q);
-    float rh = 0.0f, rl = 0.0f;
-#pragma unroll 8
-    for (int q = 0; q < Q4; ++q) {
-        const float4 t = __ldcg(rp4 + q);
-        ff_add(rh, rl, t.x);
-        ff_add(rh, rl, t.y);
-        ff_add(rh, rl, t.z);
-        ff_add(rh, rl, t.w);
+    float rh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, rl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    int q = 0;
+    for (; q + 16 <= Q4; q += 16) {
+        float4 t[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) t[i] = __ldcg(rp4 + q + i);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            ff_add(rh[0], rl[0], t[i].x);
+            ff_add(rh[1], rl[1], t[i].y);
+            ff_add(rh[2], rl[2], t[i].z);
+            ff_add(rh[3], rl[3], t[i].w);
+        }
     }
-    R = ff_value(rh, rl);
+    for (; q < Q4; ++q) {
+        const float4 t = __ldcg(rp4 + q);
+        ff_add(rh[0], rl[0], t.x);
+        ff_add(rh[1], rl[1], t.y);
+        ff_add(rh[2], rl[2], t.z);
+        ff_add(rh[3], rl[3], t.w);
+    }
+    R = (ff_value(rh[0], rl[0]) + ff_value(rh[1], rl[1])) + (ff_value(rh[2], rl[2]) + ff_value(rh[3], rl[3]));
     const long long s = l / kW, cl = l - s * kW;
-    // CTAs whose unit range intersects stripe s, ascending
-    const long long ua = s * N, ub = s * N + N - 1;
-    long long c0 = (long long)(((unsigned long long)ua * (unsigned long long)P.G) / (unsigned long long)P.total);
-    while (c0 > 0 && unit_begin(P, c0) > ua) --c0;
-    while (c0 + 1 < P.G && unit_begin(P, c0 + 1) <= ua) ++c0;
+    // CTAs whose unit range meets stripe s, ascending (host table: no dependent search)
+    const long long c0 = __ldg(P.sc0 + s), c1 = __ldg(P.sc1 + s);
     float ch = 0.0f, clo = 0.0f, th[NP], tl[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) th[k] = tl[k] = 0.0f;
-    long long ubg = unit_begin(P, c0);
-    for (long long cta = c0; cta < P.G && ubg <= ub; ++cta) {
-        const long long unx = unit_begin(P, cta + 1);
-        if (unx > ubg) {
-            const long long fs = ubg / N;
+#pragma unroll 2
+    for (long long cta = c0; cta < c1; ++cta) {
+        const long long fs = __ldg(P.cfs + cta);
+        if (fs >= 0) {
             const float *cp0 = P.colpart + ((cta * P.slots + (s - fs)) * P.cgroups * (NP + 1)) * kW + cl;
             // all (group, component) loads of one segment are independent: issue them together
             auto add_groups = [&](auto G) {
@@ -1256,7 +1288,6 @@ __device__ __forceinline__ void gather_adjoint(const Params &P, long long l, dou
             else
                 add_groups(std::integral_constant<int, 1>());
         }
-        ubg = unx;
     }
     Cc = ff_value(ch, clo);
 #pragma unroll
@@ -1268,37 +1299,109 @@ template <int NP>
 __device__ __forceinline__ void gather_adjoint64(const Params &P, long long l, double &R, double &Cc,
                                                  double (&TX)[NP])
 {
-    const long long N = P.N;
     const double *rp = P.rowpart64 + l * P.Q;
     double r = 0.0;
     for (int q = 0; q < P.Q; ++q) r += __ldcg(rp + q);
     R = r;
     const long long s = l / kW, cl = l - s * kW;
-    const long long ua = s * N, ub = s * N + N - 1;
-    long long c0 = (long long)(((unsigned long long)ua * (unsigned long long)P.G) / (unsigned long long)P.total);
-    while (c0 > 0 && unit_begin(P, c0) > ua) --c0;
-    while (c0 + 1 < P.G && unit_begin(P, c0 + 1) <= ua) ++c0;
+    const long long c0 = __ldg(P.sc0 + s), c1 = __ldg(P.sc1 + s);
     double cc = 0.0, tx[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) tx[k] = 0.0;
-    long long ubg = unit_begin(P, c0);
-    for (long long cta = c0; cta < P.G && ubg <= ub; ++cta) {
-        const long long unx = unit_begin(P, cta + 1);
-        if (unx > ubg) {
-            const long long fs = ubg / N;
-            const double *cp0 = P.colpart64 + ((cta * P.slots + (s - fs)) * kWR * (NP + 1)) * kW + cl;
-            for (int g = 0; g < kWR; ++g) {
-                const double *cp = cp0 + g * (NP + 1) * kW;
-                cc += __ldcg(cp);
+    // one pre-reduced block per CTA segment (the FP64 pass adds its row groups in shared memory)
+    for (long long cta = c0; cta < c1; ++cta) {
+        const long long fs = __ldg(P.cfs + cta);
+        if (fs >= 0) {
+            const double *cp = P.colpart64 + ((cta * P.slots + (s - fs)) * (NP + 1)) * kW + cl;
+            cc += __ldcg(cp);
 #pragma unroll
-                for (int k = 0; k < NP; ++k) tx[k] += __ldcg(cp + (1 + k) * kW);
-            }
+            for (int k = 0; k < NP; ++k) tx[k] += __ldcg(cp + (1 + k) * kW);
         }
-        ubg = unx;
     }
     Cc = cc;
 #pragma unroll
     for (int k = 0; k < NP; ++k) TX[k] = tx[k];
+}
+
+// Four multipliers theta[idx .. idx+3] of the stored array (16-byte aligned), as doubles.
+template <typename TS>
+__device__ __forceinline__ void load_theta4(const TS *th, long long idx, float iscl, double (&o)[4])
+{
+    if constexpr (std::is_same<TS, double>::value) {
+        const double2 a = __ldcg(reinterpret_cast<const double2 *>(th + idx));
+        const double2 b = __ldcg(reinterpret_cast<const double2 *>(th + idx + 2));
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    } else {
+        using St = Store<TS>;
+        float t[4];
+        St::unpack(__ldcg(reinterpret_cast<const typename St::Vec *>(th + idx)), t, iscl);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[j] = (double)t[j];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Finite ball in Q_2: sum of squares of the clamped multipliers of iteration l (the pairs this
+// CTA's pair pass wrote, and the y >= 0 rows of its fold rows), and the radial scaling of the
+// stored array once foldA(l) knows the factor.  FP64 sums; FP32 or FP64 storage.
+// ---------------------------------------------------------------------------
+template <typename TS, int NP>
+__device__ void phase_ball_norm(const Params &P, long long ell, double *red, long long vc)
+{
+    const int p = (int)(ell & 1);
+    const TS *__restrict__ th = (const TS *)P.theta[p];
+    const long long N = P.N, ld = P.ld;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double ss = 0.0;
+    long long u = unit_begin(P, vc);
+    const long long uend = unit_begin(P, vc + 1);
+    while (u < uend) {
+        const long long s = u / N, r0 = u - s * N, r1 = min(N, r0 + (uend - u));
+        const long long col0 = s * kW + (warp & 1) * 128 + lane * 4;
+        if (col0 < ld)
+            for (long long r = r0 + (warp >> 1); r < r1; r += kWR) {
+                double t[4];
+                load_theta4<TS>(th, r * ld + col0, P.st_inv_scale, t);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) ss += t[j] * t[j];   // padding columns and diagonal hold 0
+            }
+        u += r1 - r0;
+    }
+    for (RowIter it(P, vc); it.more(); it.next()) {
+        const long long l = it.row();
+        if (l < N) {
+            const double m = __ldcg(P.mu[p] + l);
+            ss += m * m;
+        }
+    }
+    double vals[1] = {ss};
+    const bool ismax[1] = {false};
+    block_reduce<1>(vals, ismax, red);
+    if (threadIdx.x == 0) P.ballpart[vc] = vals[0];
+}
+
+template <typename TS>
+__device__ void phase_ball_scale(const Params &P, long long ell, long long vc)
+{
+    const int p = (int)(ell & 1);
+    const double c = __ldcg(&P.st->scal[p].ball_c);
+    if (!(c < 1.0)) return;
+    if constexpr (std::is_same<TS, float>::value || std::is_same<TS, double>::value) {
+        TS *__restrict__ th = (TS *)P.theta[p];
+        const long long N = P.N, ld = P.ld;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        long long u = unit_begin(P, vc);
+        const long long uend = unit_begin(P, vc + 1);
+        while (u < uend) {
+            const long long s = u / N, r0 = u - s * N, r1 = min(N, r0 + (uend - u));
+            const long long col0 = s * kW + (warp & 1) * 128 + lane * 4;
+            if (col0 < ld)
+                for (long long r = r0 + (warp >> 1); r < r1; r += kWR)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) th[r * ld + col0 + j] = (TS)((double)th[r * ld + col0 + j] * c);
+            u += r1 - r0;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1320,12 +1423,37 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red, long lo
         }
         __syncthreads();
     }
+    // finite ball: theta^(1)_l = c Pi_{>=0}(.), c = min(1, B_theta / ||(clamped pairs, clamped mu)||_2),
+    // from the partial sums of squares of the norm phase, reduced in the same order by every CTA
+    __shared__ double s_ballc;
+    double ballc = 1.0;
+    if (P.ball) {
+        if (threadIdx.x < 32) {
+            double ss = 0.0;
+            for (int i = threadIdx.x; i < P.G; i += 32) ss += __ldcg(P.ballpart + i);
+            ss = warp_sum(ss);
+            if (threadIdx.x == 0) {
+                const double nrm = sqrt(ss);
+                s_ballc = nrm > P.B_theta ? P.B_theta / nrm : 1.0;
+                if (vc == 0) P.st->scal[p].ball_c = s_ballc;
+            }
+        }
+        __syncthreads();
+        ballc = s_ballc;
+    }
     double a = 0.0, b = 0.0, cc = 0.0, mviol = 0.0, mcomp = 0.0, sviol = 0.0, smuy = 0.0;
     for (RowIter it(P, vc); it.more(); it.next()) {
         const long long l = it.row();
         if (l >= N) continue;
         double R, Cc, TX[NP];
         gather_adjoint<NP>(P, l, R, Cc, TX);
+        if (P.ball && ballc < 1.0) {
+            R *= ballc;
+            Cc *= ballc;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) TX[k] *= ballc;
+            P.mu[p][l] = __ldcg(P.mu[p] + l) * ballc;
+        }
         const double v = R - Cc;               // (A_1^T theta)_l = row sum - column sum
         P.v[p][l] = v;
         const double hl = __ldg(P.h + l), mu = __ldcg(P.mu[p] + l);
@@ -1372,23 +1500,6 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red, long lo
 // ---------------------------------------------------------------------------
 // KKT pass at theta^(1)_l: per-pair g = (C eta)_p; FP32 (screen) or FP64
 // ---------------------------------------------------------------------------
-// Four multipliers theta[idx .. idx+3] of the stored array (16-byte aligned), as doubles.
-template <typename TS>
-__device__ __forceinline__ void load_theta4(const TS *th, long long idx, float iscl, double (&o)[4])
-{
-    if constexpr (std::is_same<TS, double>::value) {
-        const double2 a = __ldcg(reinterpret_cast<const double2 *>(th + idx));
-        const double2 b = __ldcg(reinterpret_cast<const double2 *>(th + idx + 2));
-        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
-    } else {
-        using St = Store<TS>;
-        float t[4];
-        St::unpack(__ldcg(reinterpret_cast<const typename St::Vec *>(th + idx)), t, iscl);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) o[j] = (double)t[j];
-    }
-}
-
 // With FP64 multipliers the screen is the FP64 evaluation itself (F64X).
 template <typename TS, int NP, bool F64>
 __device__ void phase_kkt(const Params &P, long long ell, double *red, long long vc)

@@ -9,14 +9,17 @@
 
 namespace crk {
 
-enum Phase : int { PH_FOLDB = 0, PH_PAIR = 1, PH_FOLDA = 2, PH_KKT32 = 3, PH_KKT64 = 4, PH_DECIDE32 = 5, PH_DECIDE64 = 6 };
+enum Phase : int {
+    PH_FOLDB = 0, PH_PAIR = 1, PH_FOLDA = 2, PH_KKT32 = 3, PH_KKT64 = 4, PH_DECIDE32 = 5, PH_DECIDE64 = 6,
+    PH_BALL_NORM = 7, PH_BALL_SCALE = 8   // finite B_theta: norm of the clamped iterate, radial scaling
+};
 
 // Dynamic shared memory of the pair pass (the larger of the CUDA-core and tensor-core layouts;
 // the FP64 pass stages nothing in shared memory).
 template <typename TS, int NP> constexpr size_t pair_smem_bytes()
 {
     if constexpr (std::is_same<TS, double>::value) {
-        return 0;
+        return f64_smem_bytes<NP>();
     } else {
         return PairSmem<TS, NP>::bytes > TcShape<TS, NP>::bytes ? PairSmem<TS, NP>::bytes : TcShape<TS, NP>::bytes;
     }
@@ -140,6 +143,8 @@ k_phase(const __grid_constant__ Params P, int phase, long long ell, double tol, 
         break;
     }
     case PH_FOLDA: phase_foldA<NP>(P, ell, red, blockIdx.x); break;
+    case PH_BALL_NORM: phase_ball_norm<TS, NP>(P, ell, red, blockIdx.x); break;
+    case PH_BALL_SCALE: phase_ball_scale<TS>(P, ell, blockIdx.x); break;
     case PH_KKT32: phase_kkt<TS, NP, false>(P, ell, red, blockIdx.x); break;
     case PH_KKT64: phase_kkt<TS, NP, true>(P, ell, red, blockIdx.x); break;
     case PH_DECIDE32:

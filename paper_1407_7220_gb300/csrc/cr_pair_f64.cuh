@@ -9,15 +9,20 @@
 // sums, column sums, Theta^T X) accumulated in FP64 into FP64 partials (the layouts of the FP32
 // pass).  The problems it serves are small (their two arrays sit in L2), so the tiles are read
 // with plain coalesced loads: the CTA partition into (stripe, row) units, the warp layout (2
-// warps across a 256-column stripe, 4 row groups, 4 columns per lane) and the partial layouts
-// are those of the streaming pass.  GB300's FP64 pipe is narrow, so the grid uses every SM.
+// warps across a 256-column stripe, 4 row groups, 4 columns per lane) and the row partials are
+// those of the streaming pass; the 4 row groups' column partials are added in shared memory
+// (fixed order) so that the fold reads one block per CTA segment.  GB300's FP64 pipe is narrow,
+// so the grid uses every SM.
 #pragma once
 
 #include "cr_kernels.cuh"
 
 namespace crk {
 
-template <int NP> __device__ void phase_pair_f64(const Params &P, long long ell, long long vc)
+// Shared memory of the pass: one (NP + 1) x 256 block of FP64 column partials.
+template <int NP> constexpr size_t f64_smem_bytes() { return (size_t)(NP + 1) * kW * sizeof(double) + 128; }
+
+template <int NP> __device__ void phase_pair_f64(const Params &P, long long ell, unsigned char *smem, long long vc)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wc = warp & 1, rg = warp >> 1;
@@ -89,15 +94,26 @@ template <int NP> __device__ void phase_pair_f64(const Params &P, long long ell,
             for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
             if (lane == 0) rp[r * P.Q] = rs;
         }
-        // column partials of this segment, one block per row group (added in FP64 by foldA)
-        const int slotc = (int)(s - first_stripe);
-        double *cp = P.colpart64 + (((vc * P.slots + slotc) * kWR + rg) * (NP + 1)) * kW + wc * 128 + lane * 4;
+        // column partials of this segment: the row groups added in order 0..3 in shared memory,
+        // then one block to global memory (added in FP64 by foldA)
+        double *red = reinterpret_cast<double *>(smem);
+        const int cl = wc * 128 + lane * 4;
+        for (int g = 0; g < kWR; ++g) {
+            if (rg == g) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            cp[j] = csum[j];
+                for (int j = 0; j < 4; ++j) {
+                    red[cl + j] = g == 0 ? csum[j] : red[cl + j] + csum[j];
 #pragma unroll
-            for (int k = 0; k < NP; ++k) cp[(1 + k) * kW + j] = acc[j][k];
+                    for (int k = 0; k < NP; ++k)
+                        red[(1 + k) * kW + cl + j] = g == 0 ? acc[j][k] : red[(1 + k) * kW + cl + j] + acc[j][k];
+                }
+            }
+            __syncthreads();
         }
+        const int slotc = (int)(s - first_stripe);
+        double *cp = P.colpart64 + ((vc * P.slots + slotc) * (NP + 1)) * kW;
+        for (int i = tid; i < (NP + 1) * kW; i += kThreads) cp[i] = red[i];
+        __syncthreads();
         u += r1 - r0;
     }
     __syncthreads();

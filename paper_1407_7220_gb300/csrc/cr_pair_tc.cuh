@@ -334,7 +334,7 @@ __device__ __forceinline__ void tc_flush_rows(float (&v)[8], long long r8, long 
     v[0] += __shfl_xor_sync(full, v[0], 1);
     if ((lane & 3) == 0) {
         const long long row = r8 + ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-        if (row < r1) rp[row * Q] = v[0];
+        if (row < r1) st_keep(rp + row * Q, v[0], l2_evict_last());
     }
 }
 
@@ -358,7 +358,7 @@ __device__ __forceinline__ void tc_flush_rows(float (&v)[4], long long r4, long 
     v[0] += __shfl_xor_sync(full, v[0], 1);
     if ((lane & 7) == 0) {
         const long long row = r4 + ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
-        if (row < r1) rp[row * Q] = v[0];
+        if (row < r1) st_keep(rp + row * Q, v[0], l2_evict_last());
     }
 }
 
@@ -869,11 +869,12 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
                 const int slotc = (int)(s - first_stripe);
                 float *cp = P.colpart + ((vc * P.slots + slotc) * P.cgroups * (NP + 1)) * kW + 2 * m + eo;
                 const int n = P.n;
+                const uint64_t keep = l2_evict_last();
 #pragma unroll
                 for (int j = 0; j < H2; ++j) {
                     const int kk = h0 + j;
-                    if (kk == n) cp[0] = d2acc[j];
-                    else if (kk < NP) cp[(1 + kk) * kW] = kk < n ? d2acc[j] : 0.0f;
+                    if (kk == n) st_keep(cp, d2acc[j], keep);
+                    else if (kk < NP) st_keep(cp + (1 + kk) * kW, kk < n ? d2acc[j] : 0.0f, keep);
                 }
             }
             u += r1 - r0;

@@ -301,13 +301,42 @@ long long unit_begin_host(long long c, long long total, long long N, int G)
     return s * N + ((u - s * N) & ~7ll);
 }
 
-// The device's partition table: first unit of every CTA (G + 1 entries, capacity cap).
+// Entries of the partition table for a grid of up to G CTAs over S stripes.
+size_t partition_entries(long long G, long long S) { return (size_t)(2 * G + 1 + 2 * S); }
+
+// The device's partition table (capacity partition_entries(G at creation, S)):
+//   ubeg[c], c = 0..G: first unit of CTA c;
+//   cfs[c], c < G: first stripe of CTA c, or -1 for a CTA without units;
+//   sc0[s], sc1[s], s < S: the CTAs [sc0, sc1) whose unit ranges meet stripe s (the folds add
+//   their column partials in this ascending order).
 cr_status upload_partition(cr_ctx *h, long long *dtab)
 {
-    const Params &P = h->P;
-    std::vector<long long> t((size_t)P.G + 1);
-    for (long long c = 0; c <= P.G; ++c) t[c] = unit_begin_host(c, P.total, P.N, P.G);
+    Params &P = h->P;
+    const long long G = P.G, N = P.N, S = P.S;
+    std::vector<long long> t(partition_entries(G, S), 0);
+    long long *ub = t.data(), *cfs = ub + G + 1, *sc0 = cfs + G, *sc1 = sc0 + S;
+    for (long long c = 0; c <= G; ++c) ub[c] = unit_begin_host(c, P.total, N, (int)G);
+    for (long long s = 0; s < S; ++s) {
+        sc0[s] = G;
+        sc1[s] = 0;
+    }
+    for (long long c = 0; c < G; ++c) {
+        if (ub[c + 1] <= ub[c]) {
+            cfs[c] = -1;
+            continue;
+        }
+        cfs[c] = ub[c] / N;
+        const long long sl = (ub[c + 1] - 1) / N;
+        for (long long s = cfs[c]; s <= sl; ++s) {
+            sc0[s] = std::min(sc0[s], c);
+            sc1[s] = std::max(sc1[s], c + 1);
+        }
+    }
     CR_CUDA(h, cudaMemcpy(dtab, t.data(), sizeof(long long) * t.size(), cudaMemcpyHostToDevice));
+    P.ubeg = dtab;
+    P.cfs = dtab + G + 1;
+    P.sc0 = P.cfs + G;
+    P.sc1 = P.sc0 + S;
     return CR_OK;
 }
 
@@ -358,7 +387,7 @@ struct ProfScope {
 
 int phase_kind(int phase)
 {
-    if (phase == crk::PH_PAIR) return 0;
+    if (phase == crk::PH_PAIR || phase == crk::PH_BALL_NORM || phase == crk::PH_BALL_SCALE) return 0;
     if (phase == crk::PH_FOLDA || phase == crk::PH_FOLDB) return 1;
     return 2;
 }
@@ -399,7 +428,9 @@ cr_status run_phases(cr_ctx *h, long long ell0, long long ell1, int check_every,
     for (long long ell = ell0; ell <= ell1; ++ell) {
         if (!h->prepared) CR_TRY(launch_phase(h, crk::PH_FOLDB, ell, tol));
         CR_TRY(launch_phase(h, crk::PH_PAIR, ell, tol));
+        if (h->P.ball) CR_TRY(launch_phase(h, crk::PH_BALL_NORM, ell, tol));
         CR_TRY(launch_phase(h, crk::PH_FOLDA, ell, tol));   // with P.fuse also foldB(ell + 1)
+        if (h->P.ball) CR_TRY(launch_phase(h, crk::PH_BALL_SCALE, ell, tol));
         if (check_every > 0 && ((ell % check_every) == 0 || ell == ell1)) {
             CR_TRY(launch_phase(h, crk::PH_KKT32, ell, tol));
             CR_TRY(launch_phase(h, crk::PH_DECIDE32, ell, tol, 1));
@@ -488,16 +519,18 @@ cr_status init_state(cr_ctx *h)
     }
     CR_CUDA(h, cudaMemsetAsync(P.rowpart, 0, sizeof(float) * (size_t)P.Q * h->N, h->stream));
     CR_CUDA(h, cudaMemsetAsync(P.colpart, 0, sizeof(float) * (size_t)P.G * P.slots * P.cgroups * (h->NP + 1) * crk::kW, h->stream));
+    if (P.ball) CR_CUDA(h, cudaMemsetAsync(P.ballpart, 0, sizeof(double) * (size_t)P.G, h->stream));
     if (P.f64) {
         CR_CUDA(h, cudaMemsetAsync(P.rowpart64, 0, sizeof(double) * (size_t)P.Q * h->N, h->stream));
         CR_CUDA(h, cudaMemsetAsync(P.colpart64, 0,
-                                   sizeof(double) * (size_t)P.G * P.slots * crk::kWR * (h->NP + 1) * crk::kW,
+                                   sizeof(double) * (size_t)P.G * P.slots * (h->NP + 1) * crk::kW,
                                    h->stream));
     }
     DevState st;
     std::memset(&st, 0, sizeof st);
     st.scal[0].t = 1.0;   // t_1 = 1 (Iteration 0 of Fig. 2)
     st.scal[0].dual = -std::numeric_limits<double>::infinity();
+    st.scal[0].ball_c = 1.0;
     st.scal[1] = st.scal[0];
     CR_CUDA(h, cudaMemcpyAsync(P.st, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
     // eta(theta^(1)_0 = 0): y = h, xi = 0 (foldA of iteration 0 over zero partials)
@@ -607,6 +640,11 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
         return fail(h, CR_EINVAL, "FP64 multipliers are compiled for n <= %d (n = %d)", crk::kMaxNF64, n);
     if (f64 && (o.pair_engine == CR_PAIR_TENSOR_CORES || o.record_every > 0 || np_override > 0))
         return fail(h, CR_EINVAL, "FP64 multipliers: CUDA-core pass only, no record_every, not in a batch");
+    const bool ball = o.B_theta > 0.0 && std::isfinite(o.B_theta);
+    if (ball && (o.theta_dtype == CR_THETA_BF16 || o.theta_dtype == CR_THETA_F16 || o.pair_engine == CR_PAIR_TENSOR_CORES ||
+                 o.driver == CR_DRIVER_PERSISTENT || o.record_every > 0 || np_override > 0 || aopt))
+        return fail(h, CR_EINVAL, "finite B_theta: FP32 or FP64 multipliers, CUDA-core pass, phase driver, single "
+                                  "P-APG instances, no record_every");
     if (o.kkt_every < 1) return fail(h, CR_EINVAL, "kkt_every must be >= 1");
     h->N = N;
     h->n = n;
@@ -662,7 +700,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     // is bound by GB300's narrow FP64 pipe and spreads over more SMs
     const long long min_units = f64 ? 4 : 40;
     if (o.grid <= 0) G = (int)std::max<long long>(1, std::min<long long>(G, total / min_units));
-    h->persistent_ok = coop && per_sm > 0 && G <= max_coresident;
+    h->persistent_ok = coop && per_sm > 0 && G <= max_coresident && !ball;
     if (np_override > 0) h->persistent_ok = false;   // batch member: driven by the batch kernel only
     if (o.driver == CR_DRIVER_PERSISTENT && !h->persistent_ok)
         return fail(h, CR_EINVAL, "persistent driver: grid %d exceeds %d co-resident CTAs", G, max_coresident);
@@ -703,7 +741,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     const int tc_from = o.theta_dtype == CR_THETA_F32 ? 16 : 8;
     P.tc = (o.pair_engine == CR_PAIR_TENSOR_CORES ||
             (o.pair_engine == CR_PAIR_AUTO && h->NP >= tc_from && o.record_every <= 0 && !batch_member &&
-             o.driver != CR_DRIVER_PERSISTENT && !f64))
+             o.driver != CR_DRIVER_PERSISTENT && !f64 && !ball))
                ? 1
                : 0;
     if (P.tc) h->persistent_ok = false;   // the tensor-core pass runs in its own launch (phase driver)
@@ -797,20 +835,22 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     CR_TRY(dev_alloc(h, &P.colpart, (size_t)G * P.slots * P.cgroups * (h->NP + 1) * crk::kW));
     {
         long long *tab = nullptr;
-        CR_TRY(dev_alloc(h, &tab, (size_t)G + 1));
-        P.ubeg = tab;
+        CR_TRY(dev_alloc(h, &tab, partition_entries(G, S)));
         CR_TRY(upload_partition(h, tab));
     }
     CR_TRY(dev_alloc(h, &P.foldpart, (size_t)G * 8));
     CR_TRY(dev_alloc(h, &P.kktpart, (size_t)G * 8));
     CR_TRY(dev_alloc(h, &P.st, 1));
     P.f64 = f64 ? 1 : 0;
+    P.ball = ball ? 1 : 0;
+    P.B_theta = ball ? o.B_theta : 0.0;
+    if (ball) CR_TRY(dev_alloc(h, &P.ballpart, (size_t)G));
     if (f64) {
         CR_TRY(dev_alloc(h, &P.rec64, (size_t)N * REC));
         CR_TRY(dev_alloc(h, &P.ccol2_64, (size_t)N));
         CR_TRY(dev_alloc(h, &P.xi2_64, (size_t)N * h->NP));
         CR_TRY(dev_alloc(h, &P.rowpart64, (size_t)P.Q * N));
-        CR_TRY(dev_alloc(h, &P.colpart64, (size_t)G * P.slots * crk::kWR * (h->NP + 1) * crk::kW));
+        CR_TRY(dev_alloc(h, &P.colpart64, (size_t)G * P.slots * (h->NP + 1) * crk::kW));
     }
     if (h->alcc) {
         for (int b = 0; b < 2; ++b) {
@@ -1549,6 +1589,8 @@ struct cr_batch_ctx {
     int gcheck = 0;
     double gtol = -1.0;
     bool graph_ok = true;
+    long long graph_launches = 0;     // launches replayed from the captured CUDA graph
+    long long direct_launches = 0;    // launches made directly (capture not available)
     int factor = 1;                   // work granularity chosen by the autotuner
     long long iters = 0;
     std::string err;
@@ -1696,7 +1738,9 @@ cr_status batch_launch(cr_batch_ctx *b, long long chunk, int check_every, double
     }
     if (b->gexec) {
         CR_BCUDA(b, cudaGraphLaunch(b->gexec, b->stream));
+        ++b->graph_launches;
     } else {
+        ++b->direct_launches;
         CR_BCUDA(b, cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned long long), b->stream));
         CR_BCUDA(b, cudaLaunchCooperativeKernel(b->ks.batch, dim3(b->Gphys), dim3(crk::kThreads), args, b->ks.smem,
                                                 b->stream));
@@ -1908,6 +1952,19 @@ cr_status cr_batch_info(cr_batch_handle b, int32_t *factor, int32_t *grid, int64
     if (factor) *factor = b->factor;
     if (grid) *grid = b->Gphys;
     if (iters) *iters = b->iters;
+    return CR_OK;
+}
+
+cr_status cr_batch_stats(cr_batch_handle b, int32_t *graph_live, int64_t *graph_launches, int64_t *direct_launches,
+                         int32_t *tuned, double *tune_ms)
+{
+    if (!b) return CR_EINVAL;
+    if (graph_live) *graph_live = (b->graph_ok && b->gexec) ? 1 : 0;
+    if (graph_launches) *graph_launches = b->graph_launches;
+    if (direct_launches) *direct_launches = b->direct_launches;
+    if (tuned) *tuned = (int32_t)b->tune_factor.size();
+    if (tune_ms)
+        for (size_t i = 0; i < b->tune_ms.size(); ++i) tune_ms[i] = b->tune_ms[i];
     return CR_OK;
 }
 

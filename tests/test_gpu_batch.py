@@ -65,3 +65,17 @@ def test_batch_solve_reaches_tolerance_per_instance():
     o = O.Solver(X, yb, gamma=0.1, restart=True)
     o.solve(1e-10, 2_000_000, check_every=50)
     assert _rel(bs.member(0).solution()[0], o.y_hat) <= 5e-4
+
+
+def test_batch_runs_from_its_cuda_graph_and_autotunes():
+    # the persistent launch is captured once in a CUDA graph and replayed chunk after chunk;
+    # the autotuner timed every granularity candidate
+    import paper_1407_7220_gb300 as crg
+    inst = _instances(SIZES, seed=3)
+    bs = crg.BatchSolver(inst, gamma=0.1, stochastic_round=0, restart=0)
+    bs.iterate(40)
+    bs.iterate(40)
+    st = bs.stats()
+    print(st)
+    assert st["graph_live"] and st["graph_launches"] >= 2 and st["direct_launches"] == 0
+    assert len(st["tune_ms"]) == 5 and min(st["tune_ms"]) > 0.0

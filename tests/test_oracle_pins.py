@@ -275,3 +275,133 @@ def test_oracle_jvp_matches_central_differences():
     _, d1 = O.papg_jvp(X, yb, g, L, s, K, dy, dX)
     _, d2 = O.papg_jvp(X, yb, g, L, s, K, 2.5 * dy, 2.5 * dX)
     np.testing.assert_allclose(d2, 2.5 * d1, rtol=1e-12, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Q_2 with a finite ball (Eq. (lambda_dual)): {lambda >= 0, ||lambda||_2 <= B_theta}
+# --------------------------------------------------------------------------
+def test_large_ball_leaves_the_iterates_unchanged():
+    X, yb = _inst(N=25, n=2, seed=6)
+    a = O.Solver(X, yb, gamma=0.1)
+    a.iterate(40)
+    big = 10.0 * max(1.0, np.sqrt((a.theta1 ** 2).sum() + (a.mu1 ** 2).sum()))
+    b = O.Solver(X, yb, gamma=0.1, B_theta=big)
+    b.iterate(40)
+    assert np.array_equal(a.theta1, b.theta1) and np.array_equal(a.y_hat, b.y_hat)
+
+
+@pytest.mark.parametrize("B", [0.05, 0.3])
+def test_ball_step_is_the_euclidean_projection(B):
+    # one step of Fig. 2 from theta0 (beta = 0 at the first iteration): theta^(1) = Pi_{Q_2}(v),
+    # v = theta0 - (1/L) C eta(theta0), built here from the explicit matrices; the projection
+    # is computed independently by SLSQP on min ||q - v||^2 s.t. q >= 0, ||q||^2 <= B^2
+    from scipy.optimize import minimize
+    X, yb = _inst(N=5, n=2, seed=8)
+    N = 5
+    rng = np.random.default_rng(2)
+    th0 = rng.uniform(0.0, 0.2, size=(N, N))
+    np.fill_diagonal(th0, 0.0)
+    mu0 = rng.uniform(0.0, 0.05, size=N)
+    s = O.Solver(X, yb, gamma=0.1, theta0=th0, mu0=mu0, B_theta=B)
+    C, pairs = D.big_C(X)
+    lam0 = np.concatenate([D.theta_vec(th0, pairs), mu0])
+    Hinv = np.concatenate([np.ones(N), np.full(N * 2, 1.0 / 0.1)])
+    htil = np.concatenate([s.h, np.zeros(N * 2)])
+    eta0 = Hinv * (htil + C.T @ lam0)
+    v = lam0 - (C @ eta0) / s.L
+    res = minimize(lambda q: 0.5 * np.sum((q - v) ** 2), np.maximum(v, 0.0) * 0.5, jac=lambda q: q - v,
+                   method="SLSQP", bounds=[(0.0, None)] * v.size,
+                   constraints=[{"type": "ineq", "fun": lambda q: B * B - q @ q, "jac": lambda q: -2.0 * q}],
+                   options={"ftol": 1e-15, "maxiter": 500})
+    s.iterate(1)
+    got = np.concatenate([D.theta_vec(s.theta1, pairs), s.mu1])
+    assert np.sqrt(got @ got) <= B * (1 + 1e-12) and got.min() >= 0.0
+    np.testing.assert_allclose(got, res.x, rtol=0, atol=1e-7)
+
+
+def test_dual_gradient_ascent_with_ball_is_monotone():
+    # projected gradient ascent with step 1/L on an L-smooth concave function over the convex
+    # set Q_2 never decreases the dual value, with the ball active or not
+    X, yb = _inst(N=15, n=2, seed=4)
+    s = O.Solver(X, yb, gamma=0.05, momentum=False, B_theta=0.02)
+    prev, active = -np.inf, 0
+    for _ in range(200):
+        s.iterate(1)
+        d = s.metrics["dual"]
+        assert d >= prev - 1e-12 * abs(d)
+        prev = d
+        nrm = np.sqrt((s.theta1 ** 2).sum() + (s.mu1 ** 2).sum())
+        assert nrm <= 0.02 * (1 + 1e-12)
+        active += nrm >= 0.02 * (1 - 1e-9)
+    assert active > 100   # the ball constraint binds along the run
+
+
+# --------------------------------------------------------------------------
+# Lemma 1 (Sec. II-C): ||y(gamma) - y*||_2 <= B_xi sqrt(gamma), and special cases
+# --------------------------------------------------------------------------
+def _convex_ls_1d(x, yb):
+    """Least-squares convex fit in one dimension (the textbook problem problem (original)
+    reduces to for n = 1): with the points sorted by x, the slopes between neighbours must not
+    decrease, D y >= 0; the projection of ybar onto that cone by the dual NNLS
+    min_{lam >= 0} ||D^T lam + ybar||, y* = ybar + D^T lam."""
+    from scipy.optimize import nnls
+    order = np.argsort(x)
+    xs, ys = x[order], yb[order]
+    N = len(xs)
+    D_ = np.zeros((N - 2, N))
+    for i in range(1, N - 1):
+        dl, dr = xs[i] - xs[i - 1], xs[i + 1] - xs[i]
+        D_[i - 1, i - 1] = 1.0 / dl
+        D_[i - 1, i] = -1.0 / dl - 1.0 / dr
+        D_[i - 1, i + 1] = 1.0 / dr
+    lam, _ = nnls(D_.T, -ys, maxiter=100 * N)
+    y_sorted = ys + D_.T @ lam
+    # minimum-norm subgradients: at each point, the value of [left slope, right slope] closest to 0
+    slopes = np.diff(y_sorted) / np.diff(xs)
+    lo = np.concatenate([[-np.inf], slopes])
+    hi = np.concatenate([slopes, [np.inf]])
+    xi_sorted = np.clip(0.0, lo, hi)
+    y = np.empty(N)
+    xi = np.empty(N)
+    y[order], xi[order] = y_sorted, xi_sorted
+    return y, xi
+
+
+def test_one_dimensional_case_and_holder_continuity():
+    from oracle import exact as E
+    X, yb = _inst(N=20, n=1, seed=13)
+    y_star, xi_star = _convex_ls_1d(X[:, 0], yb)
+    B_xi = np.linalg.norm(xi_star)
+    assert np.all(np.diff(np.diff(y_star[np.argsort(X[:, 0])]) / np.diff(np.sort(X[:, 0]))) >= -1e-10)
+    for gamma in (1e-1, 1e-2, 1e-3, 1e-4, 1e-5):
+        y_g, xi_g, _, _ = E.solve(X, yb, gamma)
+        assert np.linalg.norm(y_g - y_star) <= B_xi * np.sqrt(gamma) * (1 + 1e-9)   # Lemma 1
+        assert np.linalg.norm(xi_g) <= B_xi * (1 + 1e-9)                            # from its proof
+    # and the P-APG oracle at gamma = 1e-3 lands on the same y(gamma)
+    o = O.Solver(X, yb, gamma=1e-3, restart=True, restart_tol=1e-12)
+    o.solve(1e-11, 3_000_000, check_every=100)
+    y_g, _, _, _ = E.solve(X, yb, 1e-3)
+    np.testing.assert_allclose(o.y_hat, y_g, rtol=0, atol=1e-8)
+
+
+def test_noiseless_affine_data():
+    # ybar = a^T x + b is itself feasible with the subgradients xi_l = a (at gamma = 0 it is the
+    # solution, with B_xi = sqrt(N) ||a||); at gamma > 0 Lemma 1 bounds the fit's deviation
+    from oracle import exact as E
+    rng = np.random.default_rng(17)
+    N, n = 25, 2
+    X = rng.uniform(-1.0, 1.0, size=(N, n))
+    a, b = np.array([0.7, -1.3]), 0.4
+    yb = X @ a + b
+    B_xi = np.sqrt(N) * np.linalg.norm(a)
+    prev = np.inf
+    for gamma in (1e-1, 1e-2, 1e-3, 1e-4):
+        y_g, xi_g, _, _ = E.solve(X, yb, gamma)
+        dev = np.linalg.norm(y_g - yb)
+        assert dev <= B_xi * np.sqrt(gamma) * (1 + 1e-9)
+        assert dev <= prev + 1e-12     # y(gamma) moves toward ybar as gamma decreases
+        prev = dev
+    o = O.Solver(X, yb, gamma=1e-2, restart=True, restart_tol=1e-12)
+    o.solve(1e-11, 3_000_000, check_every=100)
+    y_g, _, _, _ = E.solve(X, yb, 1e-2)
+    np.testing.assert_allclose(o.y_hat, y_g, rtol=0, atol=1e-8)
