@@ -132,6 +132,16 @@ cr_status cr_create_device(const float *dX, const float *dybar, int64_t N, int32
 /* Returns the handle to Iteration 0 of Fig. 2 (theta = 0, t = 1). */
 cr_status cr_reset(cr_handle h);
 
+/* Widens the stored multipliers of a BF16 or FP16 handle to FP32 in place of the iteration:
+ * both stored iterates (theta^(1)_l, theta^(1)_{l-1}) are converted exactly, the momentum state,
+ * the FP64 aggregates and the iteration count are kept, and later iterations run with FP32
+ * multipliers (a precision schedule: cheap 16-bit iterations while the updates are large, FP32
+ * once the 16-bit rounding floor is reached).  The tensor-core pass stays when the options allow
+ * it at FP32 (n >= 16 or pair_engine = CR_PAIR_TENSOR_CORES); otherwise the CUDA-core pass.
+ * Allocates the two FP32 arrays and frees the 16-bit ones.  CR_EINVAL for any other
+ * conversion.  Blocks. */
+cr_status cr_promote(cr_handle h, int32_t theta_dtype);
+
 /* Enqueues k iterations of P-APG (Fig. 2, steps 1-4) on the handle's stream and returns
  * without waiting.  Each iteration streams the multiplier array once (read theta^(1)_l,
  * theta^(1)_{l-1}; write theta^(1)_{l+1}). */

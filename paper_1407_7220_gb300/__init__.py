@@ -49,7 +49,7 @@ exported_symbols = (
     "cr_batch_create", "cr_batch_solve", "cr_batch_iterate", "cr_batch_reset", "cr_batch_instance",
     "cr_batch_info", "cr_batch_destroy", "cr_batch_last_error", "cr_backward", "cr_get_engine",
     "cr_alcc_options_default", "cr_alcc_create", "cr_alcc_iterate", "cr_alcc_solve", "cr_alcc_metrics",
-    "cr_alcc_info", "cr_problem_constants", "cr_batch_stats",
+    "cr_alcc_info", "cr_problem_constants", "cr_batch_stats", "cr_promote",
 )
 PROFILE_PAIR, PROFILE_FOLD, PROFILE_KKT, PROFILE_PERSISTENT = 0, 1, 2, 3
 
@@ -108,6 +108,8 @@ def lib():
             L.cr_create_device.argtypes = [fp, fp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Options),
                                            ctypes.POINTER(H)]
             L.cr_reset.argtypes = [H]
+            L.cr_promote.argtypes = [H, ctypes.c_int32]
+            L.cr_promote.restype = ctypes.c_int
             L.cr_iterate.argtypes = [H, ctypes.c_int64]
             L.cr_solve.argtypes = [H, ctypes.c_double, ctypes.c_int64, i64p]
             L.cr_objective.argtypes = [H, dp, dp, dp]
@@ -249,6 +251,12 @@ class Solver:
 
     def iterate(self, k: int):
         self._check(lib().cr_iterate(self._h, int(k)))
+
+    def promote(self, theta_dtype="f32"):
+        """cr_promote: continue the iteration with FP32 multipliers (from BF16 or FP16)."""
+        v = _DTYPES[theta_dtype.lower()] if isinstance(theta_dtype, str) else int(theta_dtype)
+        self._check(lib().cr_promote(self._h, v))
+        self.options.theta_dtype = v
 
     def solve(self, tol: float, max_iter: int) -> tuple[bool, int]:
         done = ctypes.c_int64()

@@ -15,6 +15,9 @@
 //          accumulate colsum(Theta2) and Theta2 (xibar2/gamma) for the X terms of xi2
 //   fold 2 (per point): Xbar += colsum(Theta2) xibar2/gamma - (Theta2 xibar2/gamma)
 // Accumulation uses FP64 atomics (order-dependent only at FP64 rounding level).
+// T = float reverses the FP32 pass (its two-chain residual); T = double reverses the FP64 pass
+// of cr_pair_f64.cuh (one chain, FP64 storage and arithmetic), so that the masks recomputed
+// here are the forward's in either case.
 #pragma once
 
 #include "cr_kernels.cuh"
@@ -24,18 +27,18 @@ namespace crk {
 constexpr int kBRows = 64;     // rows per backward task
 constexpr int kBCols = 128;    // columns per backward task (one warp width x 4)
 
-struct BwdParams {
+template <typename T> struct BwdParamsT {
     long long N, ld;
     int n, S128, REC;
-    float invL, beta, c1, c2;
+    T invL, beta, c1, c2;
     double invL_d, inv_gamma, shift;
-    const float *thc, *thp;         // theta1_{l-1}, theta1_{l-2}
-    const float *rowrec;            // N x REC {y2 - s, x}
-    const float *ccol2, *xi2;       // forward column data of iteration l
-    const float *b1, *b2;           // thetabar2_{l+1}, thetabar2_{l+2} (N x ld)
+    const T *thc, *thp;             // theta1_{l-1}, theta1_{l-2}
+    const T *rowrec;                // N x REC {y2 - s, x}
+    const T *ccol2, *xi2;           // forward column data of iteration l
+    const T *b1, *b2;               // thetabar2_{l+1}, thetabar2_{l+2} (N x ld)
     const float *ubar;              // dLoss/dyhat (N) on the last iteration, else null
-    const float *yb2, *ccolb, *xib; // pass 2 inputs: ybar2 (rows), xibar2.x/gamma - ybar2, xibar2/gamma (cols)
-    float *outb;                    // thetabar2_l (N x ld)
+    const T *yb2, *ccolb, *xib;     // pass 2 inputs: ybar2 (rows), xibar2.x/gamma - ybar2, xibar2/gamma (cols)
+    T *outb;                        // thetabar2_l (N x ld)
     double *acc_row, *acc_col;      // [N][NP+1] accumulators (zeroed by the folds)
     // fold inputs
     const double *X64, *h;
@@ -44,15 +47,43 @@ struct BwdParams {
     double beta_d, c1_d, c2_d;
     double *mub_out;                // mubar2_l
     double *ybar_acc, *X_acc;       // dLoss/dybar (N), dLoss/dX (N x n), FP64
-    float *yb2_out, *ccolb_out, *xib_out;
+    T *yb2_out, *ccolb_out, *xib_out;
+};
+using BwdParams = BwdParamsT<float>;
+
+template <typename T> struct Vec4Of;
+template <> struct Vec4Of<float> {
+    __device__ static __forceinline__ void load(const float *p, float (&o)[4])
+    {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    }
+    __device__ static __forceinline__ void store(float *p, const float (&v)[4])
+    {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <> struct Vec4Of<double> {
+    __device__ static __forceinline__ void load(const double *p, double (&o)[4])
+    {
+        const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    }
+    __device__ static __forceinline__ void store(double *p, const double (&v)[4])
+    {
+        *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2 *>(p + 2) = make_double2(v[2], v[3]);
+    }
 };
 
-template <int NP, int PASS>
+template <typename T, int NP, int PASS>
 __global__ void __launch_bounds__(256)
-k_adj_pass(const BwdParams B)
+k_adj_pass(const BwdParamsT<T> B)
 {
     constexpr int K1 = NP + 1;
-    __shared__ float red[8][K1][kBCols];
+    constexpr bool F64 = std::is_same<T, double>::value;
+    // FP32: the 8 warps' column sums meet in shared memory; FP64: each warp adds its own
+    __shared__ float red[F64 ? 1 : 8][F64 ? 1 : K1][F64 ? 1 : kBCols];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long N = B.N, ld = B.ld;
     const int REC = B.REC;
@@ -62,115 +93,125 @@ k_adj_pass(const BwdParams B)
         const long long col0 = stripe * kBCols + lane * 4;
         const bool vec_ok = col0 < ld;
         bool colv[4];
-        float ccol[4], xi[4][NP], cb[4], xb[4][NP], ub[4];
+        T ccol[4], xi[4][NP], cb[4], xb[4][NP];
+        float ub[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const long long c = col0 + j;
             colv[j] = c < N;
             ccol[j] = colv[j] ? B.ccol2[c] : 0.0f;
             ub[j] = (colv[j] && B.ubar) ? B.ubar[c] : 0.0f;
-            cb[j] = (PASS == 2 && colv[j]) ? B.ccolb[c] : 0.0f;
+            cb[j] = (PASS == 2 && colv[j]) ? B.ccolb[c] : (T)0;
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
-                xi[j][k] = colv[j] ? B.xi2[c * NP + k] : 0.0f;
-                xb[j][k] = (PASS == 2 && colv[j]) ? B.xib[c * NP + k] : 0.0f;
+                xi[j][k] = colv[j] ? B.xi2[c * NP + k] : (T)0;
+                xb[j][k] = (PASS == 2 && colv[j]) ? B.xib[c * NP + k] : (T)0;
             }
         }
-        float cacc[4][K1];
+        T cacc[4][K1];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
-            for (int k = 0; k < K1; ++k) cacc[j][k] = 0.0f;
+            for (int k = 0; k < K1; ++k) cacc[j][k] = (T)0;
         const long long r0 = rblk * kBRows, r1 = min(N, r0 + kBRows);
         for (long long r = r0 + warp; r < r1; r += 8) {
-            float rv[1 + NP];
+            T rv[1 + NP];
 #pragma unroll
             for (int q = 0; q < 1 + NP; ++q) rv[q] = B.rowrec[r * REC + q];
             const float ur = B.ubar ? B.ubar[r] : 0.0f;
-            const float ybr = PASS == 2 ? B.yb2[r] : 0.0f;
-            float tc[4] = {0, 0, 0, 0}, tp[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0}, a2[4] = {0, 0, 0, 0};
+            const T ybr = PASS == 2 ? B.yb2[r] : (T)0;
+            T tc[4] = {0, 0, 0, 0}, tp[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0}, a2[4] = {0, 0, 0, 0};
             if (vec_ok) {
-                const float4 t4 = *reinterpret_cast<const float4 *>(B.thc + r * ld + col0);
-                const float4 p4 = *reinterpret_cast<const float4 *>(B.thp + r * ld + col0);
-                tc[0] = t4.x; tc[1] = t4.y; tc[2] = t4.z; tc[3] = t4.w;
-                tp[0] = p4.x; tp[1] = p4.y; tp[2] = p4.z; tp[3] = p4.w;
-                if (B.b1) {
-                    const float4 q4 = *reinterpret_cast<const float4 *>(B.b1 + r * ld + col0);
-                    a1[0] = q4.x; a1[1] = q4.y; a1[2] = q4.z; a1[3] = q4.w;
-                }
-                if (B.b2) {
-                    const float4 q4 = *reinterpret_cast<const float4 *>(B.b2 + r * ld + col0);
-                    a2[0] = q4.x; a2[1] = q4.y; a2[2] = q4.z; a2[3] = q4.w;
-                }
+                Vec4Of<T>::load(B.thc + r * ld + col0, tc);
+                Vec4Of<T>::load(B.thp + r * ld + col0, tp);
+                if (B.b1) Vec4Of<T>::load(B.b1 + r * ld + col0, a1);
+                if (B.b2) Vec4Of<T>::load(B.b2 + r * ld + col0, a2);
             }
-            float racc[K1];
+            T racc[K1];
 #pragma unroll
-            for (int k = 0; k < K1; ++k) racc[k] = 0.0f;
-            float outv[4];
+            for (int k = 0; k < K1; ++k) racc[k] = (T)0;
+            T outv[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                outv[j] = 0.0f;
+                outv[j] = (T)0;
                 if (!colv[j] || col0 + j == r) continue;
                 // the forward pair pass, operation for operation
-                const float th2 = fmaf(B.beta, tc[j] - tp[j], tc[j]);
-                float g0 = rv[0] + ccol[j], g1 = 0.0f;
+                const T th2 = fma(B.beta, tc[j] - tp[j], tc[j]);
+                T v;
+                if constexpr (F64) {
+                    T g = rv[0] + ccol[j];   // one chain, as the FP64 pass
 #pragma unroll
-                for (int k = 0; k < NP; ++k) {
-                    if (k & 1) g1 = fmaf(-xi[j][k], rv[1 + k], g1);
-                    else g0 = fmaf(-xi[j][k], rv[1 + k], g0);
+                    for (int k = 0; k < NP; ++k) g = fma(-xi[j][k], rv[1 + k], g);
+                    v = fma(-g, B.invL, th2);
+                } else {
+                    T g0 = rv[0] + ccol[j], g1 = 0.0f;   // two chains (even and odd k), as the FP32 pass
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) {
+                        if (k & 1) g1 = fmaf(-xi[j][k], rv[1 + k], g1);
+                        else g0 = fmaf(-xi[j][k], rv[1 + k], g0);
+                    }
+                    v = fmaf(-(g0 + g1), B.invL, th2);
                 }
-                const float v = fmaf(-(g0 + g1), B.invL, th2);
-                const float A = B.c1 * a1[j] + B.c2 * a2[j] + (ur - ub[j]);
-                const float w = v > 0.0f ? A : 0.0f;
+                const T A = B.c1 * a1[j] + B.c2 * a2[j] + (T)(ur - ub[j]);
+                const T w = v > (T)0 ? A : (T)0;
                 if (PASS == 1) {
-                    const float gb = -w * B.invL;
+                    const T gb = -w * B.invL;
                     racc[0] += gb;
 #pragma unroll
-                    for (int k = 0; k < NP; ++k) racc[1 + k] = fmaf(gb, xi[j][k], racc[1 + k]);
+                    for (int k = 0; k < NP; ++k) racc[1 + k] = fma(gb, xi[j][k], racc[1 + k]);
                     cacc[j][0] += gb;
 #pragma unroll
-                    for (int k = 0; k < NP; ++k) cacc[j][1 + k] = fmaf(gb, rv[1 + k], cacc[j][1 + k]);
+                    for (int k = 0; k < NP; ++k) cacc[j][1 + k] = fma(gb, rv[1 + k], cacc[j][1 + k]);
                 } else {
-                    float t = ybr + cb[j];
+                    T t = ybr + cb[j];
 #pragma unroll
-                    for (int k = 0; k < NP; ++k) t = fmaf(-xb[j][k], rv[1 + k], t);
+                    for (int k = 0; k < NP; ++k) t = fma(-xb[j][k], rv[1 + k], t);
                     outv[j] = w + t;
 #pragma unroll
-                    for (int k = 0; k < NP; ++k) racc[1 + k] = fmaf(th2, xb[j][k], racc[1 + k]);
+                    for (int k = 0; k < NP; ++k) racc[1 + k] = fma(th2, xb[j][k], racc[1 + k]);
                     cacc[j][0] += th2;
                 }
             }
-            if (PASS == 2 && vec_ok)
-                *reinterpret_cast<float4 *>(B.outb + r * ld + col0) = make_float4(outv[0], outv[1], outv[2], outv[3]);
+            if (PASS == 2 && vec_ok) Vec4Of<T>::store(B.outb + r * ld + col0, outv);
 #pragma unroll
             for (int k = 0; k < K1; ++k) {
-                const float t = warp_sum(racc[k]);
-                if (lane == 0 && (PASS == 1 || k > 0) && t != 0.0f) atomicAdd(B.acc_row + r * K1 + k, (double)t);
+                const T t = warp_sum(racc[k]);
+                if (lane == 0 && (PASS == 1 || k > 0) && t != (T)0) atomicAdd(B.acc_row + r * K1 + k, (double)t);
             }
         }
-        // column sums: reduce the 8 warps in shared memory, one atomic per column and term
+        const int kmax = PASS == 1 ? K1 : 1;
+        if constexpr (F64) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+            for (int j = 0; j < 4; ++j) {
+                const long long c = col0 + j;
 #pragma unroll
-            for (int k = 0; k < K1; ++k) red[warp][k][lane * 4 + j] = cacc[j][k];
-        __syncthreads();
-        for (int e = threadIdx.x; e < K1 * kBCols; e += 256) {
-            const int k = e / kBCols, cl = e % kBCols;
-            float a = 0.0f;
+                for (int k = 0; k < K1; ++k)
+                    if (c < N && k < kmax && cacc[j][k] != 0.0) atomicAdd(B.acc_col + c * K1 + k, cacc[j][k]);
+            }
+        } else {
+            // column sums: reduce the 8 warps in shared memory, one atomic per column and term
 #pragma unroll
-            for (int w = 0; w < 8; ++w) a += red[w][k][cl];
-            const long long c = stripe * kBCols + cl;
-            const int kmax = PASS == 1 ? K1 : 1;
-            if (c < N && k < kmax && a != 0.0f) atomicAdd(B.acc_col + c * K1 + k, (double)a);
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int k = 0; k < K1; ++k) red[warp][k][lane * 4 + j] = cacc[j][k];
+            __syncthreads();
+            for (int e = threadIdx.x; e < K1 * kBCols; e += 256) {
+                const int k = e / kBCols, cl = e % kBCols;
+                float a = 0.0f;
+#pragma unroll
+                for (int w = 0; w < 8; ++w) a += red[w][k][cl];
+                const long long c = stripe * kBCols + cl;
+                if (c < N && k < kmax && a != 0.0f) atomicAdd(B.acc_col + c * K1 + k, (double)a);
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
 // Fold of the reverse step (FP64, one thread per point).
-template <int NP, int PASS>
+template <typename T, int NP, int PASS>
 __global__ void __launch_bounds__(256)
-k_adj_fold(const BwdParams B)
+k_adj_fold(const BwdParamsT<T> B)
 {
     constexpr int K1 = NP + 1;
     const long long N = B.N;
@@ -193,7 +234,7 @@ k_adj_fold(const BwdParams B)
             double d = 0.0;
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
-                float xf = 0.0f;
+                T xf = (T)0;
                 if (k < n) {
                     const double xk = B.X64[l * n + k];
                     const double xib = Cc * xk - B.acc_col[l * K1 + 1 + k];   // A_2^T gbar
@@ -201,12 +242,12 @@ k_adj_fold(const BwdParams B)
                     B.X_acc[l * n + k] += Cc * (double)B.xi2[l * NP + k] - B.acc_row[l * K1 + 1 + k];
                     const double xg = xib * B.inv_gamma;
                     d += xg * xk;
-                    xf = (float)xg;
+                    xf = (T)xg;
                 }
                 B.xib_out[l * NP + k] = xf;
             }
-            B.yb2_out[l] = (float)yb2;
-            B.ccolb_out[l] = (float)(d - yb2);
+            B.yb2_out[l] = (T)yb2;
+            B.ccolb_out[l] = (T)(d - yb2);
         } else {
             const double Cth = B.acc_col[l * K1];
 #pragma unroll
@@ -225,12 +266,12 @@ struct BwdKernels {
     const void *pass1, *pass2, *fold1, *fold2;
 };
 
-// reverse mode is compiled for n <= 10 (padded widths 2, 4, 5, 8, 10)
-template <int NP> BwdKernels make_bwd()
+// reverse mode is compiled for n <= 10 (padded widths 2, 4, 5, 8, 10), FP32 or FP64 multipliers
+template <typename TS, int NP> BwdKernels make_bwd()
 {
-    if constexpr (NP <= 10)
-        return BwdKernels{(const void *)k_adj_pass<NP, 1>, (const void *)k_adj_pass<NP, 2>,
-                          (const void *)k_adj_fold<NP, 1>, (const void *)k_adj_fold<NP, 2>};
+    if constexpr (NP <= 10 && (std::is_same<TS, float>::value || std::is_same<TS, double>::value))
+        return BwdKernels{(const void *)k_adj_pass<TS, NP, 1>, (const void *)k_adj_pass<TS, NP, 2>,
+                          (const void *)k_adj_fold<TS, NP, 1>, (const void *)k_adj_fold<TS, NP, 2>};
     else
         return BwdKernels{nullptr, nullptr, nullptr, nullptr};
 }

@@ -334,7 +334,7 @@ template <typename TS, int NP> KernelSet make_set()
     }
     k.smem = pair_smem_bytes<TS, NP>();
     k.NP = NP;
-    k.bwd = make_bwd<NP>();
+    k.bwd = make_bwd<TS, NP>();
     return k;
 }
 

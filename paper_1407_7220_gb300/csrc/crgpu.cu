@@ -23,6 +23,19 @@
 #include "crgpu.h"
 
 namespace crk {
+// Widening copy of a stored multiplier array to FP32 (exact: every BF16 value and every FP16
+// value times its power-of-two scale is an FP32 number).
+__global__ void k_widen_bf16(const __nv_bfloat16 *in, float *out, size_t count)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = __bfloat162float(in[i]);
+}
+__global__ void k_widen_f16(const __half *in, float *out, size_t count, float inv_scale)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = __half2float(in[i]) * inv_scale;
+}
+
 __global__ void k_bwd_finish(long long N, int n, const float *ubar, const double *ybar_acc, const double *X_acc,
                              float *dybar, float *dX)
 {
@@ -544,7 +557,7 @@ cr_status init_state(cr_ctx *h)
 // ---- checkpoints of the iteration state (differentiation) ------------------
 cr_status ckpt_save(cr_ctx *h, cr_ctx::Checkpoint &c)
 {
-    const size_t th = (size_t)h->N * h->ld * sizeof(float);
+    const size_t th = (size_t)h->N * h->ld * theta_elem_size(h->opt.theta_dtype);
     const long long N = h->N;
     auto al = [&](void **p, size_t bytes) {
         if (cudaMalloc(p, bytes) != cudaSuccess) return false;
@@ -589,7 +602,7 @@ cr_status ckpt_save(cr_ctx *h, cr_ctx::Checkpoint &c)
 
 cr_status ckpt_restore(cr_ctx *h, const cr_ctx::Checkpoint &c)
 {
-    const size_t th = (size_t)h->N * h->ld * sizeof(float);
+    const size_t th = (size_t)h->N * h->ld * theta_elem_size(h->opt.theta_dtype);
     for (int b = 0; b < 2; ++b) {
         CR_CUDA(h, cudaMemcpyAsync(h->P.theta[b], c.th[b], th, cudaMemcpyDeviceToDevice, h->stream));
         CR_CUDA(h, cudaMemcpyAsync(h->P.v[b], c.v[b], sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->stream));
@@ -638,8 +651,8 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     const bool f64 = o.theta_dtype == CR_THETA_F64;
     if (f64 && n > crk::kMaxNF64)
         return fail(h, CR_EINVAL, "FP64 multipliers are compiled for n <= %d (n = %d)", crk::kMaxNF64, n);
-    if (f64 && (o.pair_engine == CR_PAIR_TENSOR_CORES || o.record_every > 0 || np_override > 0))
-        return fail(h, CR_EINVAL, "FP64 multipliers: CUDA-core pass only, no record_every, not in a batch");
+    if (f64 && (o.pair_engine == CR_PAIR_TENSOR_CORES || np_override > 0))
+        return fail(h, CR_EINVAL, "FP64 multipliers: CUDA-core pass only, not in a batch");
     const bool ball = o.B_theta > 0.0 && std::isfinite(o.B_theta);
     if (ball && (o.theta_dtype == CR_THETA_BF16 || o.theta_dtype == CR_THETA_F16 || o.pair_engine == CR_PAIR_TENSOR_CORES ||
                  o.driver == CR_DRIVER_PERSISTENT || o.record_every > 0 || np_override > 0 || aopt))
@@ -780,8 +793,8 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     P.bar_timeout_ns = (unsigned long long)(o.barrier_timeout_ms > 0 ? o.barrier_timeout_ms : 4000) * 1000000ull;
     P.bar_extra = o.test_barrier_extra > 0 ? o.test_barrier_extra : 0;
     h->record_every = o.record_every > 0 ? o.record_every : 0;
-    if (h->record_every > 0 && (o.theta_dtype != CR_THETA_F32 || !h->ks.bwd.pass1))
-        return fail(h, CR_EINVAL, "record_every needs FP32 theta and n <= 10");
+    if (h->record_every > 0 && ((o.theta_dtype != CR_THETA_F32 && o.theta_dtype != CR_THETA_F64) || !h->ks.bwd.pass1))
+        return fail(h, CR_EINVAL, "record_every needs FP32 or FP64 theta and n <= 10");
 
     const size_t es = theta_elem_size(o.theta_dtype);
     for (int b = 0; b < (h->alcc ? 1 : 2); ++b) {   // ALCC keeps one multiplier array
@@ -1127,6 +1140,81 @@ cr_status cr_create_device(const float *dX, const float *dybar, int64_t N, int32
     return finish_create(create_impl(Xv, yv, N, n, opt, out), out);
 }
 
+cr_status cr_promote(cr_handle h, int32_t theta_dtype)
+{
+    CR_TRY(papg_only(h));
+    const int from = h->opt.theta_dtype;
+    if (theta_dtype != CR_THETA_F32 || (from != CR_THETA_BF16 && from != CR_THETA_F16))
+        return fail(h, CR_EINVAL, "cr_promote: from BF16 or FP16 multipliers to FP32 only (dtype %d -> %d)", from,
+                    theta_dtype);
+    Params &P = h->P;
+    const long long N = h->N;
+    const size_t count = (size_t)N * h->ld;
+    KernelSet ks = kernels_for(CR_THETA_F32, h->NP);
+    if (!ks.phase) return fail(h, CR_EINVAL, "cr_promote: no FP32 kernel for n = %d", h->n);
+    // the engine: the tensor-core pass stays if the options allow it at FP32, else the CUDA cores
+    // (a CUDA-core handle never moves to the tensor cores: their operands are written by foldB)
+    const int newtc = (P.tc && (h->opt.pair_engine == CR_PAIR_TENSOR_CORES || h->NP >= 16)) ? 1 : 0;
+    void *nt[2] = {nullptr, nullptr};
+    for (int b = 0; b < 2; ++b) {
+        CR_TRY(dev_alloc(h, (float **)&nt[b], count));
+        const int grid = 4 * h->num_sms;
+        if (from == CR_THETA_BF16)
+            crk::k_widen_bf16<<<grid, 256, 0, h->stream>>>((const __nv_bfloat16 *)P.theta[b], (float *)nt[b], count);
+        else
+            crk::k_widen_f16<<<grid, 256, 0, h->stream>>>((const __half *)P.theta[b], (float *)nt[b], count,
+                                                           P.st_inv_scale);
+        CR_CUDA(h, cudaGetLastError());
+    }
+    CR_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (int b = 0; b < 2; ++b) {
+        auto it = std::find(h->allocs.begin(), h->allocs.end(), P.theta[b]);
+        if (it != h->allocs.end()) h->allocs.erase(it);
+        cudaFree(P.theta[b]);
+        P.theta[b] = nt[b];
+    }
+    auto encode = tensor_map_encoder();
+    if (!encode) return fail(h, CR_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    for (int b = 0; b < 2; ++b) {
+        cuuint64_t gdim[2] = {(cuuint64_t)N, (cuuint64_t)N};
+        cuuint64_t gstride[1] = {(cuuint64_t)h->ld * 4};
+        cuuint32_t box[2] = {(cuuint32_t)crk::kW, (cuuint32_t)crk::kRS}, box32[2] = {(cuuint32_t)crk::kW, 32u};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = encode(&P.tmap[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, P.theta[b], gdim, gstride, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS)
+            r = encode(&P.tmap32[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, P.theta[b], gdim, gstride, box32, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(h, CR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
+    if (newtc != P.tc) {
+        // the partial-sum layouts of the two engines differ: rowpart is 4S (tensor cores) or 2S wide,
+        // colpart has 1 or kWR row groups; the next pair pass writes them before the fold reads them
+        const long long S = P.S;
+        P.tc = newtc;
+        P.Q = (int)(((P.tc ? 4 : 2) * S + 3) / 4 * 4);
+        P.cgroups = P.tc ? 1 : crk::kWR;
+        CR_TRY(dev_alloc(h, &P.rowpart, (size_t)P.Q * N));
+        CR_TRY(dev_alloc(h, &P.colpart, (size_t)P.G * P.slots * P.cgroups * (h->NP + 1) * crk::kW));
+        CR_CUDA(h, cudaMemsetAsync(P.rowpart, 0, sizeof(float) * (size_t)P.Q * N, h->stream));
+    }
+    h->ks = ks;
+    CR_CUDA(h, cudaFuncSetAttribute(ks.persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks.smem));
+    CR_CUDA(h, cudaFuncSetAttribute(ks.phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks.smem));
+    CR_CUDA(h, cudaFuncSetAttribute(ks.pair_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks.smem));
+    int per_sm = 0, coop = 0;
+    CR_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks.persistent, crk::kThreads, ks.smem));
+    CR_CUDA(h, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
+    h->persistent_ok = coop && per_sm > 0 && P.G <= per_sm * h->num_sms && !P.tc && !P.ball;
+    P.st_scale = 1.0f;
+    P.st_inv_scale = 1.0f;
+    h->opt.theta_dtype = CR_THETA_F32;
+    CR_CUDA(h, cudaStreamSynchronize(h->stream));
+    return CR_OK;
+}
+
 cr_status cr_reset(cr_handle h)
 {
     if (!h) return CR_EINVAL;
@@ -1311,16 +1399,18 @@ cr_status cr_profile(cr_handle h, int32_t kind, double *ms, int64_t *launches)
     return CR_OK;
 }
 
-cr_status cr_backward(cr_handle h, const float *dL_dyhat, float *dL_dybar, float *dL_dX)
+}  // extern "C"
+
+// Reverse mode over FP32 (T = float) or FP64 (T = double) multipliers: the saved forward data of
+// every recomputed iteration (multipliers, row records, column data) have the storage type.
+template <typename T>
+static cr_status backward_impl(cr_handle h, const float *dL_dyhat, float *dL_dybar, float *dL_dX)
 {
-    CR_TRY(papg_only(h));
-    if (!dL_dyhat || !dL_dybar || !dL_dX) return fail(h, CR_EINVAL, "NULL buffer");
-    if (h->record_every <= 0 || h->ckpt.empty() || h->opt.theta_dtype != CR_THETA_F32)
-        return fail(h, CR_ESTATE, "cr_backward needs iterations run with record_every > 0 (FP32 theta)");
+    constexpr bool F64 = std::is_same<T, double>::value;
     const long long K = h->iters, k = h->record_every, N = h->N, ld = h->ld;
     const int n = h->n, NP = h->NP, K1 = NP + 1, REC = rec_floats(NP);
     if ((long long)h->ckpt.size() < (K + k - 1) / k) return fail(h, CR_ESTATE, "missing checkpoints");
-    const size_t thb = (size_t)N * ld * sizeof(float);
+    const size_t thb = (size_t)N * ld * sizeof(T);
     // workspace
     auto al = [&](void **p, size_t bytes) {
         if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
@@ -1329,22 +1419,22 @@ cr_status cr_backward(cr_handle h, const float *dL_dyhat, float *dL_dybar, float
     };
     for (void *p : h->bwd_allocs) cudaFree(p);
     h->bwd_allocs.clear();
-    std::vector<float *> segTh(k + 1), segRec(k), segCcol(k), segXi(k);
+    std::vector<T *> segTh(k + 1), segRec(k), segCcol(k), segXi(k);
     std::vector<double *> segV(k + 2), segMu(k + 2);
-    float *bb[2], *yb2, *ccolb, *xib;
+    T *bb[2], *yb2, *ccolb, *xib;
     double *mub[2], *acc_row, *acc_col, *ybar_acc, *X_acc;
     bool ok = true;
     for (long long i = 0; i <= k && ok; ++i) ok = al((void **)&segTh[i], thb);
     for (long long i = 0; i < k && ok; ++i)
-        ok = al((void **)&segRec[i], sizeof(float) * N * REC) && al((void **)&segCcol[i], sizeof(float) * N) &&
-             al((void **)&segXi[i], sizeof(float) * N * NP);
+        ok = al((void **)&segRec[i], sizeof(T) * N * REC) && al((void **)&segCcol[i], sizeof(T) * N) &&
+             al((void **)&segXi[i], sizeof(T) * N * NP);
     for (long long i = 0; i < k + 2 && ok; ++i)
         ok = al((void **)&segV[i], sizeof(double) * N) && al((void **)&segMu[i], sizeof(double) * N);
     ok = ok && al((void **)&bb[0], thb) && al((void **)&bb[1], thb) && al((void **)&mub[0], sizeof(double) * N) &&
          al((void **)&mub[1], sizeof(double) * N) && al((void **)&acc_row, sizeof(double) * N * K1) &&
          al((void **)&acc_col, sizeof(double) * N * K1) && al((void **)&ybar_acc, sizeof(double) * N) &&
-         al((void **)&X_acc, sizeof(double) * N * n) && al((void **)&yb2, sizeof(float) * N) &&
-         al((void **)&ccolb, sizeof(float) * N) && al((void **)&xib, sizeof(float) * N * NP);
+         al((void **)&X_acc, sizeof(double) * N * n) && al((void **)&yb2, sizeof(T) * N) &&
+         al((void **)&ccolb, sizeof(T) * N) && al((void **)&xib, sizeof(T) * N * NP);
     if (!ok) {
         (void)cudaGetLastError();
         return fail(h, CR_ENOMEM, "reverse-mode workspace allocation failed");
@@ -1385,9 +1475,13 @@ cr_status cr_backward(cr_handle h, const float *dL_dyhat, float *dL_dybar, float
             const long long q = ell - c;
             if (ell < e)
                 CR_CUDA(h, cudaMemcpyAsync(segTh[q + 1], h->P.theta[ell & 1], thb, cudaMemcpyDeviceToDevice, h->stream));
-            CR_CUDA(h, cudaMemcpyAsync(segRec[q - 1], h->P.rowrec, sizeof(float) * N * REC, cudaMemcpyDeviceToDevice, h->stream));
-            CR_CUDA(h, cudaMemcpyAsync(segCcol[q - 1], h->P.ccol2, sizeof(float) * N, cudaMemcpyDeviceToDevice, h->stream));
-            CR_CUDA(h, cudaMemcpyAsync(segXi[q - 1], h->P.xi2, sizeof(float) * N * NP, cudaMemcpyDeviceToDevice, h->stream));
+            // the row and column data this iteration's pair pass read (FP64 copies for FP64 multipliers)
+            const void *rec = F64 ? (const void *)h->P.rec64 : (const void *)h->P.rowrec;
+            const void *ccol = F64 ? (const void *)h->P.ccol2_64 : (const void *)h->P.ccol2;
+            const void *xi2 = F64 ? (const void *)h->P.xi2_64 : (const void *)h->P.xi2;
+            CR_CUDA(h, cudaMemcpyAsync(segRec[q - 1], rec, sizeof(T) * N * REC, cudaMemcpyDeviceToDevice, h->stream));
+            CR_CUDA(h, cudaMemcpyAsync(segCcol[q - 1], ccol, sizeof(T) * N, cudaMemcpyDeviceToDevice, h->stream));
+            CR_CUDA(h, cudaMemcpyAsync(segXi[q - 1], xi2, sizeof(T) * N * NP, cudaMemcpyDeviceToDevice, h->stream));
             CR_CUDA(h, cudaMemcpyAsync(segV[q + 1], h->P.v[ell & 1], sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
             CR_CUDA(h, cudaMemcpyAsync(segMu[q + 1], h->P.mu[ell & 1], sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
             DevState st;
@@ -1397,22 +1491,22 @@ cr_status cr_backward(cr_handle h, const float *dL_dyhat, float *dL_dybar, float
         // reverse the segment
         for (long long ell = e; ell > c; --ell) {
             const long long q = ell - c;
-            crk::BwdParams B{};
+            crk::BwdParamsT<T> B{};
             B.N = N;
             B.ld = ld;
             B.n = n;
             B.S128 = (int)S128;
             B.REC = REC;
-            B.invL = h->P.invL;
+            B.invL = F64 ? (T)h->P.invL_d : (T)h->P.invL;
             B.invL_d = h->P.invL_d;
             B.inv_gamma = h->P.inv_gamma;
             B.shift = h->P.shift;
-            B.beta = (float)beta[ell];
+            B.beta = (T)beta[ell];
             B.beta_d = beta[ell];
             B.c1_d = ell + 1 <= K ? 1.0 + beta[ell + 1] : 0.0;
             B.c2_d = ell + 2 <= K ? -beta[ell + 2] : 0.0;
-            B.c1 = (float)B.c1_d;
-            B.c2 = (float)B.c2_d;
+            B.c1 = (T)B.c1_d;
+            B.c2 = (T)B.c2_d;
             B.thc = segTh[q];
             B.thp = segTh[q - 1];
             B.rowrec = segRec[q - 1];
@@ -1458,6 +1552,19 @@ cr_status cr_backward(cr_handle h, const float *dL_dyhat, float *dL_dybar, float
     CR_TRY(ckpt_restore(h, fin));
     CR_CUDA(h, cudaStreamSynchronize(h->stream));
     return status;
+}
+
+extern "C" {
+
+cr_status cr_backward(cr_handle h, const float *dL_dyhat, float *dL_dybar, float *dL_dX)
+{
+    CR_TRY(papg_only(h));
+    if (!dL_dyhat || !dL_dybar || !dL_dX) return fail(h, CR_EINVAL, "NULL buffer");
+    const int dt = h->opt.theta_dtype;
+    if (h->record_every <= 0 || h->ckpt.empty() || (dt != CR_THETA_F32 && dt != CR_THETA_F64))
+        return fail(h, CR_ESTATE, "cr_backward needs iterations run with record_every > 0 (FP32 or FP64 theta)");
+    return dt == CR_THETA_F64 ? backward_impl<double>(h, dL_dyhat, dL_dybar, dL_dX)
+                              : backward_impl<float>(h, dL_dyhat, dL_dybar, dL_dX);
 }
 
 cr_status cr_get_device_state(cr_handle h, const void **dtheta, int64_t *ld, const double **dX, const double **dy,

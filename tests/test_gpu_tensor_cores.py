@@ -165,3 +165,37 @@ def test_16bit_full_size_matches_fp32_path():
         err = _rel(res[dt], res["f32"])
         print(f"{dt} N=100000 {K} iterations: rel err vs FP32 {err:.2e}")
         assert err <= 1e-3
+
+
+# -------------------------------------------------------------------------
+# precision schedule: 16-bit multipliers first, then FP32 (cr_promote)
+# -------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype,n", [("bf16", 10), ("f16", 10), ("bf16", 20)])
+def test_promotion_widens_exactly_and_keeps_iterating(crg, dtype, n):
+    from tests import devarray
+    X, yb, _ = datagen.make("maxaff" if n == 10 else "lse", N=700, n=n)
+    g = crg.Solver(X, yb, gamma=0.1, theta_dtype=dtype, stochastic_round=1, restart=0)
+    g.iterate(15)
+    before = devarray.theta_f64(g.device_state(), 700, dtype, fp16_exponent=g.options.fp16_exponent)
+    y0, _ = g.solution()
+    g.promote("f32")
+    after = devarray.theta_f64(g.device_state(), 700, "f32")
+    assert np.array_equal(before, after)                    # the widening is exact
+    assert np.array_equal(g.solution()[0], y0)              # the iterate itself is unchanged
+    assert g.info()["engine"] == ("tensor_cores" if n >= 16 else "cuda_cores")
+    g.iterate(15)
+    assert g.info()["iters"] == 30 and np.isfinite(g.solution()[0]).all()
+    with pytest.raises(crg.CrError):
+        g.promote("f32")                                    # already FP32
+
+
+def test_promoted_schedule_converges_to_the_exact_fit(crg):
+    import os
+    X, yb, _ = datagen.make("sq2", N=500)
+    ref = np.load(os.path.join(os.path.dirname(__file__), "golden", "sq2_N500_g0.1_exact.npz"))
+    g = crg.Solver(X, yb, gamma=0.1, theta_dtype="bf16", stochastic_round=1, restart=0, kkt_every=50)
+    g.solve(5e-2, 200_000)                                  # above the BF16 rounding floor
+    g.promote("f32")
+    conv, _ = g.solve(1e-4, 400_000)
+    assert conv and g.kkt_residual()["kkt"] <= 1e-4
+    assert _rel(g.solution()[0], ref["y_hat"]) <= 3e-4
