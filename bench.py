@@ -165,7 +165,7 @@ def run_reference(args):
 # N(N-1) pair updates (the per-stage vectors make the excess over 3 b proportional to the
 # pairs); keyed by (engine, theta dtype, padded n).  A kernel change invalidates an entry.
 TRAFFIC_BYTES_PER_PAIR = {
-    ("cuda_cores", "f32", 10): (519.218859e6 + 222.125824e6) / (8000 * 7999),
+    ("cuda_cores", "f32", 10): (517.62048e6 + 219.80288e6) / (8000 * 7999),
     ("tensor_cores", "bf16", 20): (742.873728e6 + 278.586368e6) / (12000 * 11999),
 }
 
