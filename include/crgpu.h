@@ -359,6 +359,28 @@ cr_status cr_batch_stats(cr_batch_handle b, int32_t *graph_live, int64_t *graph_
 void cr_batch_destroy(cr_batch_handle b);
 const char *cr_batch_last_error(cr_batch_handle b);
 
+/* ---- P-APG with K blocks (Sec. II-A, Fig. 2) -------------------------------------------------
+ * The points are partitioned into blocks (block_of[l] = block of point l, any ids in [0, N)).
+ * The pairwise constraints between blocks and the y >= 0 rows of C (Eq. (eq:C)) are dualized and
+ * P-APG (plain momentum) runs on their dual; Step 1 separates into one problem per block,
+ *     min 1/2 ||y_i - a_i||^2 + gamma/2 ||xi_i - b_i||^2  s.t. the pairwise constraints inside block i,
+ * with a = ybar + s + A_1^T theta^(2) + mu^(2) and b = A_2^T theta^(2) / gamma (dualized rows only).
+ * The library solves all block problems together by an inner P-APG on their duals (FP64, the
+ * pairs inside the blocks), warm-started from the previous call's inner multipliers with the
+ * momentum restarted (as from Iteration 0), for inner_iters (even, >= 2) iterations per outer
+ * iteration: an inexact Step 1, as the paper's ALCC or interior-point block solves.  K = N (every
+ * point its own block) is the P-APG of cr_create; K = 1 makes Step 1 the whole problem.
+ * Multipliers and arithmetic are FP64 (n <= 10); device memory: 4 N x ceil16(N) FP64 arrays
+ * (outer and inner iterates).  The handle answers cr_get_info and cr_destroy; cr_reset and the
+ * P-APG calls of cr_create return CR_ESTATE on it. */
+cr_status cr_blocks_create(const double *X, const double *ybar, int64_t N, int32_t n, const int32_t *block_of,
+                           const cr_options *opt, int32_t inner_iters, cr_handle *out);
+/* k outer iterations, then Step 1 once more at the dual iterate theta^(1)_l (the primal point of
+ * Theorem 1, read by cr_blocks_solution).  Blocks. */
+cr_status cr_blocks_iterate(cr_handle h, int64_t k);
+/* The primal point (yhat with the shift removed, xi), host buffers (either may be NULL).  Blocks. */
+cr_status cr_blocks_solution(cr_handle h, double *yhat, double *xi);
+
 /* Static description of a status code. */
 const char *cr_status_str(cr_status s);
 

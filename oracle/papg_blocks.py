@@ -13,7 +13,11 @@ Step 1 separates into one problem per block,
 
 the projection of the closed-form point (h + v, w/gamma) onto the block's constraint set in the
 norm weighted by diag(1, gamma).  The oracle solves it exactly through its dual, a nonnegative
-least-squares problem (scipy's active-set Lawson-Hanson NNLS).  Step 2 is the projected step on
+least-squares problem (scipy's active-set Lawson-Hanson NNLS), or -- with ``inner_iters`` set --
+inexactly, as the paper's block solvers do: ``inner_iters`` iterations of P-APG (Fig. 2) on each
+block problem's dual (every pair inside the block dualized: the closed form y = a + A_1b^T lam,
+xi = b + A_2b^T lam / gamma, the clamp of lam - (constraint values) / L_in, the t-sequence from
+t = 1), started at the previous call's multipliers lam.  Step 2 is the projected step on
 the dualized rows, Steps 3-4 the momentum of Fig. 2.  With singleton blocks (K = N) this is the
 P-APG of ``oracle.py``; with one block (K = 1) Step 1 is the whole problem.
 
@@ -43,7 +47,7 @@ def pair_rows(X, pairs):
 class BlockPapg:
     """P-APG (Fig. 2) on the dual of the constraints between blocks and of the y >= 0 rows."""
 
-    def __init__(self, X, ybar, blocks, gamma: float, L: float, s: float):
+    def __init__(self, X, ybar, blocks, gamma: float, L: float, s: float, inner_iters=None, L_inner=None):
         self.X = np.ascontiguousarray(X, dtype=np.float64)
         N, n = self.X.shape
         self.N, self.n, self.gamma, self.L = N, n, float(gamma), float(L)
@@ -62,6 +66,9 @@ class BlockPapg:
             loc = [(i, j) for i in range(len(b)) for j in range(len(b)) if i != j]
             A1b, A2b = pair_rows(self.X[b], loc)
             self.intra.append((A1b, A2b))
+        self.inner_iters = None if inner_iters is None else int(inner_iters)
+        self.L_inner = float(L if L_inner is None else L_inner)
+        self.lam = [np.zeros(A1b.shape[0]) for A1b, _ in self.intra]   # inner multipliers (warm start)
         m = len(self.cross)
         # Iteration 0 of Fig. 2: theta^(1)_0 = theta^(2)_1 = 0, t_1 = 1
         self.th1p = np.zeros(m)         # theta^(1)_{l-1}
@@ -70,7 +77,10 @@ class BlockPapg:
         self.mu2 = np.zeros(N)
         self.t = 1.0
         self.iters = 0
-        self.y, self.xi = self.step1(self.th2, self.mu2)
+        if self.inner_iters is None:
+            self.y, self.xi = self.step1(self.th2, self.mu2)
+        else:   # the inexact Step 1 moves its warm start: it runs only inside iterate()
+            self.y, self.xi = self.h.copy(), np.zeros((N, n))
 
     def step1(self, theta, mu):
         """Step 1: eta(theta, mu), block by block (exact NNLS on each block's dual)."""
@@ -81,10 +91,13 @@ class BlockPapg:
         xi0 = w / g
         y = np.empty(N)
         xi = np.empty((N, n))
-        for b, (A1b, A2b) in zip(self.blocks, self.intra):
+        for i, (b, (A1b, A2b)) in enumerate(zip(self.blocks, self.intra)):
             yb0, xb0 = y0[b], xi0[b].ravel()
             if A1b.shape[0] == 0:        # a single point: no constraint inside
                 y[b], xi[b] = yb0, xb0.reshape(-1, n)
+                continue
+            if self.inner_iters is not None:
+                y[b], xi[b] = self._inner_papg(i, A1b, A2b, yb0, xb0)
                 continue
             # min_{lambda >= 0} 1/2 || [A1b^T ; A2b^T / sqrt(g)] lambda + [yb0 ; sqrt(g) xb0] ||^2
             M = np.vstack([A1b.T, A2b.T / np.sqrt(g)])
@@ -93,6 +106,25 @@ class BlockPapg:
             y[b] = yb0 + A1b.T @ lam
             xi[b] = (xb0 + (A2b.T @ lam) / g).reshape(-1, n)
         return y, xi
+
+    def _inner_papg(self, i, A1b, A2b, a, b):
+        """inner_iters iterations of P-APG (Fig. 2) on block i's dual from its last multipliers."""
+        g, Lin = self.gamma, self.L_inner
+        lam1 = self.lam[i]            # lambda^(1) of the last call
+        lam2 = lam1.copy()            # Iteration 0 at lam1: lambda^(2)_1 = lambda^(1)_0
+        lamp = lam1
+        t = 1.0
+        for _ in range(self.inner_iters):
+            y = a + A1b.T @ lam2                                   # Step 1 (closed form)
+            xi = b + (A2b.T @ lam2) / g
+            gc = A1b @ y + A2b @ xi                                # the constraint values
+            l1 = np.maximum(0.0, lam2 - gc / Lin)                  # Step 2
+            tn = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))         # Step 3
+            beta = (t - 1.0) / tn
+            lam2 = l1 + beta * (l1 - lamp)                         # Step 4
+            lamp, t = l1, tn
+        self.lam[i] = lamp
+        return a + A1b.T @ lamp, (b + (A2b.T @ lamp) / g).reshape(-1, self.n)
 
     def iterate(self, k: int):
         N, n = self.N, self.n

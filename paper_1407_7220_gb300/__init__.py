@@ -23,7 +23,7 @@ import threading
 import numpy as np
 
 __all__ = [
-    "CrError", "Options", "Solver", "AlccOptions", "AlccSolver", "problem_constants", "lib", "library_path",
+    "CrError", "Options", "Solver", "AlccOptions", "AlccSolver", "BlockSolver", "problem_constants", "lib", "library_path",
     "exported_symbols",
     "THETA_F32", "THETA_BF16", "THETA_F16", "THETA_F64", "DRIVER_AUTO", "DRIVER_PERSISTENT", "DRIVER_PHASES",
     "PAIR_AUTO", "PAIR_CUDA_CORES", "PAIR_TENSOR_CORES",
@@ -49,7 +49,8 @@ exported_symbols = (
     "cr_batch_create", "cr_batch_solve", "cr_batch_iterate", "cr_batch_reset", "cr_batch_instance",
     "cr_batch_info", "cr_batch_destroy", "cr_batch_last_error", "cr_backward", "cr_get_engine",
     "cr_alcc_options_default", "cr_alcc_create", "cr_alcc_iterate", "cr_alcc_solve", "cr_alcc_metrics",
-    "cr_alcc_info", "cr_problem_constants", "cr_batch_stats", "cr_promote",
+    "cr_alcc_info", "cr_problem_constants", "cr_batch_stats", "cr_promote", "cr_blocks_create",
+    "cr_blocks_iterate", "cr_blocks_solution",
 )
 PROFILE_PAIR, PROFILE_FOLD, PROFILE_KKT, PROFILE_PERSISTENT = 0, 1, 2, 3
 
@@ -108,6 +109,12 @@ def lib():
             L.cr_create_device.argtypes = [fp, fp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Options),
                                            ctypes.POINTER(H)]
             L.cr_reset.argtypes = [H]
+            L.cr_blocks_create.argtypes = [dp, dp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(Options), ctypes.c_int32, ctypes.POINTER(H)]
+            L.cr_blocks_iterate.argtypes = [H, ctypes.c_int64]
+            L.cr_blocks_solution.argtypes = [H, dp, dp]
+            for name in ("cr_blocks_create", "cr_blocks_iterate", "cr_blocks_solution"):
+                getattr(L, name).restype = ctypes.c_int
             L.cr_promote.argtypes = [H, ctypes.c_int32]
             L.cr_promote.restype = ctypes.c_int
             L.cr_iterate.argtypes = [H, ctypes.c_int64]
@@ -380,6 +387,50 @@ class AlccSolver(Solver):
         mu = ctypes.c_double()
         self._check(lib().cr_alcc_info(self._h, ctypes.byref(o), ctypes.byref(it), ctypes.byref(mu), ctypes.byref(lm)))
         return {"outer": o.value, "inner_total": it.value, "mu": mu.value, "lmax_next": lm.value}
+
+
+class BlockSolver(Solver):
+    """P-APG with the points partitioned into blocks (Sec. II-A; ``cr_blocks_*``).
+
+    blocks: list of index arrays (a partition of range(N)) or an (N,) array of block ids.
+    inner_iters: inner P-APG iterations (even) per outer iteration, Step 1 of the block problems.
+    Keyword arguments set ``cr_options`` (``gamma``, ``L`` ...); FP64 multipliers throughout."""
+
+    def __init__(self, X, ybar, blocks, inner_iters: int = 100, **opts):
+        self._h = ctypes.c_void_p()
+        L = lib()
+        o = default_options(**opts)
+        self.options = o
+        Xa = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
+        ya = np.ascontiguousarray(np.asarray(ybar, dtype=np.float64))
+        N, n = Xa.shape
+        if isinstance(blocks, (list, tuple)):
+            ids = np.empty(N, dtype=np.int32)
+            for i, b in enumerate(blocks):
+                ids[np.asarray(b, dtype=np.int64)] = i
+        else:
+            ids = np.ascontiguousarray(np.asarray(blocks, dtype=np.int32))
+        self._ids = ids
+        st = L.cr_blocks_create(_dptr(Xa), _dptr(ya), N, n, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                ctypes.byref(o), int(inner_iters), ctypes.byref(self._h))
+        if st != CR_OK:
+            raise CrError(st, L.cr_last_error(None).decode())
+        self.N, self.n = int(N), int(n)
+
+    def iterate(self, k: int):
+        self._check(lib().cr_blocks_iterate(self._h, int(k)))
+
+    def solution(self):
+        y = np.empty(self.N)
+        xi = np.empty((self.N, self.n))
+        self._check(lib().cr_blocks_solution(self._h, _dptr(y), _dptr(xi)))
+        return y, xi
+
+    def info(self) -> dict:
+        it = ctypes.c_int64()
+        Lc, s = ctypes.c_double(), ctypes.c_double()
+        self._check(lib().cr_get_info(self._h, ctypes.byref(it), None, ctypes.byref(Lc), ctypes.byref(s)))
+        return {"iters": it.value, "L": Lc.value, "shift": s.value}
 
 
 class _Member(Solver):

@@ -8,6 +8,6 @@ KernelSet kernels_f16(int NP)
     if (NP == V) return make_set<__half, V>();
     CR_NP_LIST(CR_CASE)
 #undef CR_CASE
-    return KernelSet{nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, {nullptr, nullptr, nullptr, nullptr}};
+    return KernelSet{};
 }
 }  // namespace crk

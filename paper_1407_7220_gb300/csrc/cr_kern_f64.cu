@@ -8,6 +8,6 @@ KernelSet kernels_f64(int NP)
     if (NP == V) return make_set<double, V>();
     CR_NP_LIST_F64(CR_CASE)
 #undef CR_CASE
-    return KernelSet{nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, {nullptr, nullptr, nullptr, nullptr}};
+    return KernelSet{};
 }
 }  // namespace crk

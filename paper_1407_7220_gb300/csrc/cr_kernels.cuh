@@ -123,6 +123,13 @@ struct Params {
     // FP64 multipliers (theta_dtype F64): the pair pass runs in FP64 on FP64 copies of its
     // inputs and writes FP64 partials (same layouts as rowrec, ccol2, xi2, rowpart, colpart)
     int f64;
+    // P-APG with K blocks (Sec. II-A): block id of every point; pair mask of the FP64 pass
+    // (0 none, 1 pairs between blocks only, 2 pairs inside a block only); the inner problem's
+    // subgradient offset (xi = xi_off + A_2^T theta / gamma) and no y >= 0 rows
+    const int *blk;
+    int blkmode;
+    const double *xi_off;
+    int no_mu;
     // Q_2 with a finite ball ||lambda||_2 <= B_theta (Eq. (lambda_dual)): per-CTA partial sums
     // of squares of the clamped multipliers (pairs and y >= 0 rows)
     int ball;
@@ -642,9 +649,9 @@ __device__ __forceinline__ void foldB_row(const Params &P, int c, int p, long lo
     const int n = P.n;
     double v2 = b1 * __ldcg(P.v[c] + l) - beta * __ldcg(P.v[p] + l);
     double mu2 = b1 * __ldcg(P.mu[c] + l) - beta * __ldcg(P.mu[p] + l);
-    double y2 = __ldg(P.h + l) + v2 + mu2;
+    double y2 = __ldcg(P.h + l) + v2 + mu2;
     double mun = mu2 - y2 * P.invL_d;     // Step 2 on the y >= 0 rows of C
-    P.mu[p][l] = mun > 0.0 ? mun : 0.0;
+    P.mu[p][l] = (mun > 0.0 && !P.no_mu) ? mun : 0.0;
     double ys = y2 - P.shift;
     double d = 0.0;
 #pragma unroll
@@ -652,6 +659,7 @@ __device__ __forceinline__ void foldB_row(const Params &P, int c, int p, long lo
         float xf = 0.0f;
         if (k < n) {
             double xi = (b1 * __ldcg(P.w[c] + l * n + k) - beta * __ldcg(P.w[p] + l * n + k)) * P.inv_gamma;
+            if (P.xi_off) xi += __ldcg(P.xi_off + l * n + k);
             d += xi * __ldg(P.X64 + l * n + k);
             xf = (float)xi;
         }
@@ -666,7 +674,10 @@ __device__ __forceinline__ void foldB_row(const Params &P, int c, int p, long lo
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
             double xi = 0.0;
-            if (k < n) xi = (b1 * __ldcg(P.w[c] + l * n + k) - beta * __ldcg(P.w[p] + l * n + k)) * P.inv_gamma;
+            if (k < n) {
+                xi = (b1 * __ldcg(P.w[c] + l * n + k) - beta * __ldcg(P.w[p] + l * n + k)) * P.inv_gamma;
+                if (P.xi_off) xi += __ldcg(P.xi_off + l * n + k);
+            }
             P.xi2_64[l * NP + k] = xi;
         }
     }
@@ -1456,7 +1467,7 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red, long lo
         }
         const double v = R - Cc;               // (A_1^T theta)_l = row sum - column sum
         P.v[p][l] = v;
-        const double hl = __ldg(P.h + l), mu = __ldcg(P.mu[p] + l);
+        const double hl = __ldcg(P.h + l), mu = __ldcg(P.mu[p] + l);
         const double y = hl + v + mu;          // Step 1 closed form
         const double ys = y - P.shift;
         double d = 0.0, xin = 0.0;
@@ -1467,7 +1478,7 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red, long lo
                 const double xk = __ldg(P.X64 + l * n + k);
                 const double wk = Cc * xk - TX[k];   // (A_2^T theta)_l = Cc_l x_l - (theta^T X)_l
                 P.w[p][l * n + k] = wk;
-                const double xi = wk * P.inv_gamma;
+                const double xi = wk * P.inv_gamma + (P.xi_off ? __ldcg(P.xi_off + l * n + k) : 0.0);
                 P.xi1_64[l * n + k] = xi;
                 d += xi * xk;
                 xin += xi * xi;

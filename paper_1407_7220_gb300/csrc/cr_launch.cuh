@@ -4,6 +4,7 @@
 
 #include "cr_kernels.cuh"
 #include "cr_backward.cuh"
+#include "cr_blocks.cuh"
 #include "cr_pair_f64.cuh"
 #include "cr_pair_tc.cuh"
 
@@ -313,6 +314,7 @@ struct KernelSet {
     size_t smem;
     int NP;
     BwdKernels bwd;
+    const void *blocks_prepare, *blocks_records;   // K-block P-APG (FP64 multipliers only)
 };
 
 // dLoss/dybar = ubar + accumulated, dLoss/dX = accumulated (FP64 -> FP32 outputs)
@@ -328,9 +330,13 @@ template <typename TS, int NP> KernelSet make_set()
     if constexpr (std::is_same<TS, double>::value) {
         k.pair_tc = nullptr;   // FP64 multipliers: CUDA cores only, single instances only
         k.batch = nullptr;
+        k.blocks_prepare = (const void *)k_blocks_prepare<NP>;
+        k.blocks_records = (const void *)k_blocks_records<NP>;
     } else {
         k.pair_tc = (const void *)k_pair_tc<TS, NP>;
         k.batch = (const void *)k_batch<TS, NP>;
+        k.blocks_prepare = nullptr;
+        k.blocks_records = nullptr;
     }
     k.smem = pair_smem_bytes<TS, NP>();
     k.NP = NP;

@@ -40,10 +40,12 @@ template <int NP> __device__ void phase_pair_f64(const Params &P, long long ell,
         const long long col0 = s * kW + wc * 128 + lane * 4;   // this lane's 4 columns
         const bool vec_ok = col0 < ld;                          // ld is a multiple of 16
         double ccol[4], nxi[4][NP], csum[4], acc[4][NP];
+        int bcol[4] = {-1, -1, -1, -1};   // block ids of this lane's columns (K-block P-APG)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const long long cj = col0 + j;
             const bool v = cj < N;
+            if (P.blkmode && v) bcol[j] = __ldg(P.blk + cj);
             ccol[j] = v ? __ldcg(P.ccol2_64 + cj) : 0.0;
             csum[j] = 0.0;
 #pragma unroll
@@ -54,6 +56,7 @@ template <int NP> __device__ void phase_pair_f64(const Params &P, long long ell,
         }
         double *rp = P.rowpart64 + (s * 2 + wc);   // row r's partial at rp[r * Q]
         for (long long r = r0 + rg; r < r1; r += kWR) {
+            const int brow = P.blkmode ? __ldg(P.blk + r) : -2;
             const double *rec = P.rec64 + r * REC;
             const double yr = __ldcg(rec);
             double xr[NP];
@@ -79,6 +82,8 @@ template <int NP> __device__ void phase_pair_f64(const Params &P, long long ell,
                 const double v = fma(-g, invL, th2);
                 double nw = v > 0.0 ? v : 0.0;                         // projection on theta >= 0
                 if (cj >= N || cj == r) nw = 0.0;                      // padding columns, diagonal
+                // K blocks: the outer dual holds the pairs between blocks, the inner one those inside
+                if ((P.blkmode == 1 && bcol[j] == brow) || (P.blkmode == 2 && bcol[j] != brow)) nw = 0.0;
                 out[j] = nw;
                 rs += nw;
                 csum[j] += nw;

@@ -103,6 +103,13 @@ struct cr_ctx {
     bool a_have_metrics = false;
     double a_metrics[4] = {0, 0, 0, 0};
     std::vector<float> a_rec0, a_ccol0;   // column data of (y_0, xi_0) = (ybar, 0)
+    // P-APG with K blocks (cr_blocks_*): this handle holds the outer dual (pairs between blocks,
+    // y >= 0 rows); `inner` the pairs inside the blocks (Step 1 by inner P-APG)
+    bool blocks = false;
+    cr_ctx *inner = nullptr;
+    int inner_iters = 0;
+    int K = 0;
+    double *b_a = nullptr, *b_b = nullptr, *b_mu2 = nullptr;   // a, b of Step 1's block problems; mu^(2)
 };
 
 namespace {
@@ -159,7 +166,7 @@ KernelSet kernels_for(int dtype, int NP)
     case CR_THETA_BF16: return crk::kernels_bf16(NP);
     case CR_THETA_F16: return crk::kernels_f16(NP);
     case CR_THETA_F64: return crk::kernels_f64(NP);
-    default: return KernelSet{nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, {nullptr, nullptr, nullptr, nullptr}};
+    default: return KernelSet{};
     }
 }
 
@@ -1079,6 +1086,31 @@ cr_status papg_only(cr_ctx *h)
 {
     CR_TRY(usable(h));
     if (h->alcc) return fail(h, CR_ESTATE, "an ALCC handle: use the cr_alcc_* calls");
+    if (h->blocks) return fail(h, CR_ESTATE, "a K-block handle: use the cr_blocks_* calls");
+    return CR_OK;
+}
+
+// Step 1 of the K-block P-APG at the outer iterate ell: a, b from the outer aggregates (at
+// theta^(2)_ell, or at theta^(1)_ell itself), then inner_iters iterations of the inner P-APG.
+cr_status blocks_step1(cr_ctx *h, long long ell, int at_theta1)
+{
+    cr_ctx *in = h->inner;
+    const int grid = 4 * h->num_sms;
+    {
+        Params P = h->P;
+        double *a = h->b_a, *b = h->b_b, *m2 = h->b_mu2;
+        void *args[] = {&P, &a, &b, &m2, &ell, &at_theta1};
+        CR_CUDA(h, cudaLaunchKernel(h->ks.blocks_prepare, dim3(grid), dim3(256), args, 0, h->stream));
+    }
+    // The inner handle runs on the same stream.  Every call restarts the inner P-APG as from its
+    // Iteration 0 (t_1 = 1: no momentum in its first two iterations) at its current multipliers:
+    // its iterations are numbered 1..M again, and with M even the last multipliers and their
+    // aggregates sit in buffer 0, where iteration 1 reads its starting point.
+    const double one = 1.0;
+    CR_CUDA(h, cudaMemcpyAsync(&in->P.st->scal[0].t, &one, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    cr_status s = run_phases(in, 1, h->inner_iters, 0, -1.0);
+    if (s != CR_OK) return fail(h, s, "inner iterations: %s", in->err.c_str());
+    in->iters = h->inner_iters;
     return CR_OK;
 }
 
@@ -1218,6 +1250,7 @@ cr_status cr_promote(cr_handle h, int32_t theta_dtype)
 cr_status cr_reset(cr_handle h)
 {
     if (!h) return CR_EINVAL;
+    if (h->blocks) return fail(h, CR_ESTATE, "a K-block handle is not reset: create it anew");
     if (h->alcc) return alcc_init(h);
     ckpt_clear(h);
     return init_state(h);
@@ -1657,6 +1690,7 @@ void cr_destroy(cr_handle h)
 {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->inner) cr_destroy(h->inner);
     ckpt_clear(h);
     for (void *p : h->bwd_allocs) cudaFree(p);
     for (auto &e : h->evs) {
@@ -1667,6 +1701,126 @@ void cr_destroy(cr_handle h)
     for (void *p : h->allocs) cudaFree(p);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
+}
+
+// ---- P-APG with K blocks (Sec. II-A) -------------------------------------------------------
+
+cr_status cr_blocks_create(const double *X, const double *ybar, int64_t N, int32_t n, const int32_t *block_of,
+                           const cr_options *opt, int32_t inner_iters, cr_handle *out)
+{
+    if (!out) return create_error(CR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (check_inputs(X, ybar, N, n) != CR_OK)
+        return create_error(CR_EINVAL, "need X, ybar finite, 1 <= n <= 32 and N >= n + 1");
+    if (!block_of || inner_iters < 2 || (inner_iters & 1))
+        return create_error(CR_EINVAL, "need block_of (N entries) and an even inner_iters >= 2");
+    if (n > crk::kMaxNF64) return create_error(CR_EINVAL, "K-block P-APG runs with FP64 multipliers: n <= 10");
+    std::vector<int> used((size_t)N, 0);
+    for (long long l = 0; l < N; ++l) {
+        if (block_of[l] < 0 || block_of[l] >= N) return create_error(CR_EINVAL, "block ids must lie in [0, N)");
+        used[block_of[l]] = 1;
+    }
+    int K = 0;
+    for (int u : used) K += u;
+    cr_options o;
+    if (opt) o = *opt;
+    else cr_options_default(&o);
+    o.theta_dtype = CR_THETA_F64;
+    o.driver = CR_DRIVER_PHASES;
+    o.pair_engine = CR_PAIR_CUDA_CORES;
+    o.record_every = 0;
+    o.restart = 0;
+    o.momentum = 1;
+    o.B_theta = 0.0;
+    std::vector<double> Xv(X, X + (size_t)N * n), yv(ybar, ybar + N);
+    cr_handle h = nullptr, in = nullptr;
+    cr_status s = create_impl(Xv, yv, N, n, &o, &h);
+    if (s != CR_OK) return finish_create(s, &h);
+    o.stream = h->stream;   // one stream for both duals
+    std::vector<double> Xi(X, X + (size_t)N * n), yi(ybar, ybar + N);
+    s = create_impl(Xi, yi, N, n, &o, &in);
+    if (s != CR_OK) {
+        std::string m = in ? in->err : std::string("inner handle");
+        if (in) cr_destroy(in);
+        cr_destroy(h);
+        return create_error(s, m.c_str());
+    }
+    h->inner = in;
+    h->blocks = true;
+    h->K = K;
+    h->inner_iters = inner_iters;
+    int *blk = nullptr;
+    CR_TRY(dev_alloc(h, &blk, (size_t)N));
+    std::vector<int> bv(block_of, block_of + N);
+    CR_CUDA(h, cudaMemcpyAsync(blk, bv.data(), sizeof(int) * N, cudaMemcpyHostToDevice, h->stream));
+    CR_TRY(dev_alloc(h, &h->b_a, (size_t)N));
+    CR_TRY(dev_alloc(h, &h->b_b, (size_t)N * n));
+    CR_TRY(dev_alloc(h, &h->b_mu2, (size_t)N));
+    // outer: the pairs between blocks; its foldB is replaced by the block Step 1 (no fusion)
+    h->P.blk = blk;
+    h->P.blkmode = 1;
+    h->P.fuse = 0;
+    // inner: the pairs inside the blocks, Step 1 of the block problems (linear term a, subgradient
+    // offset b, no y >= 0 rows), plain P-APG iterations without fusion (a and b change between calls)
+    in->P.blk = blk;
+    in->P.blkmode = 2;
+    in->P.fuse = 0;
+    in->P.no_mu = 1;
+    in->P.h = h->b_a;
+    in->P.xi_off = h->b_b;
+    in->prepared = false;
+    CR_CUDA(h, cudaMemcpyAsync(h->b_a, h->P.h, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+    CR_CUDA(h, cudaMemsetAsync(h->b_b, 0, sizeof(double) * N * n, h->stream));
+    CR_CUDA(h, cudaStreamSynchronize(h->stream));
+    // Iteration 0 (theta = 0, mu = 0): the inner handle's state too
+    s = init_state(in);
+    if (s != CR_OK) {
+        cr_destroy(h);
+        return create_error(s, "inner reset failed");
+    }
+    *out = h;
+    return CR_OK;
+}
+
+cr_status cr_blocks_iterate(cr_handle h, int64_t k)
+{
+    CR_TRY(usable(h));
+    if (!h->blocks) return fail(h, CR_ESTATE, "not a K-block handle");
+    if (k < 0) return fail(h, CR_EINVAL, "k < 0");
+    const int grid = 4 * h->num_sms;
+    for (long long i = 0; i < k; ++i) {
+        const long long ell = h->iters + 1;
+        CR_TRY(blocks_step1(h, ell, 0));   // eta_ell at theta^(2)_ell
+        {
+            Params P = h->P;
+            const double *y = h->inner->P.y1, *xi = h->inner->P.xi1_64, *m2 = h->b_mu2;
+            long long e = ell;
+            void *args[] = {&P, &y, &xi, &m2, &e};
+            CR_CUDA(h, cudaLaunchKernel(h->ks.blocks_records, dim3(grid), dim3(256), args, 0, h->stream));
+        }
+        CR_TRY(launch_phase(h, crk::PH_PAIR, ell, -1.0));
+        CR_TRY(launch_phase(h, crk::PH_FOLDA, ell, -1.0));
+        h->prepared = false;
+        h->iters = ell;
+    }
+    // the primal point at the dual iterate theta^(1)_l (Theorem 1), Step 1 solved again
+    if (k > 0) CR_TRY(blocks_step1(h, h->iters, 1));
+    DevState st;
+    return read_state(h, &st);
+}
+
+cr_status cr_blocks_solution(cr_handle h, double *yhat, double *xi)
+{
+    CR_TRY(usable(h));
+    if (!h->blocks) return fail(h, CR_ESTATE, "not a K-block handle");
+    if (h->iters == 0) CR_TRY(blocks_step1(h, 0, 1));   // Iteration 0: the block problems at (h, 0)
+    cr_ctx *in = h->inner;
+    if (yhat) CR_CUDA(h, cudaMemcpyAsync(yhat, in->P.y1, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->stream));
+    if (xi) CR_CUDA(h, cudaMemcpyAsync(xi, in->P.xi1_64, sizeof(double) * h->N * h->n, cudaMemcpyDeviceToHost, h->stream));
+    CR_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (yhat)
+        for (long long l = 0; l < h->N; ++l) yhat[l] -= h->P.shift;
+    return CR_OK;
 }
 
 const char *cr_status_str(cr_status s) { return cr_status_str_impl(s); }

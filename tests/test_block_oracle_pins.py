@@ -90,3 +90,24 @@ def test_fewer_blocks_start_closer():
         b.iterate(1)
         e[K] = np.abs(b.y_hat - o.y_hat).max()
     assert e[2] < e[16]
+
+
+def test_inexact_step1_tends_to_the_exact_one():
+    # the inner P-APG on the block problems' duals (the inexact Step 1) approaches the exact NNLS
+    # Step 1 as its iteration count grows; singleton blocks have no inner constraints at all
+    X, yb = _inst(30)
+    g, L, s = 0.1, O.lipschitz(X, 0.1), O.shift(yb)
+    bl = _blocks(30, 2)
+    ex = BlockPapg(X, yb, bl, g, L, s)
+    ex.iterate(4)
+    errs = []
+    for M in (50, 500, 6000):
+        inx = BlockPapg(X, yb, bl, g, L, s, inner_iters=M)
+        inx.iterate(4)
+        errs.append(np.abs(inx.y_hat - ex.y_hat).max() / np.abs(ex.y_hat).max())
+    assert errs[2] <= 1e-6 and errs[2] < errs[1] < errs[0]
+    one = BlockPapg(X, yb, [[l] for l in range(30)], g, L, s, inner_iters=4)
+    o = O.Solver(X, yb, gamma=g, L=L, s=s, momentum=True, restart=False)
+    one.iterate(10)
+    o.iterate(10)
+    np.testing.assert_allclose(one.y_hat, o.y_hat, rtol=0, atol=1e-11 * np.abs(o.y_hat).max())
