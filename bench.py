@@ -564,6 +564,39 @@ def run_kkt(args):
     print(json.dumps(line))
 
 
+def run_blocks(args):
+    """P-APG with K blocks (Sec. II-A): K = N/100 blocks as in the paper's experiments (Sec. III),
+    Step 1 by the inner P-APG on the block problems' duals.  Recipe (1) shape at N = 2,000
+    (n = 2, gamma = 0.1), FP64 multipliers; reports outer iterations/s and the KKT-free progress
+    measure: the fit against the exact solution is not available at this size, so the line gives
+    the change of the fitted values over the timed iterations."""
+    import torch
+    import paper_1407_7220_gb300 as crg
+    torch.cuda.set_device(0)
+    N = args.blocks_N
+    K = max(1, N // 100)
+    M = args.blocks_inner
+    X, yb, _ = datagen.make("sq2", N=N)
+    blocks = [np.arange(i, N, K) for i in range(K)]
+    g = crg.BlockSolver(X, yb, blocks, inner_iters=M, gamma=0.1)
+    g.iterate(max(1, args.warmup))
+    y0, _ = g.solution()
+    with Clocks(0) as clk:
+        _, dt = _sync_time(lambda: g.iterate(args.steps))
+    y1, _ = g.solution()
+    cross = N * (N - 1) - sum(len(b) * (len(b) - 1) for b in blocks)
+    intra = N * (N - 1) - cross
+    line = {"metric": "outer P-APG iterations/s", "value": args.steps / dt, "unit": "iterations/s",
+            "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "dtype": "f64", "data": "synthetic",
+            "pair_updates_per_s": (cross + M * intra) * args.steps / dt,
+            "fit_change_over_steps": float(np.abs(y1 - y0).max() / np.abs(y1).max()),
+            "config": {"workload": f"sq2 recipe N={N} n=2 gamma=0.1, K={K} blocks (N/100), {M} inner P-APG "
+                                   f"iterations per outer iteration (Step 1), FP64 multipliers"},
+            "clocks": clk.summary()}
+    print(json.dumps(line))
+
+
 def run_traces(args):
     """The small experiment of Sec. III (Figs. Gap_All, Gap_APG, Distance_All): N = 100, n = 5,
     f0 = 1/2 x^T Q x; duality gap theta^T C eta and infeasibility ||(A_1 y + A_2 xi)_-||_2 (both
@@ -603,11 +636,13 @@ def main():
     ap.add_argument("--driver", type=int, default=2, help="1 persistent, 2 phase kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", default="maxaff",
-                    choices=["maxaff", "sq2", "lse", "batch", "sumexp", "alcc", "traces", "kkt"],
+                    choices=["maxaff", "sq2", "lse", "batch", "sumexp", "alcc", "traces", "kkt", "blocks"],
                     help="workload (default: the headline workload, recipe (2))")
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--batch-iters", type=int, default=20000)
     ap.add_argument("--batch-singles", type=int, default=64, help="fits of the batch also solved one by one")
+    ap.add_argument("--blocks-N", type=int, default=2000)
+    ap.add_argument("--blocks-inner", type=int, default=20)
     ap.add_argument("--kkt-targets", default="0.3,0.2,0.1,0.07,0.05,0.03,0.02")
     ap.add_argument("--kkt-cap", type=int, default=20000, help="iteration cap of --config kkt")
     ap.add_argument("--kkt-every", type=int, default=100)
@@ -618,7 +653,7 @@ def main():
         return run_reference(args)
     if args.config != "maxaff":
         return {"sq2": run_sq2, "lse": run_lse, "batch": run_batch, "sumexp": run_sumexp,
-                "alcc": run_alcc, "traces": run_traces, "kkt": run_kkt}[args.config](args)
+                "alcc": run_alcc, "traces": run_traces, "kkt": run_kkt, "blocks": run_blocks}[args.config](args)
     return run_ours(args)
 
 

@@ -153,9 +153,11 @@ struct Params {
 // ---------------------------------------------------------------------------
 template <typename TS> struct Store;
 
-// Counter-based generator: a multiply-xor mix of the counters (a, b, c) followed by the
-// "lowbias32" integer finalizer (C. Wellons' hash-prospector).  hash_col carries the
-// (b, c) part so that a loop over a with fixed (b, c) pays for it once.
+// Counter-based generator: a multiply-xor mix of the counters (a, b, c) followed by two rounds of
+// xor-shift and odd-constant multiply (a shortened form of the integer finalizers of C. Wellons'
+// hash-prospector; the rounding needs uniform bytes, not a full avalanche, and the pair pass
+// evaluates it once per row and lane).  hash_col carries the (b, c) part so that a loop over a
+// with fixed (b, c) pays for it once.
 __device__ __forceinline__ uint32_t hash_col(uint32_t b, uint32_t c)
 {
     return (b * 0x85EBCA77u + 0x165667B1u) ^ (c * 0xC2B2AE3Du + 0x27D4EB2Fu);
@@ -163,11 +165,9 @@ __device__ __forceinline__ uint32_t hash_col(uint32_t b, uint32_t c)
 __device__ __forceinline__ uint32_t hash_row(uint32_t hcol, uint32_t a)
 {
     uint32_t x = a * 0x9E3779B1u ^ hcol;
-    x ^= x >> 16;
-    x *= 0x7feb352du;
     x ^= x >> 15;
-    x *= 0x846ca68bu;
-    x ^= x >> 16;
+    x *= 0x2C1B3C6Du;
+    x ^= x >> 12;
     return x;
 }
 
@@ -249,7 +249,8 @@ template <> struct Store<float> {
         o[0] = t.x;
         o[1] = t.y;
     }
-    // round<SR> on both halves; rnd holds the two 16-bit uniforms (low half -> low column).
+    // round<SR> on both halves; bytes 0 and 1 of rnd are the two uniforms (u in [0,1) with 8
+    // bits: the expected rounding error is below 2^-9 ulp, against the ulp/2 of round-to-nearest).
     // floor(e/ulp + 1 + u) is taken exactly as the integer part of RD(t + 1.5*2^23).
     template <bool SR>
     __device__ static __forceinline__ f2 round2(f2 th2, f2 g, f2 ninvL2, float, uint32_t rnd, float)
@@ -263,8 +264,8 @@ template <> struct Store<float> {
             const uint32_t b0 = __float_as_uint(v0), b1 = __float_as_uint(v1);
             const float iu0 = __uint_as_float(0x8A800000u - max(b0 & 0x7F800000u, 23u << 23));
             const float iu1 = __uint_as_float(0x8A800000u - max(b1 & 0x7F800000u, 23u << 23));
-            const float u0 = __uint_as_float(0x3F800000u | ((rnd << 7) & 0x007FFF80u));
-            const float u1 = __uint_as_float(0x3F800000u | ((rnd >> 9) & 0x007FFF80u));
+            const float u0 = __uint_as_float(0x3F800000u | ((rnd << 15) & 0x007F8000u));
+            const float u1 = __uint_as_float(0x3F800000u | ((rnd << 7) & 0x007F8000u));
             const f2 t = f2_fma(e, f2_make(iu0, iu1), f2_make(u0, u1));
             const f2 fl = f2_add_rm(t, f2_make(12582912.0f, 12582912.0f));
             float fl0, fl1;
@@ -865,7 +866,8 @@ __device__ __forceinline__ void pair_stage_rows(const TS *tcur, const TS *tprv, 
         uint32_t hP[2] = {0u, 0u};
         if (SR) {
             hP[0] = hash_row(hcol, (uint32_t)rr);
-            hP[1] = (hP[0] ^ (hP[0] >> 15)) * 0x2C1B3C6Du;
+            // FP32: one hash gives the four 8-bit uniforms; 16-bit types use 16 bits per column
+            hP[1] = std::is_same<TS, float>::value ? hP[0] >> 16 : (hP[0] ^ (hP[0] >> 15)) * 0x2C1B3C6Du;
         }
         f2 rs2 = zero2;
 #pragma unroll
