@@ -165,8 +165,7 @@ def run_reference(args):
 # N(N-1) pair updates (the per-stage vectors make the excess over 3 b proportional to the
 # pairs); keyed by (engine, theta dtype, padded n).  A kernel change invalidates an entry.
 TRAFFIC_BYTES_PER_PAIR = {
-    ("cuda_cores", "f32", 10): (517.62048e6 + 219.80288e6) / (8000 * 7999),
-    ("tensor_cores", "bf16", 20): (742.873728e6 + 278.586368e6) / (12000 * 11999),
+    ("cuda_cores", "f32", 10): (517.62944e6 + 219.862016e6) / (8000 * 7999),
 }
 
 
@@ -192,14 +191,11 @@ def run_ours(args):
     X, yb, _ = datagen.make(RECIPE, N=N, n=n, seed=datagen.default_seed(RECIPE) + rank)
     stream = torch.cuda.Stream(device=dev)
     opts = dict(gamma=GAMMA, theta_dtype=args.dtype, stochastic_round=1, restart=0, driver=args.driver,
-                profile=1, stream=stream.cuda_stream)
+                profile=0, stream=stream.cuda_stream)
 
-    # --- device-resident throughput (value) ---
+    # --- device-resident throughput (value): K steps with no events between the launches ---
     s = crg.Solver(X, yb, **opts)
     s.iterate(args.warmup)
-    torch.cuda.synchronize()
-    for k in range(4):
-        s.profile(k)  # drop warm-up timings
     barrier = (lambda: torch.distributed.barrier()) if ws > 1 else (lambda: None)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -212,6 +208,20 @@ def run_ours(args):
         torch.cuda.synchronize()
     barrier()
     ms = dist_max(ev0.elapsed_time(ev1), dev)
+    s.close()
+
+    # --- the same K steps again with CUDA events around every launch: per-kernel durations for
+    # the roofline (the events serialize the launches, so this region does not give the value) ---
+    s = crg.Solver(X, yb, **dict(opts, profile=1))
+    s.iterate(args.warmup)
+    torch.cuda.synchronize()
+    for k in range(4):
+        s.profile(k)  # drop warm-up timings
+    barrier()
+    with Clocks(local) as clk_k:
+        s.iterate(args.steps)
+        torch.cuda.synchronize()
+    barrier()
     pair_ms, pair_n = s.profile(crg.PROFILE_PAIR)
     fold_ms, fold_n = s.profile(crg.PROFILE_FOLD)
     engine = s.info()["engine"]
@@ -278,7 +288,9 @@ def run_ours(args):
                     "note": "create from pinned host arrays + K iterations + fitted values back, per run"},
             "gpu_launches": launches,
             "clocks": clk.summary(),
-            "kernel_ms": {"pair": pair_ms, "fold": fold_ms, "persistent": pers_ms, "kkt": kkt_ms},
+            "kernel_ms": {"pair": pair_ms, "fold": fold_ms, "persistent": pers_ms, "kkt": kkt_ms,
+                          "region": "a second run of the K steps with events around every launch",
+                          "clocks": clk_k.summary()},
         }
         if cpu:
             line["cpu_baseline"] = cpu

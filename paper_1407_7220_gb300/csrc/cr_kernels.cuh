@@ -101,6 +101,8 @@ struct Params {
     float alcc_delta;               // ALCC passes: relative bound of the FP32 residual's error, (n + 4) 2^-23
     int momentum, restart, sr;
     int fuse;           // 1: foldA(l) also performs foldB(l+1) (plain P-APG: beta needs no reduction)
+    int fold_stats;     // 1: foldA writes its objective / y >= 0 partial sums (foldpart); with P.fuse the
+                        // drivers ask for them on check iterations and the last iteration of a call only
     double restart_tol;
     unsigned int seed;
     unsigned long long bar_timeout_ns;   // bound of every grid-barrier wait
@@ -115,6 +117,7 @@ struct Params {
     double *y1, *xi1_64;            // eta(theta^(1)) in FP64 (y shifted)
     double *v[2];           // A_1^T theta^(1) of the two latest iterates (N)
     double *w[2];           // A_2^T theta^(1) (N x n)
+    double *dd[2];          // w_l . x_l of the two latest iterates (N): foldB's xi^(2).x by linearity
     double *mu[2];          // multipliers of the y >= 0 rows (N)
     float *rowpart;         // [N][Q]: row sums per (stripe, column half), Q = ceil4(2S), padding 0
     int Q;
@@ -153,23 +156,22 @@ struct Params {
 // ---------------------------------------------------------------------------
 template <typename TS> struct Store;
 
-// Counter-based generator: a multiply-xor mix of the counters (a, b, c) followed by two rounds of
-// xor-shift and odd-constant multiply (a shortened form of the integer finalizers of C. Wellons'
-// hash-prospector; the rounding needs uniform bytes, not a full avalanche, and the pair pass
-// evaluates it once per row and lane).  hash_col carries the (b, c) part so that a loop over a
-// with fixed (b, c) pays for it once.
+// Counter-based generator for the stochastic rounding: hash_col mixes the column group and the
+// iteration seed (b, c) once per segment; hash_row then takes the row a with one multiply-add,
+// one odd-constant multiply and one xor-shift (a single round of the multiply/xor-shift integer
+// finalizers of C. Wellons' hash-prospector: the rounding needs 16-bit uniforms that vary from
+// pair to pair and iteration to iteration, not a full avalanche, and the pair pass evaluates it
+// once per row and lane); hash_next derives a second word from the first.
 __device__ __forceinline__ uint32_t hash_col(uint32_t b, uint32_t c)
 {
     return (b * 0x85EBCA77u + 0x165667B1u) ^ (c * 0xC2B2AE3Du + 0x27D4EB2Fu);
 }
 __device__ __forceinline__ uint32_t hash_row(uint32_t hcol, uint32_t a)
 {
-    uint32_t x = a * 0x9E3779B1u ^ hcol;
-    x ^= x >> 15;
-    x *= 0x2C1B3C6Du;
-    x ^= x >> 12;
-    return x;
+    const uint32_t x = (a * 0x9E3779B1u + hcol) * 0x2C1B3C6Du;
+    return x ^ (x >> 15);
 }
+__device__ __forceinline__ uint32_t hash_next(uint32_t h) { return (h ^ (h >> 16)) * 0x85EBCA77u; }
 
 // Packed FP32 pairs (the f32x2 arithmetic of sm_100 and later): one instruction performs
 // two IEEE single-precision operations, each half rounded exactly as the scalar one, so a
@@ -249,9 +251,13 @@ template <> struct Store<float> {
         o[0] = t.x;
         o[1] = t.y;
     }
-    // round<SR> on both halves; bytes 0 and 1 of rnd are the two uniforms (u in [0,1) with 8
-    // bits: the expected rounding error is below 2^-9 ulp, against the ulp/2 of round-to-nearest).
-    // floor(e/ulp + 1 + u) is taken exactly as the integer part of RD(t + 1.5*2^23).
+    // round<SR> on both halves: r = v + k ulp(v), k = floor(e/ulp(v) + u), u uniform in [0,1)
+    // from 16 bits (the low half of rnd for the first value, the high half for the second).
+    // The scaling s = 2^(1 - E) (E the exponent of |v|, |v| clamped below at 2^-100) is the
+    // complemented exponent field of |v|, so e s = (e/ulp) 2^-22.  t = e s + U with
+    // U = 2^-15 + u 2^-22 (the 16 bits of u are the low mantissa bits of U) carries e/ulp + u to
+    // 2^-16; RD(t + 3 - 2^-15) lands in [2, 4), whose spacing is 2^-22, so its bit pattern minus
+    // that of 3 is k (in {-1, 0, 1} since |e| <= ulp/2).
     template <bool SR>
     __device__ static __forceinline__ f2 round2(f2 th2, f2 g, f2 ninvL2, float, uint32_t rnd, float)
     {
@@ -262,16 +268,16 @@ template <> struct Store<float> {
         if (SR) {
             const f2 e = f2_fma(g, ninvL2, f2_sub(th2, v));
             const uint32_t b0 = __float_as_uint(v0), b1 = __float_as_uint(v1);
-            const float iu0 = __uint_as_float(0x8A800000u - max(b0 & 0x7F800000u, 23u << 23));
-            const float iu1 = __uint_as_float(0x8A800000u - max(b1 & 0x7F800000u, 23u << 23));
-            const float u0 = __uint_as_float(0x3F800000u | ((rnd << 15) & 0x007F8000u));
-            const float u1 = __uint_as_float(0x3F800000u | ((rnd << 7) & 0x007F8000u));
-            const f2 t = f2_fma(e, f2_make(iu0, iu1), f2_make(u0, u1));
-            const f2 fl = f2_add_rm(t, f2_make(12582912.0f, 12582912.0f));
+            const float s0 = __uint_as_float(~__float_as_uint(fmaxf(fabsf(v0), 0x1p-100f)) & 0x7F800000u);
+            const float s1 = __uint_as_float(~__float_as_uint(fmaxf(fabsf(v1), 0x1p-100f)) & 0x7F800000u);
+            const float u0 = __uint_as_float(__byte_perm(rnd, 0x38000000u, 0x7610u));   // U = 2^-15 + u 2^-22
+            const float u1 = __uint_as_float(__byte_perm(rnd, 0x38000000u, 0x7632u));
+            const f2 t = f2_fma(e, f2_make(s0, s1), f2_make(u0, u1));
+            const f2 fl = f2_add_rm(t, f2_make(3.0f - 0x1p-15f, 3.0f - 0x1p-15f));
             float fl0, fl1;
             f2_split(fl, fl0, fl1);
-            r0 = __uint_as_float(b0 + __float_as_uint(fl0) - 0x4B400001u);
-            r1 = __uint_as_float(b1 + __float_as_uint(fl1) - 0x4B400001u);
+            r0 = __uint_as_float(b0 + __float_as_uint(fl0) - 0x40400000u);   // b + k
+            r1 = __uint_as_float(b1 + __float_as_uint(fl1) - 0x40400000u);
         }
         // projection on theta >= 0 as max(r, 0): for v > 0 the rounded r is >= 0; for v < 0 it is
         // negative, and for v = -0 or +0 it is 0, a NaN pattern (max gives 0) or, with SR, the
@@ -647,6 +653,7 @@ template <int NP>
 __device__ __forceinline__ void foldB_row(const Params &P, int c, int p, long long l, double beta)
 {
     const double b1 = 1.0 + beta;
+    const double g1 = b1 * P.inv_gamma, g0 = beta * P.inv_gamma;
     const int n = P.n;
     double v2 = b1 * __ldcg(P.v[c] + l) - beta * __ldcg(P.v[p] + l);
     double mu2 = b1 * __ldcg(P.mu[c] + l) - beta * __ldcg(P.mu[p] + l);
@@ -654,33 +661,30 @@ __device__ __forceinline__ void foldB_row(const Params &P, int c, int p, long lo
     double mun = mu2 - y2 * P.invL_d;     // Step 2 on the y >= 0 rows of C
     P.mu[p][l] = (mun > 0.0 && !P.no_mu) ? mun : 0.0;
     double ys = y2 - P.shift;
-    double d = 0.0;
+    // xi^(2) = ((1 + beta) w_c - beta w_p) / gamma (+ the offset of the K-block inner problems),
+    // and xi^(2).x_l by the same linearity from w.x of the two iterates
+    double d = (b1 * __ldcg(P.dd[c] + l) - beta * __ldcg(P.dd[p] + l)) * P.inv_gamma;
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         float xf = 0.0f;
+        double xi = 0.0;
         if (k < n) {
-            double xi = (b1 * __ldcg(P.w[c] + l * n + k) - beta * __ldcg(P.w[p] + l * n + k)) * P.inv_gamma;
-            if (P.xi_off) xi += __ldcg(P.xi_off + l * n + k);
-            d += xi * __ldg(P.X64 + l * n + k);
+            xi = fma(g1, __ldcg(P.w[c] + l * n + k), -(g0 * __ldcg(P.w[p] + l * n + k)));
+            if (P.xi_off) {
+                const double o = __ldcg(P.xi_off + l * n + k);
+                xi += o;
+                d += o * __ldg(P.X64 + l * n + k);
+            }
             xf = (float)xi;
         }
         P.xi2[l * NP + k] = xf;
+        if (P.f64) P.xi2_64[l * NP + k] = xi;   // the FP64 pass reads the column data unrounded
     }
     P.rowrec[l * RecLayout<NP>::REC] = (float)ys;
     P.ccol2[l] = (float)(d - ys);
     if (P.f64) {
-        // the FP64 pass reads the same column and row data unrounded
         P.rec64[l * RecLayout<NP>::REC] = ys;
         P.ccol2_64[l] = d - ys;
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            double xi = 0.0;
-            if (k < n) {
-                xi = (b1 * __ldcg(P.w[c] + l * n + k) - beta * __ldcg(P.w[p] + l * n + k)) * P.inv_gamma;
-                if (P.xi_off) xi += __ldcg(P.xi_off + l * n + k);
-            }
-            P.xi2_64[l * NP + k] = xi;
-        }
     }
     if (P.tc) {
         // Xi of column l as the A operand of the residual product: stripe l/256, column pair
@@ -866,10 +870,9 @@ __device__ __forceinline__ void pair_stage_rows(const TS *tcur, const TS *tprv, 
         uint32_t hP[2] = {0u, 0u};
         if (SR) {
             hP[0] = hash_row(hcol, (uint32_t)rr);
-            // FP32: one hash gives the four 8-bit uniforms; 16-bit types use 16 bits per column
-            hP[1] = std::is_same<TS, float>::value ? hP[0] >> 16 : (hP[0] ^ (hP[0] >> 15)) * 0x2C1B3C6Du;
+            hP[1] = hash_next(hP[0]);   // 16 bits per column
         }
-        f2 rs2 = zero2;
+        f2 rs2;
 #pragma unroll
         for (int P = 0; P < 2; ++P) {
             const f2 th2 = f2_fma(beta2, f2_sub(tc[P], tp[P]), tc[P]);   // theta^(2) = theta^(1) + beta (theta^(1) - prev)
@@ -912,7 +915,7 @@ __device__ __forceinline__ void pair_stage_rows(const TS *tcur, const TS *tprv, 
             }
             outv[P] = sv;
             const f2 vv = St::decoded2(sv, iscl2);
-            rs2 = f2_add(rs2, vv);                                          // row sum    (A_1^T, + part)
+            rs2 = P == 0 ? vv : f2_add(rs2, vv);                            // row sum    (A_1^T, + part)
             csum[P] = f2_add(csum[P], vv);                                  // column sum (A_1^T, - part)
 #pragma unroll
             for (int k = 0; k < NP; ++k) acc[P][k] = f2_fma(vv, xb[k], acc[P][k]);   // theta^T X (A_2^T)
@@ -1421,7 +1424,7 @@ __device__ void phase_ball_scale(const Params &P, long long ell, long long vc)
 // foldA(l): reduce partials of theta^(1)_l in FP64; eta(theta^(1)_l); dual terms
 // ---------------------------------------------------------------------------
 template <int NP>
-__device__ void phase_foldA(const Params &P, long long ell, double *red, long long vc)
+__device__ void phase_foldA(const Params &P, long long ell, double *red, long long vc, bool stats = true)
 {
     const int p = (int)(ell & 1);
     const long long N = P.N;
@@ -1472,7 +1475,7 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red, long lo
         const double hl = __ldcg(P.h + l), mu = __ldcg(P.mu[p] + l);
         const double y = hl + v + mu;          // Step 1 closed form
         const double ys = y - P.shift;
-        double d = 0.0, xin = 0.0;
+        double dw = 0.0, doff = 0.0, xin = 0.0;
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
             float xf = 0.0f;
@@ -1480,28 +1483,38 @@ __device__ void phase_foldA(const Params &P, long long ell, double *red, long lo
                 const double xk = __ldg(P.X64 + l * n + k);
                 const double wk = Cc * xk - TX[k];   // (A_2^T theta)_l = Cc_l x_l - (theta^T X)_l
                 P.w[p][l * n + k] = wk;
-                const double xi = wk * P.inv_gamma + (P.xi_off ? __ldcg(P.xi_off + l * n + k) : 0.0);
+                double xi = wk * P.inv_gamma;
+                if (P.xi_off) {
+                    const double o = __ldcg(P.xi_off + l * n + k);
+                    xi += o;
+                    doff += o * xk;
+                }
                 P.xi1_64[l * n + k] = xi;
-                d += xi * xk;
-                xin += xi * xi;
+                dw += wk * xk;
+                if (stats) xin += xi * xi;
                 xf = (float)xi;
             }
             P.xi1[l * NP + k] = xf;
         }
+        P.dd[p][l] = dw;
+        const double d = dw * P.inv_gamma + doff;   // xi_l . x_l
         P.y1[l] = y;
         P.yrow1[l] = (float)ys;
         P.ccol1[l] = (float)(d - ys);
-        const double uu = y - hl;
-        a += uu * uu;
-        b += xin;
-        cc += uu * y;
-        mviol = fmax(mviol, -y);
-        mcomp = fmax(mcomp, mu * fabs(y));
-        if (y < 0.0) sviol += y * y;
-        smuy += mu * y;
+        if (stats) {
+            const double uu = y - hl;
+            a += uu * uu;
+            b += xin;
+            cc += uu * y;
+            mviol = fmax(mviol, -y);
+            mcomp = fmax(mcomp, mu * fabs(y));
+            if (y < 0.0) sviol += y * y;
+            smuy += mu * y;
+        }
         if (!isfinite(y) || !isfinite(d)) atomicCAS(&P.st->error, 0, ERR_NUMERIC);
         if (P.fuse) foldB_row<NP>(P, p, p ^ 1, l, s_nbeta);   // this row of foldB(l+1)
     }
+    if (!stats) return;   // the same value in every thread of the grid
     double vals[7] = {a, b, cc, mviol, mcomp, sviol, smuy};
     const bool ismax[7] = {false, false, false, true, true, false, false};
     block_reduce<7>(vals, ismax, red);

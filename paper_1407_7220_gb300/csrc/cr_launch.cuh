@@ -62,9 +62,9 @@ __device__ __forceinline__ void persistent_body(const Params &P, long long ell0,
     for (long long ell = ell0; ell <= ell1; ++ell) {
         phase_pair<TS, NP>(P, ell, sm, full, empty, kstage, blockIdx.x);
         if (!grid_barrier(P, bar)) return;
-        phase_foldA<NP>(P, ell, red, blockIdx.x);
-        if (!grid_barrier(P, bar)) return;
         const bool check = check_every > 0 && ((ell % check_every) == 0 || ell == ell1);
+        phase_foldA<NP>(P, ell, red, blockIdx.x, !P.fuse || check || ell == ell1);
+        if (!grid_barrier(P, bar)) return;
         if (check) {
             phase_kkt<TS, NP, false>(P, ell, red, blockIdx.x);
             if (!grid_barrier(P, bar)) return;
@@ -125,6 +125,10 @@ k_persistent(const __grid_constant__ Params P, long long ell0, long long ell1, i
 
 // One phase of one iteration (the CR_DRIVER_PHASES path and the stand-alone metric
 // calls).  Every kernel is a no-op once the state says converged or failed.
+// Launched as a programmatic dependent of the previous phase: its CTAs may be placed while the
+// previous grid drains, and griddepcontrol.wait (before any access to the state) holds them
+// until that grid has completed and its writes are visible; the next phase may then be
+// launched early in turn.  Without a programmatic launch both instructions are no-ops.
 template <typename TS, int NP>
 __global__ void __launch_bounds__(kThreads, 1)
 k_phase(const __grid_constant__ Params P, int phase, long long ell, double tol, double sigma)
@@ -132,6 +136,8 @@ k_phase(const __grid_constant__ Params P, int phase, long long ell, double tol, 
     extern __shared__ unsigned char sm_raw[];
     __shared__ double red[72];
     __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int conv = __ldcg(&P.st->converged), err = __ldcg(&P.st->error);
     if (err != 0) return;
     if (conv != 0 && phase != PH_KKT64 && phase != PH_DECIDE64) return;
@@ -143,7 +149,7 @@ k_phase(const __grid_constant__ Params P, int phase, long long ell, double tol, 
         phase_pair<TS, NP>(P, ell, aligned_smem(sm_raw), full, empty, kstage, blockIdx.x);
         break;
     }
-    case PH_FOLDA: phase_foldA<NP>(P, ell, red, blockIdx.x); break;
+    case PH_FOLDA: phase_foldA<NP>(P, ell, red, blockIdx.x, P.fold_stats != 0); break;
     case PH_BALL_NORM: phase_ball_norm<TS, NP>(P, ell, red, blockIdx.x); break;
     case PH_BALL_SCALE: phase_ball_scale<TS>(P, ell, blockIdx.x); break;
     case PH_KKT32: phase_kkt<TS, NP, false>(P, ell, red, blockIdx.x); break;

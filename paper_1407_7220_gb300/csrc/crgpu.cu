@@ -83,6 +83,7 @@ struct cr_ctx {
         long long iter = -1;
         void *th[2] = {nullptr, nullptr};
         double *v[2] = {nullptr, nullptr}, *w[2] = {nullptr, nullptr}, *mu[2] = {nullptr, nullptr};
+        double *dd[2] = {nullptr, nullptr};
         DevState st;
         // full snapshots also keep the minimizer at theta^(1) and the fold partials
         bool full = false;
@@ -412,9 +413,10 @@ int phase_kind(int phase)
     return 2;
 }
 
-cr_status launch_phase(cr_ctx *h, int phase, long long ell, double tol, int grid = -1)
+cr_status launch_phase(cr_ctx *h, int phase, long long ell, double tol, int grid = -1, int fold_stats = 1)
 {
     Params P = h->P;
+    P.fold_stats = fold_stats;
     void *args[] = {&P, &phase, &ell, &tol, &h->sigma};
     const int g = grid > 0 ? grid : h->P.G;
     ProfScope ps(h, phase_kind(phase));
@@ -423,7 +425,19 @@ cr_status launch_phase(cr_ctx *h, int phase, long long ell, double tol, int grid
         CR_CUDA(h, cudaLaunchKernel(h->ks.pair_tc, dim3(g), dim3(crk::kTcThreads), targs, h->ks.smem, h->stream));
         return CR_OK;
     }
-    CR_CUDA(h, cudaLaunchKernel(h->ks.phase, dim3(g), dim3(crk::kThreads), args, h->ks.smem, h->stream));
+    // programmatic dependent launch: k_phase waits (griddepcontrol.wait) for the previous grid
+    // before it reads anything, so its launch may overlap the previous kernel's drain
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g);
+    cfg.blockDim = dim3(crk::kThreads);
+    cfg.dynamicSmemBytes = h->ks.smem;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CR_CUDA(h, cudaLaunchKernelExC(&cfg, h->ks.phase, args));
     if (phase == crk::PH_FOLDA) h->prepared = h->P.fuse != 0;
     else if (phase == crk::PH_FOLDB) h->prepared = false;
     return CR_OK;
@@ -446,12 +460,16 @@ cr_status launch_persistent(cr_ctx *h, long long ell0, long long ell1, int check
 cr_status run_phases(cr_ctx *h, long long ell0, long long ell1, int check_every, double tol)
 {
     for (long long ell = ell0; ell <= ell1; ++ell) {
+        const bool check = check_every > 0 && ((ell % check_every) == 0 || ell == ell1);
+        // the objective and y >= 0 partial sums: every iteration without P.fuse (the restart test
+        // of foldB reads them), else where a check or the caller (cr_objective) reads them
+        const int stats = (!h->P.fuse || check || ell == ell1) ? 1 : 0;
         if (!h->prepared) CR_TRY(launch_phase(h, crk::PH_FOLDB, ell, tol));
         CR_TRY(launch_phase(h, crk::PH_PAIR, ell, tol));
         if (h->P.ball) CR_TRY(launch_phase(h, crk::PH_BALL_NORM, ell, tol));
-        CR_TRY(launch_phase(h, crk::PH_FOLDA, ell, tol));   // with P.fuse also foldB(ell + 1)
+        CR_TRY(launch_phase(h, crk::PH_FOLDA, ell, tol, -1, stats));   // with P.fuse also foldB(ell + 1)
         if (h->P.ball) CR_TRY(launch_phase(h, crk::PH_BALL_SCALE, ell, tol));
-        if (check_every > 0 && ((ell % check_every) == 0 || ell == ell1)) {
+        if (check) {
             CR_TRY(launch_phase(h, crk::PH_KKT32, ell, tol));
             CR_TRY(launch_phase(h, crk::PH_DECIDE32, ell, tol, 1));
             Params P = h->P;
@@ -536,6 +554,7 @@ cr_status init_state(cr_ctx *h)
         CR_CUDA(h, cudaMemsetAsync(P.v[b], 0, sizeof(double) * h->N, h->stream));
         CR_CUDA(h, cudaMemsetAsync(P.w[b], 0, sizeof(double) * h->N * h->n, h->stream));
         CR_CUDA(h, cudaMemsetAsync(P.mu[b], 0, sizeof(double) * h->N, h->stream));
+        CR_CUDA(h, cudaMemsetAsync(P.dd[b], 0, sizeof(double) * h->N, h->stream));
     }
     CR_CUDA(h, cudaMemsetAsync(P.rowpart, 0, sizeof(float) * (size_t)P.Q * h->N, h->stream));
     CR_CUDA(h, cudaMemsetAsync(P.colpart, 0, sizeof(float) * (size_t)P.G * P.slots * P.cgroups * (h->NP + 1) * crk::kW, h->stream));
@@ -574,7 +593,8 @@ cr_status ckpt_save(cr_ctx *h, cr_ctx::Checkpoint &c)
     if (!c.th[0]) {
         for (int b = 0; b < 2; ++b)
             if (!al(&c.th[b], th) || !al((void **)&c.v[b], sizeof(double) * h->N) ||
-                !al((void **)&c.w[b], sizeof(double) * h->N * h->n) || !al((void **)&c.mu[b], sizeof(double) * h->N)) {
+                !al((void **)&c.w[b], sizeof(double) * h->N * h->n) || !al((void **)&c.mu[b], sizeof(double) * h->N) ||
+                !al((void **)&c.dd[b], sizeof(double) * h->N)) {
                 (void)cudaGetLastError();
                 return fail(h, CR_ENOMEM, "checkpoint allocation failed");
             }
@@ -600,6 +620,7 @@ cr_status ckpt_save(cr_ctx *h, cr_ctx::Checkpoint &c)
         CR_CUDA(h, cudaMemcpyAsync(c.v[b], h->P.v[b], sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->stream));
         CR_CUDA(h, cudaMemcpyAsync(c.w[b], h->P.w[b], sizeof(double) * h->N * h->n, cudaMemcpyDeviceToDevice, h->stream));
         CR_CUDA(h, cudaMemcpyAsync(c.mu[b], h->P.mu[b], sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(c.dd[b], h->P.dd[b], sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->stream));
     }
     CR_CUDA(h, cudaMemcpyAsync(&c.st, h->P.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
     CR_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -615,6 +636,7 @@ cr_status ckpt_restore(cr_ctx *h, const cr_ctx::Checkpoint &c)
         CR_CUDA(h, cudaMemcpyAsync(h->P.v[b], c.v[b], sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->stream));
         CR_CUDA(h, cudaMemcpyAsync(h->P.w[b], c.w[b], sizeof(double) * h->N * h->n, cudaMemcpyDeviceToDevice, h->stream));
         CR_CUDA(h, cudaMemcpyAsync(h->P.mu[b], c.mu[b], sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->stream));
+        CR_CUDA(h, cudaMemcpyAsync(h->P.dd[b], c.dd[b], sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->stream));
     }
     if (c.full) {
         const long long N = h->N;
@@ -794,6 +816,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     // foldB(l+1) fused into foldA(l): plain P-APG (beta from the t-sequence alone), no recording
     // (cr_backward restores checkpoints and re-runs foldB), not in a batch
     P.fuse = (o.restart == 0 && o.record_every <= 0 && np_override <= 0 && !h->alcc) ? 1 : 0;
+    P.fold_stats = 1;
     P.restart_tol = o.restart_tol > 0.0 ? o.restart_tol : 0.0;
     P.sr = o.stochastic_round;
     P.seed = (unsigned)(o.seed ^ (o.seed >> 32));
@@ -850,6 +873,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
         CR_TRY(dev_alloc(h, &P.v[b], N));
         CR_TRY(dev_alloc(h, &P.w[b], (size_t)N * n));
         CR_TRY(dev_alloc(h, &P.mu[b], N));
+        CR_TRY(dev_alloc(h, &P.dd[b], N));
     }
     CR_TRY(dev_alloc(h, &P.rowpart, (size_t)P.Q * N));
     CR_TRY(dev_alloc(h, &P.colpart, (size_t)G * P.slots * P.cgroups * (h->NP + 1) * crk::kW));
