@@ -166,6 +166,7 @@ def run_reference(args):
 # pairs); keyed by (engine, theta dtype, padded n).  A kernel change invalidates an entry.
 TRAFFIC_BYTES_PER_PAIR = {
     ("cuda_cores", "f32", 10): (517.62944e6 + 219.862016e6) / (8000 * 7999),
+    ("tensor_cores", "bf16", 20): (737.105536e6 + 259.67936e6) / (12000 * 11999),
 }
 
 

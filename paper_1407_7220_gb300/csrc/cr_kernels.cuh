@@ -315,9 +315,10 @@ template <> struct Store<__nv_bfloat16> {
     }
     __device__ static __forceinline__ Vec pack(const float (&s)[4])
     {
+        // the top halves of two values in one byte permute
         Vec v;
-        v.x = (__float_as_uint(s[0]) >> 16) | (__float_as_uint(s[1]) & 0xFFFF0000u);
-        v.y = (__float_as_uint(s[2]) >> 16) | (__float_as_uint(s[3]) & 0xFFFF0000u);
+        v.x = __byte_perm(__float_as_uint(s[0]), __float_as_uint(s[1]), 0x7632u);
+        v.y = __byte_perm(__float_as_uint(s[2]), __float_as_uint(s[3]), 0x7632u);
         return v;
     }
     __device__ static __forceinline__ float decoded(float s, float) { return s; }
@@ -328,13 +329,22 @@ template <> struct Store<__nv_bfloat16> {
         o[0] = f2_make(b2f(t.x & 0xFFFFu), b2f(t.x >> 16));
         o[1] = f2_make(b2f(t.y & 0xFFFFu), b2f(t.y >> 16));
     }
+    // round<SR> on both halves, the update as one packed FMA (g * (-1/L) + th2 is the value of
+    // fmaf(-g, 1/L, th2) in each half)
     template <bool SR>
-    __device__ static __forceinline__ f2 round2(f2 th2, f2 g, f2, float invL, uint32_t rnd, float scl)
+    __device__ static __forceinline__ f2 round2(f2 th2, f2 g, f2 ninvL2, float, uint32_t rnd, float)
     {
-        float t0, t1, g0, g1;
-        f2_split(th2, t0, t1);
-        f2_split(g, g0, g1);
-        return f2_make(round<SR>(t0, g0, invL, rnd & 0xFFFFu, scl), round<SR>(t1, g1, invL, rnd >> 16, scl));
+        float v0, v1;
+        f2_split(f2_fma(g, ninvL2, th2), v0, v1);
+        uint32_t b0 = __float_as_uint(v0), b1 = __float_as_uint(v1);
+        if (SR) {
+            b0 += rnd & 0xFFFFu;
+            b1 += rnd >> 16;
+        } else {
+            b0 += 0x7FFFu + ((b0 >> 16) & 1u);
+            b1 += 0x7FFFu + ((b1 >> 16) & 1u);
+        }
+        return f2_make(fmaxf(__uint_as_float(b0 & 0xFFFF0000u), 0.0f), fmaxf(__uint_as_float(b1 & 0xFFFF0000u), 0.0f));
     }
     __device__ static __forceinline__ Vec pack2(const f2 (&s)[2])
     {

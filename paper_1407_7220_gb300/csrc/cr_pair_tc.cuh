@@ -218,6 +218,7 @@ struct TcBars {
     uint64_t drain[2];               // end of pass: every MMA of issuer 1 / issuer 2 done
     uint32_t tmem;
     uint32_t drain_parity[2];        // completions of drain[i] so far, mod 2 (its issuer only)
+    float rowx[4][2][4][8];          // row sums of a stage per warpgroup, stage parity, 64-column slab
 };
 
 __device__ __forceinline__ void tc_init_bars(TcBars &B)
@@ -291,7 +292,7 @@ template <> struct Pair2<__nv_bfloat16> {
     {
         float a, b;
         f2_split(s, a, b);
-        *reinterpret_cast<uint32_t *>(p) = (__float_as_uint(a) >> 16) | (__float_as_uint(b) & 0xFFFF0000u);
+        *reinterpret_cast<uint32_t *>(p) = __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632u);
     }
 };
 template <> struct Pair2<__half> {
@@ -309,8 +310,12 @@ template <> struct Pair2<__half> {
 };
 
 // Row sums of one stage (8 rows per warp) reduced across the warp with a transposing
-// butterfly (9 shuffles); entry e = 4*bit4 + 2*bit3 + bit2 of the lane id is row r8 + e.
-__device__ __forceinline__ void tc_flush_rows(float (&v)[8], long long r8, long long r1, float *rp, int Q, int lane)
+// butterfly (9 shuffles); entry e = 4*bit4 + 2*bit3 + bit2 of the lane id is row r8 + e.  The
+// four warps of a warpgroup (the four 64-column slabs of the stripe, q = 0..3) then add their
+// sums through shared memory (xb: this warpgroup's [4][8] block for the stage's parity; named
+// barrier 1 + wg), and warp q = 0 stores one partial per (stripe, row), adding in order of q.
+__device__ __forceinline__ void tc_flush_rows(float (&v)[8], long long r8, long long r1, float *rp, int Q, int lane,
+                                              float *xb, int q, int wg)
 {
     const unsigned full = 0xffffffffu;
 #pragma unroll
@@ -332,14 +337,19 @@ __device__ __forceinline__ void tc_flush_rows(float (&v)[8], long long r8, long 
     }
     v[0] += __shfl_xor_sync(full, v[0], 2);
     v[0] += __shfl_xor_sync(full, v[0], 1);
-    if ((lane & 3) == 0) {
-        const long long row = r8 + ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-        if (row < r1) st_keep(rp + row * Q, v[0], l2_evict_last());
+    const int e = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    if ((lane & 3) == 0) xb[q * 8 + e] = v[0];
+    named_barrier_sync(1 + wg, 128);
+    if (q == 0 && (lane & 3) == 0) {
+        const long long row = r8 + e;
+        const float t = ((xb[e] + xb[8 + e]) + xb[16 + e]) + xb[24 + e];
+        if (row < r1) st_keep(rp + row * Q, t, l2_evict_last());
     }
 }
 
 // The same for 4 rows per warp (6 shuffles); entry e = 2*bit4 + bit3 is row r4 + e.
-__device__ __forceinline__ void tc_flush_rows(float (&v)[4], long long r4, long long r1, float *rp, int Q, int lane)
+__device__ __forceinline__ void tc_flush_rows(float (&v)[4], long long r4, long long r1, float *rp, int Q, int lane,
+                                              float *xb, int q, int wg)
 {
     const unsigned full = 0xffffffffu;
 #pragma unroll
@@ -356,9 +366,13 @@ __device__ __forceinline__ void tc_flush_rows(float (&v)[4], long long r4, long 
     v[0] += __shfl_xor_sync(full, v[0], 4);
     v[0] += __shfl_xor_sync(full, v[0], 2);
     v[0] += __shfl_xor_sync(full, v[0], 1);
-    if ((lane & 7) == 0) {
-        const long long row = r4 + ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
-        if (row < r1) st_keep(rp + row * Q, v[0], l2_evict_last());
+    const int e = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
+    if ((lane & 7) == 0) xb[q * 8 + e] = v[0];
+    named_barrier_sync(1 + wg, 128);
+    if (q == 0 && (lane & 7) == 0) {
+        const long long row = r4 + e;
+        const float t = ((xb[e] + xb[8 + e]) + xb[16 + e]) + xb[24 + e];
+        if (row < r1) st_keep(rp + row * Q, t, l2_evict_last());
     }
 }
 
@@ -771,7 +785,7 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
             const f2 ccol = f2_make(va ? __ldcg(P.ccol2 + col0) : 0.0f, vb ? __ldcg(P.ccol2 + col0 + 1) : 0.0f);
             const uint32_t hcol = hash_col((uint32_t)(col0 >> 1), rseed);
             const bool ragged = (s * kW + kW) > N;
-            float *rp = P.rowpart + (s * 4 + q);
+            float *rp = P.rowpart + s;   // one partial per (stripe, row), stored by warp q = 0
 #pragma unroll
             for (int j = 0; j < H2; ++j) d2acc[j] = 0.0f;
             for (long long r = r0; r < r1; r += RS, ++k, cpos.next()) {
@@ -847,7 +861,7 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
                     mbar_arrive(&B.a2full[b]);
                     mbar_arrive(&empty[slot]);
                 }
-                tc_flush_rows(rs, r + rb, ok ? r1 : r, rp, P.Q, lane);
+                tc_flush_rows(rs, r + rb, ok ? r1 : r, rp, P.Q, lane, &B.rowx[wg][k & 1][0][0], q, wg);
                 // the previous D2 chunk (its MMAs had a stage to finish), then mark this one
                 if (pending) {
                     flush_d2(pch);

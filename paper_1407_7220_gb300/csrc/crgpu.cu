@@ -787,7 +787,8 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
                ? 1
                : 0;
     if (P.tc) h->persistent_ok = false;   // the tensor-core pass runs in its own launch (phase driver)
-    P.Q = (int)(((P.tc ? 4 : 2) * S + 3) / 4 * 4);   // row partials per row: one per warp column slab
+    P.Q = (int)(((P.tc ? 1 : 2) * S + 3) / 4 * 4);   // row partials per row: one per warp column slab (CUDA
+                                                               // cores) or per stripe (tensor cores)
     P.cgroups = P.tc ? 1 : crk::kWR;
     P.G = G;
     P.total = total;
@@ -1250,7 +1251,7 @@ cr_status cr_promote(cr_handle h, int32_t theta_dtype)
         // colpart has 1 or kWR row groups; the next pair pass writes them before the fold reads them
         const long long S = P.S;
         P.tc = newtc;
-        P.Q = (int)(((P.tc ? 4 : 2) * S + 3) / 4 * 4);
+        P.Q = (int)(((P.tc ? 1 : 2) * S + 3) / 4 * 4);
         P.cgroups = P.tc ? 1 : crk::kWR;
         CR_TRY(dev_alloc(h, &P.rowpart, (size_t)P.Q * N));
         CR_TRY(dev_alloc(h, &P.colpart, (size_t)P.G * P.slots * P.cgroups * (h->NP + 1) * crk::kW));
