@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 from paper_1407_7220_gb300 import datagen  # noqa: E402
 
 RECIPE, N_DEF, n_DEF, GAMMA = "maxaff", 20000, 10, 1e-2
+STEPS_DEF = 2000   # the default timed iterations of the headline workload
 HBM_FALLBACK = 6800.0
 
 
@@ -447,26 +448,29 @@ def run_batch(args):
 
 
 def run_sumexp(args):
-    """Recipe (5): N=5000, n=5: 500 unrolled iterations (checkpoint every 50), forward and backward."""
+    """Recipe (5): N=5000, n=5: 500 unrolled iterations (checkpoint every 50), forward and backward.
+    --N, --steps and --record-every change the size (for a smaller ncu case of the same kernels)."""
     import torch
     import paper_1407_7220_gb300 as crg
     torch.cuda.set_device(0)
-    X, yb, f0 = datagen.make("sumexp", N=5000, n=5)
-    K, k = 500, 50
+    N = args.N if args.N != N_DEF else 5000
+    K = args.steps if args.steps != STEPS_DEF else 500
+    k = args.record_every
+    X, yb, f0 = datagen.make("sumexp", N=N, n=5)
     s = crg.Solver(X, yb, gamma=0.1, stochastic_round=0, restart=0, record_every=k)
     _, t_fwd = _sync_time(lambda: s.iterate(K))
     y, _ = s.solution()
     u = torch.tensor(2.0 * (y - f0), dtype=torch.float32, device="cuda")   # loss ||yhat - f0||^2
     dyb = torch.empty_like(u)
-    dX = torch.empty((5000, 5), dtype=torch.float32, device="cuda")
+    dX = torch.empty((N, 5), dtype=torch.float32, device="cuda")
     _, t_bwd = _sync_time(lambda: s.backward(u, dyb, dX))
-    pairs = 5000 * 4999
-    line = {"metric": "forward + backward time, 500 unrolled iterations", "value": t_fwd + t_bwd, "unit": "s",
+    pairs = N * (N - 1)
+    line = {"metric": f"forward + backward time, {K} unrolled iterations", "value": t_fwd + t_bwd, "unit": "s",
             "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
             "forward_s": t_fwd, "backward_s": t_bwd, "backward_over_forward": t_bwd / t_fwd,
             "forward_pair_updates_per_s": pairs * K / t_fwd,
             "grad_norms": {"dybar": float(dyb.norm()), "dX": float(dX.norm())},
-            "config": {"workload": "sumexp recipe N=5000 n=5 gamma=0.1, FP32 theta, checkpoint every 50, "
+            "config": {"workload": f"sumexp recipe N={N} n=5 gamma=0.1, FP32 theta, checkpoint every {k}, "
                                    "loss ||yhat - f0||^2"}}
     print(json.dumps(line))
 
@@ -640,7 +644,7 @@ def run_traces(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=STEPS_DEF)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--N", type=int, default=N_DEF)
@@ -655,6 +659,7 @@ def main():
     ap.add_argument("--batch-iters", type=int, default=20000)
     ap.add_argument("--batch-singles", type=int, default=64, help="fits of the batch also solved one by one")
     ap.add_argument("--blocks-N", type=int, default=2000)
+    ap.add_argument("--record-every", type=int, default=50, help="checkpoint interval of --config sumexp")
     ap.add_argument("--blocks-inner", type=int, default=20)
     ap.add_argument("--kkt-targets", default="0.3,0.2,0.1,0.07,0.05,0.03,0.02")
     ap.add_argument("--kkt-cap", type=int, default=20000, help="iteration cap of --config kkt")

@@ -183,6 +183,13 @@ cr_status cr_backward(cr_handle h, const float *dL_dyhat, float *dL_dybar, float
  * dual iterate, in FP64, to host buffers (either may be NULL).  Blocks. */
 cr_status cr_get_solution(cr_handle h, double *yhat, double *xi);
 
+/* The same values into caller-owned DEVICE buffers (yhat: N doubles, xi: N x n doubles,
+ * row-major; either may be NULL), written by a kernel on the handle's stream; returns after
+ * that stream has finished the copy, so the buffers may be used from any stream.  For callers
+ * that keep the fit on the device (the autograd binding) and would otherwise copy through the
+ * host.  The buffers must not overlap the handle's own state. */
+cr_status cr_get_solution_device(cr_handle h, double *yhat, double *xi);
+
 /* Iterations run since creation/reset, momentum restarts so far, the step constant L used,
  * and the shift s.  Any pointer may be NULL. */
 cr_status cr_get_info(cr_handle h, int64_t *iters, int64_t *restarts, double *L, double *shift);

@@ -50,7 +50,7 @@ exported_symbols = (
     "cr_batch_info", "cr_batch_destroy", "cr_batch_last_error", "cr_backward", "cr_get_engine",
     "cr_alcc_options_default", "cr_alcc_create", "cr_alcc_iterate", "cr_alcc_solve", "cr_alcc_metrics",
     "cr_alcc_info", "cr_problem_constants", "cr_batch_stats", "cr_promote", "cr_blocks_create",
-    "cr_blocks_iterate", "cr_blocks_solution",
+    "cr_blocks_iterate", "cr_blocks_solution", "cr_get_solution_device",
 )
 PROFILE_PAIR, PROFILE_FOLD, PROFILE_KKT, PROFILE_PERSISTENT = 0, 1, 2, 3
 
@@ -122,6 +122,8 @@ def lib():
             L.cr_objective.argtypes = [H, dp, dp, dp]
             L.cr_kkt_residual.argtypes = [H, dp, dp, dp]
             L.cr_get_solution.argtypes = [H, dp, dp]
+            L.cr_get_solution_device.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p]
+            L.cr_get_solution_device.restype = ctypes.c_int
             L.cr_get_info.argtypes = [H, i64p, i64p, dp, dp]
             L.cr_get_engine.argtypes = [H, ctypes.POINTER(ctypes.c_int32)]
             vpp = ctypes.POINTER(ctypes.c_void_p)
@@ -286,6 +288,15 @@ class Solver:
         xi = np.empty((self.N, self.n))
         self._check(lib().cr_get_solution(self._h, _dptr(y), _dptr(xi)))
         return y, xi
+
+    def solution_device(self, yhat=None, xi=None):
+        """cr_get_solution_device: the fit into device float64 torch tensors (N,) and (N, n)."""
+        for t, shape in ((yhat, (self.N,)), (xi, (self.N, self.n))):
+            if t is not None:
+                assert t.is_cuda and t.dtype == __import__("torch").float64 and t.is_contiguous()
+                assert tuple(t.shape) == shape
+        self._check(lib().cr_get_solution_device(self._h, ctypes.c_void_p(yhat.data_ptr() if yhat is not None else 0),
+                                                 ctypes.c_void_p(xi.data_ptr() if xi is not None else 0)))
 
     def info(self) -> dict:
         it, rs = ctypes.c_int64(), ctypes.c_int64()
@@ -540,10 +551,11 @@ def convex_fit(X, ybar, iters: int, record_every: int = 50, **opts):
         def forward(ctx, X_, y_):
             s = Solver(X_.detach(), y_.detach(), record_every=int(record_every), restart=0, **opts)
             s.iterate(int(iters))
-            yhat, _ = s.solution()
+            yhat = torch.empty(X_.shape[0], dtype=torch.float64, device=y_.device)
+            s.solution_device(yhat)   # device to device, no host round trip
             ctx.solver = s
             ctx.meta = (X_.shape, X_.dtype, y_.dtype)
-            return torch.as_tensor(yhat, device=y_.device).to(y_.dtype)
+            return yhat.to(y_.dtype)
 
         @staticmethod
         def backward(ctx, gy):

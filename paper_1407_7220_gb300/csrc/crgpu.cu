@@ -1401,6 +1401,35 @@ cr_status cr_get_solution(cr_handle h, double *yhat, double *xi)
     return CR_OK;
 }
 
+// yhat = y1 - s and xi = xi1 into caller device buffers (one thread per value, grid-stride).
+__global__ void k_solution_device(const double *__restrict__ y1, const double *__restrict__ xi1, double shift,
+                                  long long N, long long Nn, double *yhat, double *xi)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N + Nn;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (i < N) {
+            if (yhat) yhat[i] = y1[i] - shift;
+        } else if (xi) {
+            xi[i - N] = xi1[i - N];
+        }
+    }
+}
+
+cr_status cr_get_solution_device(cr_handle h, double *yhat, double *xi)
+{
+    CR_TRY(usable(h));
+    if (h->blocks) return fail(h, CR_ESTATE, "K-block handle: the primal point comes from cr_blocks_solution");
+    if (yhat || xi) {
+        const long long tot = h->N + h->N * (long long)h->n;
+        const int grid = (int)std::min<long long>((tot + 255) / 256, (long long)h->num_sms * 4);
+        k_solution_device<<<grid, 256, 0, h->stream>>>(h->P.y1, h->P.xi1_64, h->P.shift, h->N,
+                                                       h->N * (long long)h->n, yhat, xi);
+        CR_CUDA(h, cudaGetLastError());
+    }
+    CR_CUDA(h, cudaStreamSynchronize(h->stream));
+    return CR_OK;
+}
+
 cr_status cr_get_info(cr_handle h, int64_t *iters, int64_t *restarts, double *L, double *shift)
 {
     if (!h) return CR_EINVAL;

@@ -338,3 +338,18 @@ def test_ball_that_never_binds_changes_nothing(crg):
         crg.Solver(X, yb, theta_dtype="bf16", B_theta=1.0)
     with pytest.raises(crg.CrError):
         crg.Solver(X, yb, driver=crg.DRIVER_PERSISTENT, B_theta=1.0)
+
+
+def test_solution_device_matches_host_copy(crg):
+    # cr_get_solution_device writes the same FP64 values as cr_get_solution, on the device
+    import torch
+    X, yb, _ = datagen.make("sq2", N=333)
+    g = crg.Solver(X, yb, gamma=0.1)
+    g.iterate(17)
+    y, xi = g.solution()
+    yd = torch.empty(333, dtype=torch.float64, device="cuda")
+    xd = torch.empty((333, 2), dtype=torch.float64, device="cuda")
+    g.solution_device(yd, xd)
+    assert np.array_equal(yd.cpu().numpy(), y) and np.array_equal(xd.cpu().numpy(), xi)
+    g.solution_device(yd, None)   # either output may be omitted
+    assert np.array_equal(yd.cpu().numpy(), y)
