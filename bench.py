@@ -425,7 +425,7 @@ def run_batch(args):
                            "cap": args.batch_iters},
             "config": {"workload": f"batch recipe: {len(inst)} fits, N_i log-uniform [64, 4096], n_i in {{1,2,5}}, "
                                    "gamma=0.1, FP32 theta, plain P-APG"},
-            "clocks": clk.summary(), "graph": bs.stats()}
+            "clocks": clk.summary(), "graph": bs.stats(), "tuning": bs.tuning()}
     bs.close()
     if args.batch_singles > 0:
         # the same fits solved one by one (each its own handle and launches) against one batched

@@ -102,7 +102,9 @@ typedef struct {
     int32_t record_every;     /* > 0: cr_iterate keeps a checkpoint every this many iterations so that
                                  cr_backward can differentiate the unrolled iterations (FP32 theta, n <= 10) */
     int32_t pair_engine;      /* CR_PAIR_*: where the pair pass computes its two dense products */
-    int32_t reserved[3];
+    int32_t batch_stage_rows; /* batches only: rows per pipeline stage of the pair pass (the tile shape), 16
+                                 or 8; 0 (default): the batch autotuner picks one */
+    int32_t reserved[2];
     double restart_tol;       /* restart only when the dual value fell by more than restart_tol * |previous|
                                  (guards the test against rounding noise); default 1e-7 */
     double B_theta;           /* radius of the ball in Q_2 = {lambda >= 0, ||lambda||_2 <= B_theta} of Eq.
@@ -359,10 +361,18 @@ cr_status cr_batch_info(cr_batch_handle b, int32_t *factor, int32_t *grid, int64
 /* How the batch launches ran: *graph_live = 1 when the launch is held as an instantiated CUDA
  * graph (0 when capture of the cooperative launch was refused and the batch launches directly);
  * graph_launches / direct_launches count the launches of each kind so far; *tuned = candidates
- * the autotuner timed, tune_ms (nullable, room for 8) their milliseconds per iteration in the
- * order of the factors 1, 2, 4, 8, 16.  Any pointer may be NULL. */
+ * the autotuner timed, tune_ms (nullable, room for 8) the milliseconds per iteration of the first
+ * 8 of them (cr_batch_tuning lists every candidate).  Any pointer may be NULL. */
 cr_status cr_batch_stats(cr_batch_handle b, int32_t *graph_live, int64_t *graph_launches, int64_t *direct_launches,
                          int32_t *tuned, double *tune_ms);
+/* The batch autotuner's choice and measurements.  The candidates are the tile shapes (rows per
+ * pipeline stage of the pair pass: 16, then 8) times the work granularities (factors 1, 2, 4,
+ * 8, 16), each timed over a few iterations from the initial point; *stage_rows and *factor are
+ * the pair in use (the fastest, or the one the options fixed).  *count = candidates timed (0 when
+ * the options fixed both); the first min(count, cap) are written to cand_rows, cand_factor and
+ * cand_ms (milliseconds per iteration).  Any pointer may be NULL. */
+cr_status cr_batch_tuning(cr_batch_handle b, int32_t cap, int32_t *count, int32_t *stage_rows, int32_t *factor,
+                          int32_t *cand_rows, int32_t *cand_factor, double *cand_ms);
 void cr_batch_destroy(cr_batch_handle b);
 const char *cr_batch_last_error(cr_batch_handle b);
 

@@ -50,7 +50,7 @@ exported_symbols = (
     "cr_batch_info", "cr_batch_destroy", "cr_batch_last_error", "cr_backward", "cr_get_engine",
     "cr_alcc_options_default", "cr_alcc_create", "cr_alcc_iterate", "cr_alcc_solve", "cr_alcc_metrics",
     "cr_alcc_info", "cr_problem_constants", "cr_batch_stats", "cr_promote", "cr_blocks_create",
-    "cr_blocks_iterate", "cr_blocks_solution", "cr_get_solution_device",
+    "cr_blocks_iterate", "cr_blocks_solution", "cr_get_solution_device", "cr_batch_tuning",
 )
 PROFILE_PAIR, PROFILE_FOLD, PROFILE_KKT, PROFILE_PERSISTENT = 0, 1, 2, 3
 
@@ -64,7 +64,7 @@ class Options(ctypes.Structure):
         ("driver", ctypes.c_int32), ("grid", ctypes.c_int32), ("fp16_exponent", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("barrier_timeout_ms", ctypes.c_int32),
         ("test_barrier_extra", ctypes.c_int32), ("profile", ctypes.c_int32), ("record_every", ctypes.c_int32),
-        ("pair_engine", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
+        ("pair_engine", ctypes.c_int32), ("batch_stage_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
         ("restart_tol", ctypes.c_double), ("B_theta", ctypes.c_double),
     ]
 
@@ -143,6 +143,9 @@ def lib():
             L.cr_batch_stats.argtypes = [H, ctypes.POINTER(ctypes.c_int32), i64p, i64p, ctypes.POINTER(ctypes.c_int32),
                                          ctypes.POINTER(ctypes.c_double)]
             L.cr_batch_stats.restype = ctypes.c_int
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            L.cr_batch_tuning.argtypes = [H, ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, ctypes.POINTER(ctypes.c_double)]
+            L.cr_batch_tuning.restype = ctypes.c_int
             L.cr_batch_destroy.argtypes = [H]
             L.cr_batch_destroy.restype = None
             L.cr_batch_last_error.argtypes = [H]
@@ -523,7 +526,19 @@ class BatchSolver:
         self._check(lib().cr_batch_stats(self._h, ctypes.byref(live), ctypes.byref(gl), ctypes.byref(dl),
                                          ctypes.byref(nt), ms))
         return {"graph_live": bool(live.value), "graph_launches": gl.value, "direct_launches": dl.value,
-                "tune_ms": [ms[i] for i in range(nt.value)]}
+                "tuned": nt.value, "tune_ms": [ms[i] for i in range(min(nt.value, 8))]}
+
+    def tuning(self) -> dict:
+        """cr_batch_tuning: the tile shape and granularity in use and every autotuner candidate."""
+        cnt, rows, fac = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        cr = (ctypes.c_int32 * 16)()
+        cf = (ctypes.c_int32 * 16)()
+        cm = (ctypes.c_double * 16)()
+        self._check(lib().cr_batch_tuning(self._h, 16, ctypes.byref(cnt), ctypes.byref(rows), ctypes.byref(fac),
+                                          cr, cf, cm))
+        n = min(cnt.value, 16)
+        return {"stage_rows": rows.value, "factor": fac.value,
+                "candidates": [{"stage_rows": cr[i], "factor": cf[i], "ms": cm[i]} for i in range(n)]}
 
     def close(self):
         if getattr(self, "_h", None):

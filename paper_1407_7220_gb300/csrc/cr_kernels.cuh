@@ -40,6 +40,14 @@ constexpr int kRS = 16;         // rows per pipeline stage
 constexpr int kRPW = kRS / kWR; // rows of a stage per consumer warp
 constexpr int kSB = 8 / kRPW;   // stages per row-sum batch (8 row sums per warp)
 static_assert(kRS % kWR == 0 && 8 % kRPW == 0, "row split of a stage");
+// The CUDA-core pass is compiled for stages of RS rows (16 by default; the batched launch also
+// has 8-row stages, a tile shape its autotuner may pick): RPW rows per consumer warp, row sums
+// flushed every SB stages (8 per warp).
+template <int RS> struct StageRows {
+    static constexpr int RPW = RS / kWR;
+    static constexpr int SB = 8 / RPW;
+    static_assert(RS % kWR == 0 && RPW >= 1 && 8 % RPW == 0, "row split of a stage");
+};
 constexpr int kMaxStages = 16;
 constexpr size_t kSmemBudget = 227 * 1024 - 2048;   // dynamic shared memory per CTA (static arrays excluded)
 
@@ -81,6 +89,7 @@ struct DevState {
 struct Params {
     CUtensorMap tmap[2];    // TMA descriptors of theta[0], theta[1]: N x N, box kRS x kW
     CUtensorMap tmap32[2];  // the same with a box of 32 rows (tensor-core pass, 16-bit theta)
+    CUtensorMap tmap8[2];   // the same with a box of 8 rows (8-row stages of the batched launch)
     // sizes
     long long N;
     int n;
@@ -809,10 +818,10 @@ __device__ void phase_foldB(const Params &P, long long ell, double *red, long lo
 // nothing stored (MAPG gradient), and theta <- a m stored in place (Fig. `fig:alcc` step 4).
 enum PairMode : int { PM_PAPG = 0, PM_ALCC_GRAD = 1, PM_ALCC_UPDATE = 2 };
 
-template <typename TS, int NP, int TILES = 2> struct PairSmem {
+template <typename TS, int NP, int TILES = 2, int RS = kRS> struct PairSmem {
     static constexpr int REC = RecLayout<NP>::REC;
-    static constexpr size_t tile_bytes = (size_t)kRS * kW * sizeof(TS);
-    static constexpr size_t rec_bytes = (size_t)kRS * REC * sizeof(float);
+    static constexpr size_t tile_bytes = (size_t)RS * kW * sizeof(TS);
+    static constexpr size_t rec_bytes = (size_t)RS * REC * sizeof(float);
     static constexpr size_t stage_bytes = TILES * tile_bytes + rec_bytes;
     // as many stages as fit (more bytes in flight per SM)
     static constexpr int kFit = (int)((kSmemBudget - 128) / stage_bytes);
@@ -841,20 +850,20 @@ static __device__ __noinline__ double alcc_exact_margin(const Params &P, long lo
 // The arithmetic of every pair is the scalar expression order of Step 2 (two chains of the
 // xi.x product, even and odd k), so the residual and the projection mask are reproducible
 // by a scalar evaluation.
-template <typename TS, int NP, bool MASK, bool SR, int MODE>
+template <typename TS, int NP, bool MASK, bool SR, int MODE, int RPW = kRPW>
 __device__ __forceinline__ void pair_stage_rows(const TS *tcur, const TS *tprv, const float *rec, int rg, int cofs,
                                                 long long r, long long r1, long long col0, long long N, long long ld,
                                                 const f2 (&ccol)[2], const f2 (&nxi)[2][NP], f2 (&acc)[2][NP],
                                                 f2 (&csum)[2], f2 beta2, f2 ninvL2, float invL, uint32_t hcol,
                                                 float scl, float iscl, f2 iscl2, TS *__restrict__ nxt, bool vec_ok,
-                                                float (&rsv)[kRPW], const Params &Pm, const f2 (&cbnd)[2])
+                                                float (&rsv)[RPW], const Params &Pm, const f2 (&cbnd)[2])
 {
     using St = Store<TS>;
     using Vec = typename St::Vec;
     constexpr int REC = RecLayout<NP>::REC;
     const f2 zero2 = 0ull;
 #pragma unroll
-    for (int i = 0; i < kRPW; ++i) {
+    for (int i = 0; i < RPW; ++i) {
         const int rl = rg + i * kWR;
         const long long rr = r + rl;
         const bool valid = !MASK || rr < r1;
@@ -941,9 +950,11 @@ __device__ __forceinline__ void pair_stage_rows(const TS *tcur, const TS *tprv, 
 // transposing butterfly: 9 shuffles leave the full sum of batch entry
 // e = 4*bit4 + 2*bit3 + bit2 (of the lane id) in every lane.  Entry e is row
 // r_last - kRS*(kSB - 1 - e/kRPW) + rg + kWR*(e % kRPW); only the nb most recent stages are written.
+template <int RS = kRS>
 __device__ __forceinline__ void flush_row_sums(float (&v)[8], int nb, long long r_last, int rg, long long r1,
                                                float *rp, int Q, int lane, uint64_t pol)
 {
+    constexpr int RPW = StageRows<RS>::RPW, SB = StageRows<RS>::SB;
     const unsigned full = 0xffffffffu;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -966,9 +977,9 @@ __device__ __forceinline__ void flush_row_sums(float (&v)[8], int nb, long long 
     v[0] += __shfl_xor_sync(full, v[0], 1);
     if ((lane & 3) == 0) {
         const int e = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-        const int sp = e / kRPW;
-        const long long row = r_last - (long long)kRS * (kSB - 1 - sp) + rg + kWR * (e % kRPW);
-        if (sp >= kSB - nb && row < r1) st_keep(rp + row * Q, v[0], pol);
+        const int sp = e / RPW;
+        const long long row = r_last - (long long)RS * (SB - 1 - sp) + rg + kWR * (e % RPW);
+        if (sp >= SB - nb && row < r1) st_keep(rp + row * Q, v[0], pol);
     }
 }
 
@@ -1023,20 +1034,21 @@ template <int S> struct RingPos {
 // Issue the stage at ring position pos: unless this is the slot's first use (reuse false),
 // wait until its previous occupant (S stages earlier) was released by all 8 warps, then
 // two tiled TMA loads and one bulk copy complete on the slot's "full" barrier.
-template <typename TS, int NP, int MODE>
+template <typename TS, int NP, int MODE, int RS = kRS>
 __device__ __forceinline__ bool produce_stage(const Params &P, unsigned char *stage0, uint64_t *full, uint64_t *empty,
-                                              const RingPos<PairSmem<TS, NP, MODE == PM_PAPG ? 2 : 1>::kStages> &pos,
-                                              bool reuse, const StageCursor &cur, int c, int p)
+                                              const RingPos<PairSmem<TS, NP, MODE == PM_PAPG ? 2 : 1, RS>::kStages> &pos,
+                                              bool reuse, const StageCursorT<RS> &cur, int c, int p)
 {
     constexpr int TILES = MODE == PM_PAPG ? 2 : 1;
-    using L = PairSmem<TS, NP, TILES>;
+    using L = PairSmem<TS, NP, TILES, RS>;
+    const CUtensorMap *tm = RS == kRS ? P.tmap : P.tmap8;   // box of RS rows
     const int slot = pos.slot;
     if (reuse && !mbar_wait(P, &empty[slot], pos.phase ^ 1u)) return false;
-    const int nrows = (int)min((long long)kRS, cur.r1 - cur.r);
+    const int nrows = (int)min((long long)RS, cur.r1 - cur.r);
     unsigned char *st = stage0 + slot * L::stage_bytes;
     mbar_arrive_expect_tx(&full[slot], (uint32_t)(TILES * L::tile_bytes + (size_t)nrows * L::REC * 4));
-    tma_load_2d(st, &P.tmap[c], (int)(cur.s * kW), (int)cur.r, &full[slot]);
-    if (TILES == 2) tma_load_2d(st + L::tile_bytes, &P.tmap[p], (int)(cur.s * kW), (int)cur.r, &full[slot]);
+    tma_load_2d(st, &tm[c], (int)(cur.s * kW), (int)cur.r, &full[slot]);
+    if (TILES == 2) tma_load_2d(st + L::tile_bytes, &tm[p], (int)(cur.s * kW), (int)cur.r, &full[slot]);
     bulk_load(st + TILES * L::tile_bytes, P.rowrec + cur.r * L::REC, (uint32_t)(nrows * L::REC * 4), &full[slot]);
     return true;
 }
@@ -1046,11 +1058,11 @@ template <int NP> __device__ void phase_pair_f64(const Params &P, long long ell,
 
 // MODE = PM_PAPG: Step 2 of P-APG at iteration ell.  The ALCC modes read and write array 0 only;
 // a = mu_k / mu_{k+1} scales the stored values of PM_ALCC_UPDATE.
-template <typename TS, int NP, int MODE = PM_PAPG>
+template <typename TS, int NP, int MODE = PM_PAPG, int RS = kRS>
 __device__ void phase_pair_stream(const Params &P, long long ell, unsigned char *smem, uint64_t *full,
                                   uint64_t *empty, unsigned long long &kstage, long long vc, float a = 1.0f);
 
-template <typename TS, int NP, int MODE = PM_PAPG>
+template <typename TS, int NP, int MODE = PM_PAPG, int RS = kRS>
 __device__ __forceinline__ void phase_pair(const Params &P, long long ell, unsigned char *smem, uint64_t *full,
                                            uint64_t *empty, unsigned long long &kstage, long long vc, float a = 1.0f)
 {
@@ -1058,18 +1070,19 @@ __device__ __forceinline__ void phase_pair(const Params &P, long long ell, unsig
         static_assert(MODE == PM_PAPG, "FP64 multipliers: P-APG only");
         phase_pair_f64<NP>(P, ell, smem, vc);
     } else {
-        phase_pair_stream<TS, NP, MODE>(P, ell, smem, full, empty, kstage, vc, a);
+        phase_pair_stream<TS, NP, MODE, RS>(P, ell, smem, full, empty, kstage, vc, a);
     }
 }
 
-template <typename TS, int NP, int MODE>
+template <typename TS, int NP, int MODE, int RS>
 __device__ void phase_pair_stream(const Params &P, long long ell, unsigned char *smem, uint64_t *full,
                                   uint64_t *empty, unsigned long long &kstage, long long vc, float a)
 {
     using St = Store<TS>;
     constexpr int TILES = MODE == PM_PAPG ? 2 : 1;
-    using L = PairSmem<TS, NP, TILES>;
+    using L = PairSmem<TS, NP, TILES, RS>;
     constexpr int S = L::kStages;
+    constexpr int RPW = StageRows<RS>::RPW, SB = StageRows<RS>::SB;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int p = MODE == PM_PAPG ? (int)(ell & 1) : 0, c = MODE == PM_PAPG ? 1 - p : 0;
     const long long N = P.N, ld = P.ld;
@@ -1081,14 +1094,14 @@ __device__ void phase_pair_stream(const Params &P, long long ell, unsigned char 
     unsigned long long nst = 0;
     for (long long u = ubeg; u < uend;) {
         const long long s = u / N, r0 = u - s * N, r1 = min(N, r0 + (uend - u));
-        nst += (unsigned long long)((r1 - r0 + kRS - 1) / kRS);
+        nst += (unsigned long long)((r1 - r0 + RS - 1) / RS);
         u += r1 - r0;
     }
     const unsigned long long kend = kstage + nst;
 
     // producer (lane 0 of warp 0): prefill the ring
     const bool producer = (tid == 0);
-    StageCursor pc;
+    StageCursorT<RS> pc;
     unsigned long long kprod = kstage;
     RingPos<S> ppos;
     bool pok = true;
@@ -1097,7 +1110,7 @@ __device__ void phase_pair_stream(const Params &P, long long ell, unsigned char 
         pc.begin(ubeg, uend, N);
         ppos.init(kprod);
         for (; kprod < kend && kprod < kstage + S && pok; ++kprod) {
-            pok = produce_stage<TS, NP, MODE>(P, stage0, full, empty, ppos, kprod >= (unsigned long long)S, pc, c, p);
+            pok = produce_stage<TS, NP, MODE, RS>(P, stage0, full, empty, ppos, kprod >= (unsigned long long)S, pc, c, p);
             pc.advance(N);
             ppos.next();
         }
@@ -1167,47 +1180,47 @@ __device__ void phase_pair_stream(const Params &P, long long ell, unsigned char 
 #pragma unroll
         for (int q = 0; q < 8; ++q) rsb[q] = 0.0f;
         int nb = 0;
-        for (long long r = r0; r < r1; r += kRS, cpos.next()) {
+        for (long long r = r0; r < r1; r += RS, cpos.next()) {
             const int slot = cpos.slot;
             if (ok && !mbar_wait(P, &full[slot], cpos.phase)) ok = false;
-            float rsn[kRPW];
+            float rsn[RPW];
 #pragma unroll
-            for (int i = 0; i < kRPW; ++i) rsn[i] = 0.0f;
+            for (int i = 0; i < RPW; ++i) rsn[i] = 0.0f;
             if (ok) {
                 const unsigned char *st = stage0 + slot * L::stage_bytes;
                 const TS *tcur = reinterpret_cast<const TS *>(st);
                 const TS *tprv = reinterpret_cast<const TS *>(st + (TILES - 1) * L::tile_bytes);   // unused by the ALCC modes
                 const float *rec = reinterpret_cast<const float *>(st + TILES * L::tile_bytes);
-                const bool fast = !ragged && (r + kRS <= r1) && !(r < colw + 128 && colw < r + kRS);
+                const bool fast = !ragged && (r + RS <= r1) && !(r < colw + 128 && colw < r + RS);
                 if (sr) {
                     if (fast)
-                        pair_stage_rows<TS, NP, false, true, MODE>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn, P, cbnd);
+                        pair_stage_rows<TS, NP, false, true, MODE, RPW>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn, P, cbnd);
                     else
-                        pair_stage_rows<TS, NP, true, true, MODE>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn, P, cbnd);
+                        pair_stage_rows<TS, NP, true, true, MODE, RPW>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn, P, cbnd);
                 } else {
                     if (fast)
-                        pair_stage_rows<TS, NP, false, false, MODE>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn, P, cbnd);
+                        pair_stage_rows<TS, NP, false, false, MODE, RPW>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn, P, cbnd);
                     else
-                        pair_stage_rows<TS, NP, true, false, MODE>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn, P, cbnd);
+                        pair_stage_rows<TS, NP, true, false, MODE, RPW>(tcur, tprv, rec, rg, cofs, r, r1, col0, N, ld, ccol, nxi, acc, csum, beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nxt, vec_ok, rsn, P, cbnd);
                 }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[slot]);
             if (producer && pok && kprod < kend) {   // refill this slot with the stage S ahead
-                pok = produce_stage<TS, NP, MODE>(P, stage0, full, empty, ppos, kprod >= (unsigned long long)S, pc, c, p);
+                pok = produce_stage<TS, NP, MODE, RS>(P, stage0, full, empty, ppos, kprod >= (unsigned long long)S, pc, c, p);
                 pc.advance(N);
                 ppos.next();
                 ++kprod;
             }
             __syncwarp();   // reconverge warp 0 after the producer lane
-            // shift the row-sum batch (most recent stage in the last kRPW entries)
+            // shift the row-sum batch (most recent stage in the last RPW entries)
 #pragma unroll
-            for (int q = 0; q < 8 - kRPW; ++q) rsb[q] = rsb[q + kRPW];
+            for (int q = 0; q < 8 - RPW; ++q) rsb[q] = rsb[q + RPW];
 #pragma unroll
-            for (int i = 0; i < kRPW; ++i) rsb[8 - kRPW + i] = rsn[i];
+            for (int i = 0; i < RPW; ++i) rsb[8 - RPW + i] = rsn[i];
             ++nb;
-            if (nb == kSB || r + kRS >= r1) {
-                flush_row_sums(rsb, nb, r, rg, r1, rp, P.Q, lane, keep);
+            if (nb == SB || r + RS >= r1) {
+                flush_row_sums<RS>(rsb, nb, r, rg, r1, rp, P.Q, lane, keep);
 #pragma unroll
                 for (int q = 0; q < 8; ++q) rsb[q] = 0.0f;
                 nb = 0;

@@ -211,7 +211,7 @@ struct BatchArgs {
     int B;
 };
 
-template <typename TS, int NP>
+template <typename TS, int NP, int RS = kRS>
 __global__ void __launch_bounds__(kThreads, 1)
 k_batch(const __grid_constant__ BatchArgs A, long long chunk, int check_every, double tol)
 {
@@ -239,7 +239,7 @@ k_batch(const __grid_constant__ BatchArgs A, long long chunk, int check_every, d
     CR_ITEMS(phase_foldB<NP>(P, ell0, red, vc));
     CR_BAR();
     for (long long ell = ell0; ell <= ell1; ++ell) {
-        CR_ITEMS(phase_pair<TS, NP>(P, ell, sm, full, empty, kstage, vc));
+        CR_ITEMS((phase_pair<TS, NP, PM_PAPG, RS>(P, ell, sm, full, empty, kstage, vc)));
         CR_BAR();
         CR_ITEMS(phase_foldA<NP>(P, ell, red, vc));
         CR_BAR();
@@ -317,7 +317,8 @@ struct KernelSet {
     const void *pair_tc;
     const void *kkt64_if;
     const void *batch;
-    size_t smem;
+    const void *batch8;                            // the batched launch with 8-row stages
+    size_t smem, smem_batch8;
     int NP;
     BwdKernels bwd;
     const void *blocks_prepare, *blocks_records;   // K-block P-APG (FP64 multipliers only)
@@ -336,15 +337,18 @@ template <typename TS, int NP> KernelSet make_set()
     if constexpr (std::is_same<TS, double>::value) {
         k.pair_tc = nullptr;   // FP64 multipliers: CUDA cores only, single instances only
         k.batch = nullptr;
+        k.batch8 = nullptr;
         k.blocks_prepare = (const void *)k_blocks_prepare<NP>;
         k.blocks_records = (const void *)k_blocks_records<NP>;
     } else {
         k.pair_tc = (const void *)k_pair_tc<TS, NP>;
         k.batch = (const void *)k_batch<TS, NP>;
+        k.batch8 = (const void *)k_batch<TS, NP, 8>;
         k.blocks_prepare = nullptr;
         k.blocks_records = nullptr;
     }
     k.smem = pair_smem_bytes<TS, NP>();
+    k.smem_batch8 = PairSmem<TS, NP, 2, 8>::bytes;
     k.NP = NP;
     k.bwd = make_bwd<TS, NP>();
     return k;

@@ -855,6 +855,11 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
         r = encode(&P.tmap32[b], tdt, 2, P.theta[b], gdim, gstride, box32, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(h, CR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        // 8-row boxes for the 8-row stages of the batched launch
+        cuuint32_t box8[2] = {(cuuint32_t)crk::kW, 8u};
+        r = encode(&P.tmap8[b], tdt, 2, P.theta[b], gdim, gstride, box8, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(h, CR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     }
     const int REC = rec_floats(h->NP);
     double *X64, *hh;
@@ -1236,6 +1241,7 @@ cr_status cr_promote(cr_handle h, int32_t theta_dtype)
         cuuint64_t gdim[2] = {(cuuint64_t)N, (cuuint64_t)N};
         cuuint64_t gstride[1] = {(cuuint64_t)h->ld * 4};
         cuuint32_t box[2] = {(cuuint32_t)crk::kW, (cuuint32_t)crk::kRS}, box32[2] = {(cuuint32_t)crk::kW, 32u};
+        cuuint32_t box8[2] = {(cuuint32_t)crk::kW, 8u};
         cuuint32_t estr[2] = {1, 1};
         CUresult r = encode(&P.tmap[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, P.theta[b], gdim, gstride, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -1244,10 +1250,14 @@ cr_status cr_promote(cr_handle h, int32_t theta_dtype)
             r = encode(&P.tmap32[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, P.theta[b], gdim, gstride, box32, estr,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS)
+            r = encode(&P.tmap8[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, P.theta[b], gdim, gstride, box8, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(h, CR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     }
     if (newtc != P.tc) {
-        // the partial-sum layouts of the two engines differ: rowpart is 4S (tensor cores) or 2S wide,
+        // the partial-sum layouts of the two engines differ: rowpart is S (tensor cores) or 2S wide,
         // colpart has 1 or kWR row groups; the next pair pass writes them before the fold reads them
         const long long S = P.S;
         P.tc = newtc;
@@ -1907,10 +1917,14 @@ struct cr_batch_ctx {
     long long graph_launches = 0;     // launches replayed from the captured CUDA graph
     long long direct_launches = 0;    // launches made directly (capture not available)
     int factor = 1;                   // work granularity chosen by the autotuner
+    int stage_rows = crk::kRS;        // rows per pipeline stage of the pair pass (16 or 8): tile shape
     long long iters = 0;
     std::string err;
     std::vector<double> tune_ms;      // autotuner measurements (ms per iteration) per candidate
     std::vector<int> tune_factor;
+    std::vector<int> tune_rows;
+    const void *kernel() const { return stage_rows == 8 ? ks.batch8 : ks.batch; }
+    size_t smem() const { return stage_rows == 8 ? ks.smem_batch8 : ks.smem; }
 };
 
 namespace {
@@ -2036,7 +2050,7 @@ cr_status batch_launch(cr_batch_ctx *b, long long chunk, int check_every, double
         bool ok = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
         if (ok) {
             cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned long long), b->stream);
-            cudaLaunchCooperativeKernel(b->ks.batch, dim3(b->Gphys), dim3(crk::kThreads), args, b->ks.smem, b->stream);
+            cudaLaunchCooperativeKernel(b->kernel(), dim3(b->Gphys), dim3(crk::kThreads), args, b->smem(), b->stream);
             ok = cudaStreamEndCapture(b->stream, &g) == cudaSuccess && g;
         }
         if (ok) ok = cudaGraphInstantiate(&b->gexec, g, 0) == cudaSuccess;
@@ -2057,7 +2071,7 @@ cr_status batch_launch(cr_batch_ctx *b, long long chunk, int check_every, double
     } else {
         ++b->direct_launches;
         CR_BCUDA(b, cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned long long), b->stream));
-        CR_BCUDA(b, cudaLaunchCooperativeKernel(b->ks.batch, dim3(b->Gphys), dim3(crk::kThreads), args, b->ks.smem,
+        CR_BCUDA(b, cudaLaunchCooperativeKernel(b->kernel(), dim3(b->Gphys), dim3(crk::kThreads), args, b->smem(),
                                                 b->stream));
     }
     return CR_OK;
@@ -2073,35 +2087,45 @@ cr_status batch_sync_error(cr_batch_ctx *b)
     return CR_OK;
 }
 
-// Autotuner: times `probe` iterations for each work granularity and keeps the fastest.
-cr_status batch_autotune(cr_batch_ctx *b, int probe)
+// Autotuner: times `probe` iterations for every tile shape (rows per pipeline stage: 16, or 8,
+// which wastes fewer rows at the ragged end of a small instance's segments) and work granularity,
+// and keeps the fastest pair.
+cr_status batch_autotune(cr_batch_ctx *b, int probe, int fixed_rows)
 {
     cudaEvent_t e0, e1;
     CR_BCUDA(b, cudaEventCreate(&e0));
     CR_BCUDA(b, cudaEventCreate(&e1));
     double best = 1e300;
-    int bestf = 1;
+    int bestf = 1, bestr = crk::kRS;
     b->tune_ms.clear();
     b->tune_factor.clear();
-    for (int f : kTuneFactors) {
-        CR_TRY(batch_plan(b, f));
-        CR_TRY(batch_reset(b));
-        CR_TRY(batch_launch(b, 2, 0, -1.0));   // warm-up
-        CR_BCUDA(b, cudaEventRecord(e0, b->stream));
-        CR_TRY(batch_launch(b, probe, 0, -1.0));
-        CR_BCUDA(b, cudaEventRecord(e1, b->stream));
-        CR_TRY(batch_sync_error(b));
-        float ms = 0.0f;
-        CR_BCUDA(b, cudaEventElapsedTime(&ms, e0, e1));
-        b->tune_ms.push_back(ms / probe);
-        b->tune_factor.push_back(f);
-        if (ms < best) {
-            best = ms;
-            bestf = f;
+    b->tune_rows.clear();
+    for (int rows : {crk::kRS, 8}) {
+        if (fixed_rows != 0 && rows != fixed_rows) continue;
+        b->stage_rows = rows;
+        for (int f : kTuneFactors) {
+            CR_TRY(batch_plan(b, f));
+            CR_TRY(batch_reset(b));
+            CR_TRY(batch_launch(b, 2, 0, -1.0));   // warm-up
+            CR_BCUDA(b, cudaEventRecord(e0, b->stream));
+            CR_TRY(batch_launch(b, probe, 0, -1.0));
+            CR_BCUDA(b, cudaEventRecord(e1, b->stream));
+            CR_TRY(batch_sync_error(b));
+            float ms = 0.0f;
+            CR_BCUDA(b, cudaEventElapsedTime(&ms, e0, e1));
+            b->tune_ms.push_back(ms / probe);
+            b->tune_factor.push_back(f);
+            b->tune_rows.push_back(rows);
+            if (ms < best) {
+                best = ms;
+                bestf = f;
+                bestr = rows;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    b->stage_rows = bestr;
     CR_TRY(batch_plan(b, bestf));
     return batch_reset(b);
 }
@@ -2134,7 +2158,7 @@ cr_status cr_batch_create(int32_t B, const int64_t *N, const int32_t *n, const d
         cr_batch_destroy(b);
         return s;
     };
-    if (!b->ks.batch) return cleanup(create_error(CR_EINVAL, "no kernel for this dtype / n"));
+    if (!b->ks.batch || !b->ks.batch8) return cleanup(create_error(CR_EINVAL, "no kernel for this dtype / n"));
     if (o.stream) {
         b->stream = (cudaStream_t)o.stream;
     } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -2175,13 +2199,16 @@ cr_status cr_batch_create(int32_t B, const int64_t *N, const int32_t *n, const d
         }
     }
     // physical grid: every co-resident CTA of the batch kernel
-    int dev = 0, sms = 0, per_sm = 0;
+    // (both tile shapes: the smaller co-resident count of the two)
+    int dev = 0, sms = 0, per_sm = 0, per_sm8 = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaFuncSetAttribute(b->ks.batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->ks.smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b->ks.batch, crk::kThreads, b->ks.smem) != cudaSuccess ||
-        per_sm < 1)
+        cudaFuncSetAttribute(b->ks.batch8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->ks.smem_batch8) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm8, b->ks.batch8, crk::kThreads, b->ks.smem_batch8) != cudaSuccess ||
+        std::min(per_sm, per_sm8) < 1)
         return cleanup(create_error(CR_ECUDA, "batch kernel does not fit on this device"));
-    b->Gphys = sms * per_sm;
+    b->Gphys = sms * std::min(per_sm, per_sm8);
     long long nitems = 0;
     for (long long g : b->Gfine) nitems += g;
     auto balloc = [&](void **p, size_t bytes) {
@@ -2194,7 +2221,10 @@ cr_status cr_batch_create(int32_t B, const int64_t *N, const int32_t *n, const d
         !balloc((void **)&b->d_active, sizeof(int) * B) || !balloc((void **)&b->d_ell, sizeof(long long)) ||
         !balloc((void **)&b->d_bar, sizeof(unsigned long long)) || !balloc((void **)&b->d_err, sizeof(int)))
         return cleanup(create_error(CR_ENOMEM, "batch descriptors"));
-    cr_status s = (o.grid > 0) ? batch_plan(b, std::max(1, o.grid)) : batch_autotune(b, 8);
+    if (o.batch_stage_rows != 0 && o.batch_stage_rows != 8 && o.batch_stage_rows != crk::kRS)
+        return cleanup(create_error(CR_EINVAL, "batch_stage_rows must be 0 (autotuned), 8 or 16"));
+    if (o.batch_stage_rows != 0) b->stage_rows = o.batch_stage_rows;
+    cr_status s = (o.grid > 0) ? batch_plan(b, std::max(1, o.grid)) : batch_autotune(b, 8, o.batch_stage_rows);
     if (s == CR_OK && o.grid > 0) s = batch_reset(b);
     if (s != CR_OK) return cleanup(create_error(s, b->err.c_str()));
     *out = b;
@@ -2279,7 +2309,22 @@ cr_status cr_batch_stats(cr_batch_handle b, int32_t *graph_live, int64_t *graph_
     if (direct_launches) *direct_launches = b->direct_launches;
     if (tuned) *tuned = (int32_t)b->tune_factor.size();
     if (tune_ms)
-        for (size_t i = 0; i < b->tune_ms.size(); ++i) tune_ms[i] = b->tune_ms[i];
+        for (size_t i = 0; i < b->tune_ms.size() && i < 8; ++i) tune_ms[i] = b->tune_ms[i];
+    return CR_OK;
+}
+
+cr_status cr_batch_tuning(cr_batch_handle b, int32_t cap, int32_t *count, int32_t *stage_rows, int32_t *factor,
+                          int32_t *cand_rows, int32_t *cand_factor, double *cand_ms)
+{
+    if (!b || cap < 0) return CR_EINVAL;
+    if (stage_rows) *stage_rows = b->stage_rows;
+    if (factor) *factor = b->factor;
+    if (count) *count = (int32_t)b->tune_ms.size();
+    for (size_t i = 0; i < b->tune_ms.size() && (int32_t)i < cap; ++i) {
+        if (cand_rows) cand_rows[i] = b->tune_rows[i];
+        if (cand_factor) cand_factor[i] = b->tune_factor[i];
+        if (cand_ms) cand_ms[i] = b->tune_ms[i];
+    }
     return CR_OK;
 }
 

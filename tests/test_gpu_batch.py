@@ -78,4 +78,36 @@ def test_batch_runs_from_its_cuda_graph_and_autotunes():
     st = bs.stats()
     print(st)
     assert st["graph_live"] and st["graph_launches"] >= 2 and st["direct_launches"] == 0
-    assert len(st["tune_ms"]) == 5 and min(st["tune_ms"]) > 0.0
+    assert st["tuned"] == 10 and len(st["tune_ms"]) == 8 and min(st["tune_ms"]) > 0.0
+
+
+def test_batch_tile_shapes_give_the_same_trajectories():
+    # 8-row and 16-row stages visit the same pairs and add every row and column partial in the
+    # same order, so the batched trajectories agree bit for bit
+    import paper_1407_7220_gb300 as crg
+    inst = _instances(SIZES, seed=11)
+    fits = {}
+    for rows in (16, 8):
+        bs = crg.BatchSolver(inst, gamma=0.1, stochastic_round=1, restart=0, grid=2, batch_stage_rows=rows)
+        assert bs.tuning()["stage_rows"] == rows
+        bs.iterate(25)
+        fits[rows] = [bs.member(i).solution()[0] for i in range(len(inst))]
+        bs.close()
+    for a, b in zip(fits[16], fits[8]):
+        assert np.array_equal(a, b)
+
+
+def test_batch_autotuner_times_tile_shapes_and_granularities():
+    import paper_1407_7220_gb300 as crg
+    inst = _instances(SIZES, seed=3)
+    bs = crg.BatchSolver(inst, gamma=0.1, stochastic_round=0, restart=0)
+    t = bs.tuning()
+    print(t)
+    cands = t["candidates"]
+    assert len(cands) == 10
+    assert {c["stage_rows"] for c in cands} == {8, 16}
+    assert {c["factor"] for c in cands} == {1, 2, 4, 8, 16}
+    best = min(cands, key=lambda c: c["ms"])
+    assert (t["stage_rows"], t["factor"]) == (best["stage_rows"], best["factor"])
+    with pytest.raises(crg.CrError):
+        crg.BatchSolver(inst, gamma=0.1, batch_stage_rows=12)
