@@ -140,6 +140,8 @@ struct Params {
     // subgradient offset (xi = xi_off + A_2^T theta / gamma) and no y >= 0 rows
     const int *blk;
     int blkmode;
+    const long long *band;  // K blocks, pairs inside blocks (points sorted by block): rows [band[2s],
+                            // band[2s+1]) of stripe s hold every such pair of its columns; nullptr: all rows
     const double *xi_off;
     int no_mu;
     // Q_2 with a finite ball ||lambda||_2 <= B_theta (Eq. (lambda_dual)): per-CTA partial sums

@@ -55,7 +55,11 @@ template <int NP> __device__ void phase_pair_f64(const Params &P, long long ell,
             }
         }
         double *rp = P.rowpart64 + (s * 2 + wc);   // row r's partial at rp[r * Q]
-        for (long long r = r0 + rg; r < r1; r += kWR) {
+        // pairs inside the blocks only: the rows of the stripe's band (the other rows' partials
+        // stay 0; the column partials of the segment are written either way)
+        const long long rb0 = P.band ? max(r0, __ldg(P.band + 2 * s)) : r0;
+        const long long rb1 = P.band ? min(r1, __ldg(P.band + 2 * s + 1)) : r1;
+        for (long long r = rb0 + rg; r < rb1; r += kWR) {
             const int brow = P.blkmode ? __ldg(P.blk + r) : -2;
             const double *rec = P.rec64 + r * REC;
             const double yr = __ldcg(rec);

@@ -111,6 +111,7 @@ struct cr_ctx {
     int inner_iters = 0;
     int K = 0;
     double *b_a = nullptr, *b_b = nullptr, *b_mu2 = nullptr;   // a, b of Step 1's block problems; mu^(2)
+    std::vector<long long> perm;      // handle order q holds the caller's point perm[q] (sorted by block)
 };
 
 namespace {
@@ -330,13 +331,13 @@ size_t partition_entries(long long G, long long S) { return (size_t)(2 * G + 1 +
 //   cfs[c], c < G: first stripe of CTA c, or -1 for a CTA without units;
 //   sc0[s], sc1[s], s < S: the CTAs [sc0, sc1) whose unit ranges meet stripe s (the folds add
 //   their column partials in this ascending order).
-cr_status upload_partition(cr_ctx *h, long long *dtab)
+cr_status upload_partition(cr_ctx *h, long long *dtab, const std::vector<long long> *ubeg = nullptr)
 {
     Params &P = h->P;
     const long long G = P.G, N = P.N, S = P.S;
     std::vector<long long> t(partition_entries(G, S), 0);
     long long *ub = t.data(), *cfs = ub + G + 1, *sc0 = cfs + G, *sc1 = sc0 + S;
-    for (long long c = 0; c <= G; ++c) ub[c] = unit_begin_host(c, P.total, N, (int)G);
+    for (long long c = 0; c <= G; ++c) ub[c] = ubeg ? (*ubeg)[c] : unit_begin_host(c, P.total, N, (int)G);
     for (long long s = 0; s < S; ++s) {
         sc0[s] = G;
         sc1[s] = 0;
@@ -1796,12 +1797,24 @@ cr_status cr_blocks_create(const double *X, const double *ybar, int64_t N, int32
     o.restart = 0;
     o.momentum = 1;
     o.B_theta = 0.0;
-    std::vector<double> Xv(X, X + (size_t)N * n), yv(ybar, ybar + N);
+    // the handles hold the points sorted by block (stable), so that the pairs inside the blocks
+    // are K diagonal squares of the multiplier arrays; cr_blocks_solution restores the caller's order
+    std::vector<long long> perm((size_t)N);
+    for (long long l = 0; l < N; ++l) perm[l] = l;
+    std::stable_sort(perm.begin(), perm.end(), [&](long long a, long long b) { return block_of[a] < block_of[b]; });
+    std::vector<double> Xv((size_t)N * n), yv((size_t)N);
+    std::vector<int> bv((size_t)N);
+    for (long long q = 0; q < N; ++q) {
+        const long long l = perm[q];
+        for (int k = 0; k < n; ++k) Xv[(size_t)q * n + k] = X[(size_t)l * n + k];
+        yv[q] = ybar[l];
+        bv[q] = block_of[l];
+    }
     cr_handle h = nullptr, in = nullptr;
     cr_status s = create_impl(Xv, yv, N, n, &o, &h);
     if (s != CR_OK) return finish_create(s, &h);
     o.stream = h->stream;   // one stream for both duals
-    std::vector<double> Xi(X, X + (size_t)N * n), yi(ybar, ybar + N);
+    std::vector<double> Xi(Xv), yi(yv);
     s = create_impl(Xi, yi, N, n, &o, &in);
     if (s != CR_OK) {
         std::string m = in ? in->err : std::string("inner handle");
@@ -1813,10 +1826,61 @@ cr_status cr_blocks_create(const double *X, const double *ybar, int64_t N, int32
     h->blocks = true;
     h->K = K;
     h->inner_iters = inner_iters;
+    h->perm = perm;
     int *blk = nullptr;
     CR_TRY(dev_alloc(h, &blk, (size_t)N));
-    std::vector<int> bv(block_of, block_of + N);
     CR_CUDA(h, cudaMemcpyAsync(blk, bv.data(), sizeof(int) * N, cudaMemcpyHostToDevice, h->stream));
+    // the inner pass visits, in stripe s, only the rows of the blocks that its columns belong to,
+    // and its CTAs share those (stripe, row) units evenly
+    {
+        Params &Q = in->P;
+        const long long S = Q.S, G = Q.G;
+        std::vector<long long> bstart((size_t)N), bend((size_t)N), band((size_t)(2 * S)), cum((size_t)S + 1, 0);
+        for (long long q = 0; q < N;) {
+            long long e = q;
+            while (e < N && bv[e] == bv[q]) ++e;
+            for (long long t = q; t < e; ++t) {
+                bstart[t] = q;
+                bend[t] = e;
+            }
+            q = e;
+        }
+        for (long long st = 0; st < S; ++st) {
+            const long long c0 = st * crk::kW, c1 = std::min<long long>(N, c0 + crk::kW) - 1;
+            band[2 * st] = bstart[c0];
+            band[2 * st + 1] = bend[c1];
+            cum[st + 1] = cum[st] + (band[2 * st + 1] - band[2 * st]);
+        }
+        const long long T = cum[S];
+        std::vector<long long> ub((size_t)G + 1);
+        for (long long c = 0; c <= G; ++c) {
+            if (c == G) {
+                ub[c] = S * N;
+                continue;
+            }
+            const long long k = (long long)(((unsigned long long)c * (unsigned long long)T) / (unsigned long long)G);
+            long long st = 0;
+            while (st + 1 < S && cum[st + 1] <= k) ++st;
+            ub[c] = st * N + band[2 * st] + (k - cum[st]);
+        }
+        int slots = 1;
+        for (long long c = 0; c < G; ++c)
+            if (ub[c + 1] > ub[c]) slots = std::max(slots, (int)((ub[c + 1] - 1) / N - ub[c] / N + 1));
+        if (slots > Q.slots) {   // both column-partial buffers are sized by the slots per CTA
+            double *cp = nullptr;
+            float *cp32 = nullptr;
+            CR_TRY(dev_alloc(in, &cp, (size_t)G * slots * (in->NP + 1) * crk::kW));
+            CR_TRY(dev_alloc(in, &cp32, (size_t)G * slots * Q.cgroups * (in->NP + 1) * crk::kW));
+            Q.colpart64 = cp;
+            Q.colpart = cp32;
+            Q.slots = slots;
+        }
+        CR_TRY(upload_partition(in, const_cast<long long *>(Q.ubeg), &ub));
+        long long *db = nullptr;
+        CR_TRY(dev_alloc(h, &db, (size_t)(2 * S)));
+        CR_CUDA(h, cudaMemcpyAsync(db, band.data(), sizeof(long long) * 2 * S, cudaMemcpyHostToDevice, h->stream));
+        Q.band = db;
+    }
     CR_TRY(dev_alloc(h, &h->b_a, (size_t)N));
     CR_TRY(dev_alloc(h, &h->b_b, (size_t)N * n));
     CR_TRY(dev_alloc(h, &h->b_mu2, (size_t)N));
@@ -1879,11 +1943,18 @@ cr_status cr_blocks_solution(cr_handle h, double *yhat, double *xi)
     if (!h->blocks) return fail(h, CR_ESTATE, "not a K-block handle");
     if (h->iters == 0) CR_TRY(blocks_step1(h, 0, 1));   // Iteration 0: the block problems at (h, 0)
     cr_ctx *in = h->inner;
-    if (yhat) CR_CUDA(h, cudaMemcpyAsync(yhat, in->P.y1, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->stream));
-    if (xi) CR_CUDA(h, cudaMemcpyAsync(xi, in->P.xi1_64, sizeof(double) * h->N * h->n, cudaMemcpyDeviceToHost, h->stream));
+    const long long N = h->N;
+    const int n = h->n;
+    std::vector<double> yv((size_t)N), xv((size_t)N * n);
+    CR_CUDA(h, cudaMemcpyAsync(yv.data(), in->P.y1, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+    CR_CUDA(h, cudaMemcpyAsync(xv.data(), in->P.xi1_64, sizeof(double) * N * n, cudaMemcpyDeviceToHost, h->stream));
     CR_CUDA(h, cudaStreamSynchronize(h->stream));
-    if (yhat)
-        for (long long l = 0; l < h->N; ++l) yhat[l] -= h->P.shift;
+    for (long long q = 0; q < N; ++q) {   // back to the caller's order
+        const long long l = h->perm[q];
+        if (yhat) yhat[l] = yv[q] - h->P.shift;
+        if (xi)
+            for (int k = 0; k < n; ++k) xi[(size_t)l * n + k] = xv[(size_t)q * n + k];
+    }
     return CR_OK;
 }
 

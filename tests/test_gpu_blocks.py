@@ -20,9 +20,10 @@ def _blocks(N, K):
     return [np.arange(i, N, K) for i in range(K)]   # interleaved partition, as equal as possible
 
 
-# K = 2, 4, and N / 100 (N = 200: K = 2), ragged blocks (96 / 3 with n = 5)
+# K = 2, 4, and N / 100 (N = 200: K = 2; N = 900: K = 9, several stripes, so that the inner pass
+# visits only the rows of each stripe's blocks), ragged blocks (96 / 3 with n = 5)
 @pytest.mark.parametrize("N,n,K,M,outer", [(120, 2, 2, 40, 15), (200, 2, 4, 20, 12), (200, 3, 2, 30, 10),
-                                           (96, 5, 3, 16, 8)])
+                                           (96, 5, 3, 16, 8), (900, 2, 9, 10, 5)])
 def test_block_papg_trajectory_matches_oracle(N, n, K, M, outer):
     import paper_1407_7220_gb300 as crg
     X, yb, _ = datagen.make("sq2" if n < 5 else "sumexp", N=N, n=n)
