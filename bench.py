@@ -268,6 +268,13 @@ def run_ours(args):
         rate, dt, cores = oracle_rate(Ns, 60, 1)
         cpu = {"value": rate, "unit": "pair-updates/s", "cores": cores, "kind": "oracle",
                "sample": f"60 P-APG iterations of the FP64 oracle at N={Ns}, n={n} of the same recipe ({dt:.1f} s)"}
+        # the same oracle on one host core (a smaller sample)
+        from oracle import oracle as O
+        O.set_num_threads(1)
+        rate1, dt1, _ = oracle_rate(2000, 10, 1)
+        O.set_num_threads(cores)
+        cpu["single_thread"] = {"value": rate1, "cores": 1,
+                                "sample": f"10 iterations at N=2000, n={n} ({dt1:.1f} s)"}
 
     if rank == 0:
         line = {

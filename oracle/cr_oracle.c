@@ -712,6 +712,16 @@ ORC_API void orc_papg_jvp_multi(const double *X, const double *ybar, int64_t N, 
     free(h); free(y); free(dy); free(xi); free(dxi); free(rs); free(drs);
 }
 
+/* Threads of the parallel loops from here on (timing the oracle single-threaded); t >= 1. */
+ORC_API void orc_set_num_threads(int t)
+{
+#ifdef _OPENMP
+    if (t >= 1) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
 ORC_API int orc_num_threads(void)
 {
 #ifdef _OPENMP

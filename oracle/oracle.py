@@ -77,6 +77,8 @@ def _load():
             lib.orc_papg_jvp_multi.restype = None
             lib.orc_num_threads.argtypes = []
             lib.orc_num_threads.restype = ctypes.c_int
+            lib.orc_set_num_threads.argtypes = [ctypes.c_int]
+            lib.orc_set_num_threads.restype = None
             _lib = lib
     return _lib
 
@@ -92,6 +94,11 @@ def _f64(a) -> np.ndarray:
 
 def num_threads() -> int:
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(t: int) -> None:
+    """Threads of the oracle's parallel loops from now on (t >= 1)."""
+    _load().orc_set_num_threads(int(t))
 
 
 def shift(ybar) -> float:
