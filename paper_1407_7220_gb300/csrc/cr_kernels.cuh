@@ -410,20 +410,46 @@ template <> struct Store<__half> {
         o[0] = f2_make(h2f(t.x & 0xFFFFu, inv_scale), h2f(t.x >> 16, inv_scale));
         o[1] = f2_make(h2f(t.y & 0xFFFFu, inv_scale), h2f(t.y >> 16, inv_scale));
     }
+    // round<SR> on both halves with packed conversions.  Stochastic rounding adds noise uniform
+    // over one FP16 step and rounds toward zero: with p = the FP16 step at s (2^(max(E,-14) - 10),
+    // E the exponent of s; the subnormal step below 2^-14), t = s + u p and the pair is
+    // RZ_f16(t0, t1), which rounds up with probability (s - RZ(s)) / p (to within the 2^-13 p that
+    // t's own rounding adds).  u p is formed as U q - 2^-15 q with U = 2^-15 (1 + X 2^-23), X the 16
+    // random bits (one byte permute), and q = 2^22 p (both exact powers-of-two scalings).
     template <bool SR>
-    __device__ static __forceinline__ f2 round2(f2 th2, f2 g, f2, float invL, uint32_t rnd, float scl)
+    __device__ static __forceinline__ f2 round2(f2 th2, f2 g, f2 ninvL2, float, uint32_t rnd, float scl)
     {
-        float t0, t1, g0, g1;
-        f2_split(th2, t0, t1);
-        f2_split(g, g0, g1);
-        return f2_make(round<SR>(t0, g0, invL, rnd & 0xFFFFu, scl), round<SR>(t1, g1, invL, rnd >> 16, scl));
+        float v0, v1;
+        f2_split(f2_fma(g, ninvL2, th2), v0, v1);
+        const float s0 = fminf(fmaxf(v0, 0.0f) * scl, 65504.0f);
+        const float s1 = fminf(fmaxf(v1, 0.0f) * scl, 65504.0f);
+        uint32_t h;
+        if (SR) {
+            const float q0 = __uint_as_float(max(__float_as_uint(s0) & 0x7F800000u, 113u << 23) + (12u << 23));
+            const float q1 = __uint_as_float(max(__float_as_uint(s1) & 0x7F800000u, 113u << 23) + (12u << 23));
+            const float U0 = __uint_as_float(__byte_perm(rnd, 0x38000000u, 0x7610u));
+            const float U1 = __uint_as_float(__byte_perm(rnd, 0x38000000u, 0x7632u));
+            const f2 q = f2_make(q0, q1);
+            const f2 c = f2_fma(f2_make(-0x1p-15f, -0x1p-15f), q, f2_make(s0, s1));   // s - 2^-15 q, exact
+            float t0, t1;
+            f2_split(f2_fma(f2_make(U0, U1), q, c), t0, t1);
+            asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(t1), "f"(t0));
+        } else {
+            asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(s1), "f"(s0));
+        }
+        const __half2 hh = *reinterpret_cast<const __half2 *>(&h);
+        return f2_make(__low2float(hh), __high2float(hh));   // sv = 0 for v <= 0 either way
     }
     __device__ static __forceinline__ Vec pack2(const f2 (&s)[2])
     {
+        // the values are FP16 numbers: one exact packed conversion per pair
         float a[4];
         f2_split(s[0], a[0], a[1]);
         f2_split(s[1], a[2], a[3]);
-        return pack(a);
+        Vec v;
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(v.x) : "f"(a[1]), "f"(a[0]));
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(v.y) : "f"(a[3]), "f"(a[2]));
+        return v;
     }
     __device__ static __forceinline__ f2 decoded2(f2 s, f2 iscl2) { return f2_mul(s, iscl2); }
 };
