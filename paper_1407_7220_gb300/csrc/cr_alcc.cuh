@@ -139,6 +139,7 @@ __device__ void phase_mapg_step(const Params &P, const AlccStep &S, long long el
         }
         P.rowrec[l * REC] = (float)y2n;
         P.ccol2[l] = (float)(d - y2n);
+        P.ccol2_64[l] = d - y2n;
         if (!isfinite(y2n) || !isfinite(d)) atomicCAS(&P.st->error, 0, ERR_NUMERIC);
     }
     double vals[4] = {dy, dx, ny, nx};
@@ -202,6 +203,7 @@ __device__ void phase_alcc_take(const Params &P, int q, long long vc)
         }
         P.rowrec[l * REC] = (float)y;
         P.ccol2[l] = (float)(d - y);
+        P.ccol2_64[l] = d - y;
     }
 }
 
@@ -235,6 +237,31 @@ __device__ void phase_alcc_stat(const Params &P, const AlccStep &S, double *red,
     }
 }
 
+// The phases of k_alcc as separate functions: each gets its own register allocation instead of
+// one allocation for the whole kernel (which spilled).
+template <typename TS, int NP, int MODE>
+__device__ __noinline__ void alcc_pair_pass(const Params &P, long long ell, unsigned char *sm, uint64_t *full,
+                                            uint64_t *empty, unsigned long long &kstage, long long vc, float a)
+{
+    phase_pair<TS, NP, MODE>(P, ell, sm, full, empty, kstage, vc, a);
+}
+template <int NP>
+__device__ __noinline__ void alcc_grad_fold(const Params &P, const AlccStep &S, long long ell, double *red, long long vc)
+{
+    phase_mapg_grad<NP>(P, S, ell, red, vc);
+}
+template <int NP>
+__device__ __noinline__ void alcc_step_fold(const Params &P, const AlccStep &S, long long ell, double w, double *red,
+                                            long long vc)
+{
+    phase_mapg_step<NP>(P, S, ell, w, red, vc);
+}
+template <typename TS, int NP>
+__device__ __noinline__ void alcc_kkt_pass(const Params &P, double *red, long long vc)
+{
+    phase_kkt<TS, NP, true>(P, 0, red, vc);
+}
+
 template <typename TS, int NP>
 __global__ void __launch_bounds__(kThreads, 1) k_alcc(const __grid_constant__ Params P, const AlccStep S)
 {
@@ -250,12 +277,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_alcc(const __grid_constant__ Pa
     long long ell = S.ell0;
     bool ret = false;
     for (; ell <= S.ell1; ++ell) {
-        phase_pair<TS, NP, PM_ALCC_GRAD>(P, ell, sm, full, empty, kstage, vc);
+        alcc_pair_pass<TS, NP, PM_ALCC_GRAD>(P, ell, sm, full, empty, kstage, vc, 1.0f);
         if (!grid_barrier(P, bar)) return;
-        phase_mapg_grad<NP>(P, S, ell, red, vc);
+        alcc_grad_fold<NP>(P, S, ell, red, vc);
         if (!grid_barrier(P, bar)) return;
         const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));   // MAPG step 3
-        phase_mapg_step<NP>(P, S, ell, (t - 1.0) / tn, red, vc);
+        alcc_step_fold<NP>(P, S, ell, (t - 1.0) / tn, red, vc);
         t = tn;
         if (!grid_barrier(P, bar)) return;
         ret = mapg_returns(P, S, ell, &s_flag);
@@ -271,10 +298,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_alcc(const __grid_constant__ Pa
     }
     phase_alcc_take<NP>(P, (int)(ell & 1), vc);
     if (!grid_barrier(P, bar)) return;
-    phase_pair<TS, NP, PM_ALCC_UPDATE>(P, 0, sm, full, empty, kstage, vc, S.a);   // theta_{k+1}, in place
+    alcc_pair_pass<TS, NP, PM_ALCC_UPDATE>(P, 0, sm, full, empty, kstage, vc, S.a);   // theta_{k+1}, in place
     if (!grid_barrier(P, bar)) return;
     phase_alcc_stat<NP>(P, S, red, vc);
-    phase_kkt<TS, NP, true>(P, 0, red, vc);   // (A_1 y_k + A_2 xi_k)_p in FP64 against theta_{k+1}
+    alcc_kkt_pass<TS, NP>(P, red, vc);   // (A_1 y_k + A_2 xi_k)_p in FP64 against theta_{k+1}
     if (!grid_barrier(P, bar)) return;
     if (vc == 0 && threadIdx.x < 32) {
         double ry = 0.0, rx = 0.0, mv = 0.0, mc = 0.0;

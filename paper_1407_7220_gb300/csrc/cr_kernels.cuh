@@ -862,12 +862,14 @@ template <typename TS, int NP, int TILES = 2, int RS = kRS> struct PairSmem {
 // theta - g_p in FP64 for pair (l1, l2) from the folds' FP64 point (y, xi)^(2) and X: the ALCC
 // passes take it for the pairs whose FP32 estimate of theta - g is close to 0, since the
 // multiplier estimate mu_k (g - theta)_- multiplies any absolute error in it by mu_k.
+// g = y_l1 + (xi_l2.x_l2 - y_l2) - xi_l2.x_l1 with the column's FP64 constant xi_l2.x_l2 - y_l2
+// from the folds: n FMAs and 2n + 2 loads (the FP32 pass's expression, in FP64, where its
+// rounding is ~2^-29 of the FP32 error that the window is drawn from).
 static __device__ __noinline__ double alcc_exact_margin(const Params &P, long long l1, long long l2, float theta)
 {
     const int n = P.n;
-    double g = __ldcg(P.ay2 + l1) - __ldcg(P.ay2 + l2);
-    for (int k = 0; k < n; ++k)
-        g -= __ldcg(P.axi2 + l2 * n + k) * (__ldg(P.X64 + l1 * n + k) - __ldg(P.X64 + l2 * n + k));
+    double g = __ldcg(P.ay2 + l1) + __ldcg(P.ccol2_64 + l2);
+    for (int k = 0; k < n; ++k) g = fma(-__ldcg(P.axi2 + l2 * n + k), __ldg(P.X64 + l1 * n + k), g);
     return (double)theta - g;
 }
 

@@ -104,6 +104,7 @@ struct cr_ctx {
     bool a_have_metrics = false;
     double a_metrics[4] = {0, 0, 0, 0};
     std::vector<float> a_rec0, a_ccol0;   // column data of (y_0, xi_0) = (ybar, 0)
+    std::vector<double> a_ccol64;         // the same column values xi.x - y in FP64 (of the point ay2 holds)
     // P-APG with K blocks (cr_blocks_*): this handle holds the outer dual (pairs between blocks,
     // y >= 0 rows); `inner` the pairs inside the blocks (Step 1 by inner P-APG)
     bool blocks = false;
@@ -910,6 +911,7 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
         }
         CR_TRY(dev_alloc(h, &P.ay2, N));
         CR_TRY(dev_alloc(h, &P.axi2, (size_t)N * n));
+        if (!P.ccol2_64) CR_TRY(dev_alloc(h, &P.ccol2_64, N));   // xi.x - y of (y, xi)^(2), FP64
         // sigma_max^2(A_1) = 2N (A_1^T A_1 = 2(N I - 1 1^T)); radii from the feasible point
         // (mean(ybar) 1, 0): Bbar = ||ybar - mean||, Bbar_y = Bbar, Bbar_xi = Bbar / sqrt(gamma)
         double mean = 0.0;
@@ -948,9 +950,11 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
         // column data of (y_0, xi_0) = (ybar, 0): row records y = ybar, xi^T x - y = -ybar
         h->a_rec0 = rec;
         h->a_ccol0.resize(N);
+        h->a_ccol64.resize(N);
         for (long long l = 0; l < N; ++l) {
             h->a_rec0[(size_t)l * REC] = (float)yb[l];
             h->a_ccol0[l] = (float)(-yb[l]);
+            h->a_ccol64[l] = -hv[l];   // ay2 starts as h
         }
         return alcc_init(h);
     }
@@ -978,6 +982,7 @@ cr_status alcc_init(cr_ctx *h)
     CR_CUDA(h, cudaMemcpyAsync(P.rowrec, h->a_rec0.data(), sizeof(float) * h->a_rec0.size(), cudaMemcpyHostToDevice,
                                h->stream));
     CR_CUDA(h, cudaMemcpyAsync(P.ccol2, h->a_ccol0.data(), sizeof(float) * N, cudaMemcpyHostToDevice, h->stream));
+    CR_CUDA(h, cudaMemcpyAsync(P.ccol2_64, h->a_ccol64.data(), sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
     CR_CUDA(h, cudaMemsetAsync(P.rowpart, 0, sizeof(float) * (size_t)P.Q * N, h->stream));
     CR_CUDA(h, cudaMemsetAsync(P.colpart, 0, sizeof(float) * (size_t)P.G * P.slots * P.cgroups * (h->NP + 1) * crk::kW,
                                h->stream));
