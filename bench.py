@@ -551,7 +551,9 @@ def run_kkt(args):
     N, n = args.N, args.n
     X, yb, _ = datagen.make(RECIPE, N=N, n=n)
     thresholds = [float(t) for t in args.kkt_targets.split(",")]
-    schedules = {"f32": ("f32", None), "bf16->f32": ("bf16", args.promote_at), "f16->f32": ("f16", args.promote_at)}
+    pb = args.promote_at if args.promote_at is not None else args.promote_at_bf16
+    ph = args.promote_at if args.promote_at is not None else args.promote_at_f16
+    schedules = {"f32": ("f32", None), "bf16->f32": ("bf16", pb), "f16->f32": ("f16", ph)}
     out = {}
     with Clocks(0) as clk:
         for name, (dt0, promote_at) in schedules.items():
@@ -583,7 +585,7 @@ def run_kkt(args):
     line = {"metric": "time to FP64-confirmed KKT residual", "unit": "s", "higher_is_better": False, "n_gpus": 1,
             "data": "synthetic", "schedules": out, "iteration_cap": args.kkt_cap,
             "config": {"workload": f"{RECIPE} recipe N={N} n={n} gamma={GAMMA}, stochastic rounding, plain P-APG; "
-                                   f"16-bit schedules widen to FP32 at KKT {args.promote_at:g}"},
+                                   f"16-bit schedules widen to FP32 at KKT {pb:g} (BF16) and {ph:g} (FP16)"},
             "clocks": clk.summary()}
     print(json.dumps(line))
 
@@ -671,7 +673,11 @@ def main():
     ap.add_argument("--kkt-targets", default="0.3,0.2,0.1,0.07,0.05,0.03,0.02")
     ap.add_argument("--kkt-cap", type=int, default=20000, help="iteration cap of --config kkt")
     ap.add_argument("--kkt-every", type=int, default=100)
-    ap.add_argument("--promote-at", type=float, default=0.2, help="KKT at which 16-bit schedules widen to FP32")
+    ap.add_argument("--promote-at", type=float, default=None, help="KKT at which both 16-bit schedules widen to FP32")
+    ap.add_argument("--promote-at-bf16", type=float, default=0.2,
+                    help="KKT at which the BF16 schedule widens to FP32 (BF16 stalls between 0.2 and 0.1 here)")
+    ap.add_argument("--promote-at-f16", type=float, default=0.1,
+                    help="KKT at which the FP16 schedule widens to FP32 (FP16 stalls between 0.1 and 0.07 here)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
