@@ -113,6 +113,11 @@ typedef struct {
                                  followed by the radial factor min(1, B_theta / ||clamped lambda||_2), which
                                  costs a norm pass and, when the ball binds, a scaling pass over the array.
                                  FP32 or FP64 multipliers, CUDA-core pass, phase driver, no record_every */
+    double promote_at;        /* BF16 or FP16 multipliers: > 0 makes cr_solve a precision schedule, solving
+                                 in the 16-bit format until the FP64-confirmed KKT residual reaches
+                                 promote_at, then widening to FP32 in place (cr_promote) and solving on to
+                                 its tol.  0 (default): no widening.  Measured on recipe (2) at N = 20,000:
+                                 0.1 for FP16 and 0.2 for BF16, just before each format stalls */
 } cr_options;
 
 /* Fills *opt with the defaults documented above. */

@@ -65,7 +65,7 @@ class Options(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("barrier_timeout_ms", ctypes.c_int32),
         ("test_barrier_extra", ctypes.c_int32), ("profile", ctypes.c_int32), ("record_every", ctypes.c_int32),
         ("pair_engine", ctypes.c_int32), ("batch_stage_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
-        ("restart_tol", ctypes.c_double), ("B_theta", ctypes.c_double),
+        ("restart_tol", ctypes.c_double), ("B_theta", ctypes.c_double), ("promote_at", ctypes.c_double),
     ]
 
 

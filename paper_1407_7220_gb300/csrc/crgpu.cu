@@ -1335,11 +1335,36 @@ cr_status cr_iterate(cr_handle h, int64_t k)
     return CR_OK;
 }
 
+static cr_status cr_solve_impl(cr_handle h, double tol, int64_t max_iter, int64_t *iters_done);
+
 cr_status cr_solve(cr_handle h, double tol, int64_t max_iter, int64_t *iters_done)
 {
     CR_TRY(papg_only(h));
     if (iters_done) *iters_done = 0;
     if (max_iter < 0 || !(tol >= 0.0)) return fail(h, CR_EINVAL, "bad tol/max_iter");
+    // precision schedule: the 16-bit format down to promote_at, then FP32
+    const int dt = h->opt.theta_dtype;
+    if ((dt == CR_THETA_BF16 || dt == CR_THETA_F16) && h->opt.promote_at > tol) {
+        int64_t d1 = 0;
+        const cr_status s1 = cr_solve_impl(h, h->opt.promote_at, max_iter, &d1);
+        if (s1 != CR_OK && s1 != CR_NOT_CONVERGED) return s1;
+        if (s1 == CR_NOT_CONVERGED) {   // the cap came first
+            if (iters_done) *iters_done = d1;
+            return s1;
+        }
+        CR_TRY(cr_promote(h, CR_THETA_F32));
+        int64_t d2 = 0;
+        const cr_status s2 = cr_solve_impl(h, tol, max_iter - d1, &d2);
+        if (iters_done) *iters_done = d1 + d2;
+        return s2;
+    }
+    return cr_solve_impl(h, tol, max_iter, iters_done);
+}
+
+// cr_solve in the current storage format
+static cr_status cr_solve_impl(cr_handle h, double tol, int64_t max_iter, int64_t *iters_done)
+{
+    if (iters_done) *iters_done = 0;
     CR_CUDA(h, cudaMemsetAsync(&h->P.st->converged, 0, sizeof(int), h->stream));
     const long long start = h->iters;
     const bool pers = h->opt.driver != CR_DRIVER_PHASES && h->persistent_ok;

@@ -199,3 +199,21 @@ def test_promoted_schedule_converges_to_the_exact_fit(crg):
     conv, _ = g.solve(1e-4, 400_000)
     assert conv and g.kkt_residual()["kkt"] <= 1e-4
     assert _rel(g.solution()[0], ref["y_hat"]) <= 3e-4
+
+
+def test_solve_runs_the_precision_schedule_of_promote_at(crg):
+    # cr_options.promote_at: cr_solve solves in FP16 down to promote_at, widens to FP32 and goes
+    # on to its tol; the same as doing the three steps by hand, bit for bit
+    X, yb, _ = datagen.make("sq2", N=400)
+    opts = dict(gamma=0.1, theta_dtype="f16", stochastic_round=1, restart=0, kkt_every=50)
+    a = crg.Solver(X, yb, promote_at=0.1, **opts)
+    conv_a, it_a = a.solve(1e-3, 200_000)
+    b = crg.Solver(X, yb, **opts)
+    c1, i1 = b.solve(0.1, 200_000)
+    b.promote("f32")
+    c2, i2 = b.solve(1e-3, 200_000 - i1)
+    assert conv_a and c1 and c2 and it_a == i1 + i2
+    assert np.array_equal(a.solution()[0], b.solution()[0])
+    assert a.kkt_residual()["kkt"] <= 1e-3
+    with pytest.raises(crg.CrError):
+        a.promote("f32")                                    # the handle is FP32 now
