@@ -393,8 +393,10 @@ const char *cr_batch_last_error(cr_batch_handle b);
  * iteration: an inexact Step 1, as the paper's ALCC or interior-point block solves.  K = N (every
  * point its own block) is the P-APG of cr_create; K = 1 makes Step 1 the whole problem.
  * Multipliers and arithmetic are FP64 (n <= 10); device memory: 4 N x ceil16(N) FP64 arrays
- * (outer and inner iterates).  The handle answers cr_get_info and cr_destroy; cr_reset and the
- * P-APG calls of cr_create return CR_ESTATE on it. */
+ * (outer and inner iterates).  The handles hold the points sorted by block (stable); the inner
+ * pass visits, in each 256-column stripe, only the rows of the blocks its columns belong to, and
+ * cr_blocks_solution returns the points in the caller's order.  The handle answers cr_get_info
+ * and cr_destroy; cr_reset and the P-APG calls of cr_create return CR_ESTATE on it. */
 cr_status cr_blocks_create(const double *X, const double *ybar, int64_t N, int32_t n, const int32_t *block_of,
                            const cr_options *opt, int32_t inner_iters, cr_handle *out);
 /* k outer iterations, then Step 1 once more at the dual iterate theta^(1)_l (the primal point of
