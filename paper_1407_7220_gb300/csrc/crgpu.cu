@@ -1429,6 +1429,7 @@ cr_status cr_objective(cr_handle h, double *primal, double *dual, double *gap)
 cr_status cr_get_solution(cr_handle h, double *yhat, double *xi)
 {
     CR_TRY(usable(h));
+    if (h->blocks) return fail(h, CR_ESTATE, "K-block handle: the primal point comes from cr_blocks_solution");
     if (yhat) {
         CR_CUDA(h, cudaMemcpyAsync(yhat, h->P.y1, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->stream));
     }

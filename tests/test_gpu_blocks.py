@@ -71,3 +71,6 @@ def test_block_solver_rejects_bad_arguments():
     g = crg.BlockSolver(X, yb, _blocks(40, 2), inner_iters=4, gamma=0.1)
     assert crg.lib().cr_iterate(g.handle, 1) == crg.CR_ESTATE
     assert crg.lib().cr_reset(g.handle) == crg.CR_ESTATE
+    # the handles hold the points sorted by block: the fit comes from cr_blocks_solution only
+    assert crg.lib().cr_get_solution(g.handle, None, None) == crg.CR_ESTATE
+    assert crg.lib().cr_get_solution_device(g.handle, None, None) == crg.CR_ESTATE
