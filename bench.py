@@ -166,8 +166,8 @@ def run_reference(args):
 # N(N-1) pair updates (the per-stage vectors make the excess over 3 b proportional to the
 # pairs); keyed by (engine, theta dtype, padded n).  A kernel change invalidates an entry.
 TRAFFIC_BYTES_PER_PAIR = {
-    ("cuda_cores", "f32", 10): (517.62944e6 + 219.862016e6) / (8000 * 7999),
-    ("tensor_cores", "bf16", 20): (737.105536e6 + 259.67936e6) / (12000 * 11999),
+    ("cuda_cores", "f32", 10): (517.621504e6 + 221.631232e6) / (8000 * 7999),
+    ("tensor_cores", "bf16", 20): (593.808384e6 + 253.485056e6) / (12000 * 11999),
 }
 
 

@@ -126,7 +126,7 @@ void cr_options_default(cr_options *opt);
 /* Creates a solver for one instance.  X: host, N x n row-major FP64; ybar: host, N FP64.
  * opt may be NULL (defaults).  Requires n >= 1, N >= n + 1 (uniqueness of y*, stated after
  * problem (original)) and finite inputs, else CR_EINVAL.  The state is Iteration 0 of Fig. 2
- * (theta^(1)_0 = theta^(2)_1 = 0, t_1 = 1).  Device memory: two N x ceil16(N) theta arrays of
+ * (theta^(1)_0 = theta^(2)_1 = 0, t_1 = 1).  Device memory: two N x ceil128(N) theta arrays of
  * the chosen dtype plus O(N n) vectors and O(N^2/32) partial sums. */
 cr_status cr_create(const double *X, const double *ybar, int64_t N, int32_t n, const cr_options *opt,
                     cr_handle *out);
@@ -283,7 +283,7 @@ void cr_destroy(cr_handle h);
  * the feasible point (mean(ybar) 1, 0): Bbar = ||ybar - mean(ybar)||, Bbar_y = Bbar,
  * Bbar_xi = Bbar / sqrt(gamma); mu_1, tau_1 and the alphas are set relative to these scales.
  *
- * Device memory: ONE N x ceil16(N) FP32 multiplier array (read once per MAPG iteration, read and
+ * Device memory: ONE N x ceil128(N) FP32 multiplier array (read once per MAPG iteration, read and
  * written once per outer iteration) plus O(N n) vectors and O(N^2/32) partial sums.  Each MAPG
  * iteration is a cooperative launch's pair pass plus two row folds in FP64; a launch runs up to
  * launch_iters MAPG iterations.  The handle answers cr_get_solution ((y_k, xi_k)),
@@ -392,7 +392,7 @@ const char *cr_batch_last_error(cr_batch_handle b);
  * momentum restarted (as from Iteration 0), for inner_iters (even, >= 2) iterations per outer
  * iteration: an inexact Step 1, as the paper's ALCC or interior-point block solves.  K = N (every
  * point its own block) is the P-APG of cr_create; K = 1 makes Step 1 the whole problem.
- * Multipliers and arithmetic are FP64 (n <= 10); device memory: 4 N x ceil16(N) FP64 arrays
+ * Multipliers and arithmetic are FP64 (n <= 10); device memory: 4 N x ceil128(N) FP64 arrays
  * (outer and inner iterates).  The handles hold the points sorted by block (stable); the inner
  * pass visits, in each 256-column stripe, only the rows of the blocks its columns belong to, and
  * cr_blocks_solution returns the points in the caller's order.  The handle answers cr_get_info

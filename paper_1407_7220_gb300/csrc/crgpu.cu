@@ -769,7 +769,11 @@ cr_status create_impl(std::vector<double> &X, std::vector<double> &yb, long long
     P.N = N;
     P.n = n;
     P.NP = h->NP;
-    h->ld = ((N + 15) / 16) * 16;
+    // rows of the multiplier arrays start on 256-byte boundaries (multiples of 128 elements): the
+    // tile loads' L2 promotion fetches 256-byte lines, and a row start inside a line made every
+    // tile row fetch one line more (N = 12,000: DRAM reads of the pass 1.07x -> 1.01x (FP32),
+    // 1.28x -> 1.03x (BF16) of the two arrays)
+    h->ld = ((N + 127) / 128) * 128;
     P.ld = h->ld;
     P.S = (int)S;
     // pair-pass engine: tensor cores for the two products when n is not tiny, unless the
