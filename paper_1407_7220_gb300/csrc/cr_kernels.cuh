@@ -357,6 +357,28 @@ template <> struct Store<__nv_bfloat16> {
         }
         return f2_make(fmaxf(__uint_as_float(b0 & 0xFFFF0000u), 0.0f), fmaxf(__uint_as_float(b1 & 0xFFFF0000u), 0.0f));
     }
+    // round2 with the packing and the projection in one conversion: after the 16-bit noise (or
+    // the round-to-nearest-even increment) the bit patterns are truncated, i.e. converted toward
+    // zero, by one packed cvt.rz.relu (negative values give 0); returns the stored values as
+    // floats and, in bits, the packed BF16 pair (low half: the first value)
+    template <bool SR>
+    __device__ static __forceinline__ f2 round2_bits(f2 th2, f2 g, f2 ninvL2, uint32_t rnd, uint32_t &bits)
+    {
+        float v0, v1;
+        f2_split(f2_fma(g, ninvL2, th2), v0, v1);
+        uint32_t b0 = __float_as_uint(v0), b1 = __float_as_uint(v1);
+        if (SR) {
+            b0 += rnd & 0xFFFFu;
+            b1 += rnd >> 16;
+        } else {
+            b0 += 0x7FFFu + ((b0 >> 16) & 1u);
+            b1 += 0x7FFFu + ((b1 >> 16) & 1u);
+        }
+        uint32_t h;
+        asm("cvt.rz.relu.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(__uint_as_float(b1)), "f"(__uint_as_float(b0)));
+        bits = h;
+        return f2_make(__uint_as_float(h << 16), __uint_as_float(h & 0xFFFF0000u));
+    }
     __device__ static __forceinline__ Vec pack2(const f2 (&s)[2])
     {
         float a[4];
@@ -425,20 +447,46 @@ template <> struct Store<__half> {
         const float s1 = fminf(fmaxf(v1, 0.0f) * scl, 65504.0f);
         uint32_t h;
         if (SR) {
-            const float q0 = __uint_as_float(max(__float_as_uint(s0) & 0x7F800000u, 113u << 23) + (12u << 23));
-            const float q1 = __uint_as_float(max(__float_as_uint(s1) & 0x7F800000u, 113u << 23) + (12u << 23));
-            const float U0 = __uint_as_float(__byte_perm(rnd, 0x38000000u, 0x7610u));
-            const float U1 = __uint_as_float(__byte_perm(rnd, 0x38000000u, 0x7632u));
-            const f2 q = f2_make(q0, q1);
-            const f2 c = f2_fma(f2_make(-0x1p-15f, -0x1p-15f), q, f2_make(s0, s1));   // s - 2^-15 q, exact
             float t0, t1;
-            f2_split(f2_fma(f2_make(U0, U1), q, c), t0, t1);
+            f2_split(sr_noise(s0, s1, rnd), t0, t1);
             asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(t1), "f"(t0));
         } else {
             asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(s1), "f"(s0));
         }
         const __half2 hh = *reinterpret_cast<const __half2 *>(&h);
         return f2_make(__low2float(hh), __high2float(hh));   // sv = 0 for v <= 0 either way
+    }
+    // The same update with th2 and g already multiplied by the scale: v s = fma(g s, -1/L, th2 s)
+    // exactly (a power-of-two factor commutes with each rounding).  The clamp to [0, 65504] is
+    // the conversion's own (.relu: negative values give 0, and the noise cannot lift a negative
+    // value above 0 since it stays below one FP16 step of it; .satfinite: 65504 above), so the
+    // stored values are those of round2 for every |v s| < 2^116.  Returns the stored FP16 numbers
+    // as floats (scaled) and, in h, the packed pair (low half: the first value).
+    template <bool SR>
+    __device__ static __forceinline__ f2 round2_scaled(f2 th2s, f2 gs, f2 ninvL2, uint32_t rnd, uint32_t &h)
+    {
+        float s0, s1;
+        f2_split(f2_fma(gs, ninvL2, th2s), s0, s1);
+        if (SR) {
+            float t0, t1;
+            f2_split(sr_noise(s0, s1, rnd), t0, t1);
+            asm("cvt.rz.relu.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(t1), "f"(t0));
+        } else {
+            asm("cvt.rn.relu.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(s1), "f"(s0));
+        }
+        const __half2 hh = *reinterpret_cast<const __half2 *>(&h);
+        return f2_make(__low2float(hh), __high2float(hh));
+    }
+    // t = s + u p of the stochastic rounding above, both halves
+    __device__ static __forceinline__ f2 sr_noise(float s0, float s1, uint32_t rnd)
+    {
+        const float q0 = __uint_as_float(max(__float_as_uint(s0) & 0x7F800000u, 113u << 23) + (12u << 23));
+        const float q1 = __uint_as_float(max(__float_as_uint(s1) & 0x7F800000u, 113u << 23) + (12u << 23));
+        const float U0 = __uint_as_float(__byte_perm(rnd, 0x38000000u, 0x7610u));
+        const float U1 = __uint_as_float(__byte_perm(rnd, 0x38000000u, 0x7632u));
+        const f2 q = f2_make(q0, q1);
+        const f2 c = f2_fma(f2_make(-0x1p-15f, -0x1p-15f), q, f2_make(s0, s1));   // s - 2^-15 q, exact
+        return f2_fma(f2_make(U0, U1), q, c);
     }
     __device__ static __forceinline__ Vec pack2(const f2 (&s)[2])
     {

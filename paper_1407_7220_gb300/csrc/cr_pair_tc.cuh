@@ -294,6 +294,7 @@ template <> struct Pair2<__nv_bfloat16> {
         f2_split(s, a, b);
         *reinterpret_cast<uint32_t *>(p) = __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632u);
     }
+    __device__ static __forceinline__ void store_bits(__nv_bfloat16 *p, uint32_t h) { *reinterpret_cast<uint32_t *>(p) = h; }
 };
 template <> struct Pair2<__half> {
     __device__ static __forceinline__ f2 load(const __half *p, float iscl)
@@ -307,15 +308,23 @@ template <> struct Pair2<__half> {
         f2_split(s, a, b);
         *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
     }
+    // the stored FP16 numbers as floats, without the inverse scale
+    __device__ static __forceinline__ f2 load_scaled(const __half *p)
+    {
+        const __half2 t = *reinterpret_cast<const __half2 *>(p);
+        return f2_make(__low2float(t), __high2float(t));
+    }
+    __device__ static __forceinline__ void store_bits(__half *p, uint32_t h) { *reinterpret_cast<uint32_t *>(p) = h; }
 };
 
 // Row sums of one stage (8 rows per warp) reduced across the warp with a transposing
 // butterfly (9 shuffles); entry e = 4*bit4 + 2*bit3 + bit2 of the lane id is row r8 + e.  The
 // four warps of a warpgroup (the four 64-column slabs of the stripe, q = 0..3) then add their
 // sums through shared memory (xb: this warpgroup's [4][8] block for the stage's parity; named
-// barrier 1 + wg), and warp q = 0 stores one partial per (stripe, row), adding in order of q.
+// barrier 1 + wg), and warp q = 0 stores one partial per (stripe, row), adding in order of q and
+// multiplying by osc (the inverse storage scale of FP16 multipliers, else 1).
 __device__ __forceinline__ void tc_flush_rows(float (&v)[8], long long r8, long long r1, float *rp, int Q, int lane,
-                                              float *xb, int q, int wg)
+                                              float *xb, int q, int wg, float osc)
 {
     const unsigned full = 0xffffffffu;
 #pragma unroll
@@ -342,14 +351,14 @@ __device__ __forceinline__ void tc_flush_rows(float (&v)[8], long long r8, long 
     named_barrier_sync(1 + wg, 128);
     if (q == 0 && (lane & 3) == 0) {
         const long long row = r8 + e;
-        const float t = ((xb[e] + xb[8 + e]) + xb[16 + e]) + xb[24 + e];
+        const float t = (((xb[e] + xb[8 + e]) + xb[16 + e]) + xb[24 + e]) * osc;
         if (row < r1) st_keep(rp + row * Q, t, l2_evict_last());
     }
 }
 
 // The same for 4 rows per warp (6 shuffles); entry e = 2*bit4 + bit3 is row r4 + e.
 __device__ __forceinline__ void tc_flush_rows(float (&v)[4], long long r4, long long r1, float *rp, int Q, int lane,
-                                              float *xb, int q, int wg)
+                                              float *xb, int q, int wg, float osc)
 {
     const unsigned full = 0xffffffffu;
 #pragma unroll
@@ -371,7 +380,7 @@ __device__ __forceinline__ void tc_flush_rows(float (&v)[4], long long r4, long 
     named_barrier_sync(1 + wg, 128);
     if (q == 0 && (lane & 7) == 0) {
         const long long row = r4 + e;
-        const float t = ((xb[e] + xb[8 + e]) + xb[16 + e]) + xb[24 + e];
+        const float t = (((xb[e] + xb[8 + e]) + xb[16 + e]) + xb[24 + e]) * osc;
         if (row < r1) st_keep(rp + row * Q, t, l2_evict_last());
     }
 }
@@ -384,24 +393,44 @@ __device__ __forceinline__ void tc_rows(const TS *tcur, const TS *tprv, const fl
                                         long long r1, long long col0, bool va, bool vb, f2 ccol,
                                         const float (&de)[TcShape<TS, NP>::RPW], const float (&dd)[TcShape<TS, NP>::RPW],
                                         f2 beta2, f2 ninvL2, float invL, uint32_t hcol, float scl, float iscl,
-                                        f2 iscl2, TS *nrow, long long ld, float (&ae)[TcShape<TS, NP>::RPW],
+                                        f2 iscl2, f2 scl2, TS *nrow, long long ld, float (&ae)[TcShape<TS, NP>::RPW],
                                         float (&ao)[TcShape<TS, NP>::RPW], float (&le)[TcShape<TS, NP>::RPW],
                                         float (&lo)[TcShape<TS, NP>::RPW], float (&rs)[TcShape<TS, NP>::RPW])
 {
     using St = Store<TS>;
     using Sh = TcShape<TS, NP>;
     constexpr int REC = Sh::REC;
+    // FP16 multipliers are stored as theta * 2^e: the step runs on scaled values (theta^(2) and g
+    // times 2^e, exact), which gives the stored numbers of the unscaled step; the row sums and the
+    // theta^T operand stay scaled and the caller unscales the sums
+    constexpr bool SCALED = std::is_same<TS, __half>::value;
+    constexpr bool BF16 = std::is_same<TS, __nv_bfloat16>::value;
 #pragma unroll
     for (int i = 0; i < Sh::RPW; ++i) {
         const int rl = rb + i;
         const long long rr = r + rl;
         const float y = rec[rl * REC];
-        const f2 tc2 = Pair2<TS>::load(tcur + rl * kW + 2 * m, iscl);
-        const f2 tp2 = Pair2<TS>::load(tprv + rl * kW + 2 * m, iscl);
+        f2 tc2, tp2;
+        if constexpr (SCALED) {
+            tc2 = Pair2<TS>::load_scaled(tcur + rl * kW + 2 * m);
+            tp2 = Pair2<TS>::load_scaled(tprv + rl * kW + 2 * m);
+        } else {
+            tc2 = Pair2<TS>::load(tcur + rl * kW + 2 * m, iscl);
+            tp2 = Pair2<TS>::load(tprv + rl * kW + 2 * m, iscl);
+        }
         const f2 th2 = f2_fma(beta2, f2_sub(tc2, tp2), tc2);   // theta^(2)
-        const f2 g = f2_sub(f2_add(f2_make(y, y), ccol), f2_make(de[i], dd[i]));
+        f2 g = f2_sub(f2_add(f2_make(y, y), ccol), f2_make(de[i], dd[i]));
         const uint32_t h = SR ? hash_row(hcol, (uint32_t)rr) : 0u;
-        f2 sv = St::template round2<SR>(th2, g, ninvL2, invL, h, scl);   // Pi_{>=0}(theta^(2) - g/L)
+        f2 sv;   // Pi_{>=0}(theta^(2) - g/L) as stored
+        uint32_t bits = 0;
+        if constexpr (SCALED) {
+            g = f2_mul(g, scl2);
+            sv = St::template round2_scaled<SR>(th2, g, ninvL2, h, bits);
+        } else if constexpr (BF16) {
+            sv = St::template round2_bits<SR>(th2, g, ninvL2, h, bits);
+        } else {
+            sv = St::template round2<SR>(th2, g, ninvL2, invL, h, scl);
+        }
         if (MASK) {
             float s0, s1;
             f2_split(sv, s0, s1);
@@ -410,10 +439,12 @@ __device__ __forceinline__ void tc_rows(const TS *tcur, const TS *tprv, const fl
             if (!vr || !vb || col0 + 1 == rr) s1 = 0.0f;
             sv = f2_make(s0, s1);
             if (va && vr) Pair2<TS>::store(nrow + i * ld, sv);
+        } else if constexpr (SCALED || BF16) {
+            Pair2<TS>::store_bits(nrow + i * ld, bits);
         } else {
             Pair2<TS>::store(nrow + i * ld, sv);
         }
-        const f2 vv = St::decoded2(sv, iscl2);
+        const f2 vv = SCALED ? sv : St::decoded2(sv, iscl2);
         float v0, v1;
         f2_split(vv, v0, v1);
         rs[i] = v0 + v1;
@@ -742,6 +773,9 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
         const float invL = P.invL;
         const float scl = P.st_scale, iscl = P.st_inv_scale;
         const f2 beta2 = f2_make(beta, beta), ninvL2 = f2_make(-invL, -invL), iscl2 = f2_make(iscl, iscl);
+        const f2 scl2 = f2_make(scl, scl);
+        // FP16 row sums and D2 come out scaled by 2^e (tc_rows): unscaled where they are stored
+        const float osc = std::is_same<TS, __half>::value ? iscl : 1.0f;
         const bool sr = P.sr != 0;
         const uint32_t rseed = P.seed ^ (uint32_t)ell * 0x632BE5ABu;
         TS *__restrict__ nxt = (TS *)P.theta[p];
@@ -826,20 +860,20 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
                     if (sr) {
                         if (fast)
                             tc_rows<TS, NP, true, false>(tcur, tprv, rec, rb, m, r, r1, col0, va, vb, ccol, de, dd,
-                                                         beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nrow, ld, ae, ao,
+                                                         beta2, ninvL2, invL, hcol, scl, iscl, iscl2, scl2, nrow, ld, ae, ao,
                                                          le, lo, rs);
                         else
                             tc_rows<TS, NP, true, true>(tcur, tprv, rec, rb, m, r, r1, col0, va, vb, ccol, de, dd,
-                                                        beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nrow, ld, ae, ao,
+                                                        beta2, ninvL2, invL, hcol, scl, iscl, iscl2, scl2, nrow, ld, ae, ao,
                                                         le, lo, rs);
                     } else {
                         if (fast)
                             tc_rows<TS, NP, false, false>(tcur, tprv, rec, rb, m, r, r1, col0, va, vb, ccol, de, dd,
-                                                          beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nrow, ld, ae,
+                                                          beta2, ninvL2, invL, hcol, scl, iscl, iscl2, scl2, nrow, ld, ae,
                                                           ao, le, lo, rs);
                         else
                             tc_rows<TS, NP, false, true>(tcur, tprv, rec, rb, m, r, r1, col0, va, vb, ccol, de, dd,
-                                                         beta2, ninvL2, invL, hcol, scl, iscl, iscl2, nrow, ld, ae, ao,
+                                                         beta2, ninvL2, invL, hcol, scl, iscl, iscl2, scl2, nrow, ld, ae, ao,
                                                          le, lo, rs);
                     }
                     // theta^T for MMA2 (column k of A = stage row)
@@ -861,7 +895,7 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
                     mbar_arrive(&B.a2full[b]);
                     mbar_arrive(&empty[slot]);
                 }
-                tc_flush_rows(rs, r + rb, ok ? r1 : r, rp, P.Q, lane, &B.rowx[wg][k & 1][0][0], q, wg);
+                tc_flush_rows(rs, r + rb, ok ? r1 : r, rp, P.Q, lane, &B.rowx[wg][k & 1][0][0], q, wg, osc);
                 // the previous D2 chunk (its MMAs had a stage to finish), then mark this one
                 if (pending) {
                     flush_d2(pch);
@@ -887,8 +921,8 @@ __device__ void phase_pair_tc(const Params &P, long long ell, unsigned char *sme
 #pragma unroll
                 for (int j = 0; j < H2; ++j) {
                     const int kk = h0 + j;
-                    if (kk == n) st_keep(cp, d2acc[j], keep);
-                    else if (kk < NP) st_keep(cp + (1 + kk) * kW, kk < n ? d2acc[j] : 0.0f, keep);
+                    if (kk == n) st_keep(cp, d2acc[j] * osc, keep);
+                    else if (kk < NP) st_keep(cp + (1 + kk) * kW, kk < n ? d2acc[j] * osc : 0.0f, keep);
                 }
             }
             u += r1 - r0;
