@@ -82,8 +82,14 @@ k_adj_pass(const BwdParamsT<T> B)
 {
     constexpr int K1 = NP + 1;
     constexpr bool F64 = std::is_same<T, double>::value;
-    // FP32: the 8 warps' column sums meet in shared memory; FP64: each warp adds its own
-    __shared__ float red[F64 ? 1 : 8][F64 ? 1 : K1][F64 ? 1 : kBCols];
+    // FP32: the row terms and the column terms of a task meet in shared memory (dynamic,
+    // bwd_smem_bytes): rowbuf holds kBRows x K1 items of 32 lane partials, item e's value of
+    // lane l at e * 32 + (l ^ (e & 31)) so that neither the lanes' stores nor the one-thread-per-
+    // item sums conflict on a bank; red holds the 8 warps' column partials [8][K1][kBCols].
+    // FP64: warp sums and one atomic per term, as before.
+    extern __shared__ float bsm[];
+    float *rowbuf = bsm;
+    float *red = bsm + kBRows * K1 * 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long N = B.N, ld = B.ld;
     const int REC = B.REC;
@@ -173,10 +179,19 @@ k_adj_pass(const BwdParamsT<T> B)
                 }
             }
             if (PASS == 2 && vec_ok) Vec4Of<T>::store(B.outb + r * ld + col0, outv);
+            if constexpr (F64) {
 #pragma unroll
-            for (int k = 0; k < K1; ++k) {
-                const T t = warp_sum(racc[k]);
-                if (lane == 0 && (PASS == 1 || k > 0) && t != (T)0) atomicAdd(B.acc_row + r * K1 + k, (double)t);
+                for (int k = 0; k < K1; ++k) {
+                    const T t = warp_sum(racc[k]);
+                    if (lane == 0 && (PASS == 1 || k > 0) && t != (T)0) atomicAdd(B.acc_row + r * K1 + k, (double)t);
+                }
+            } else {
+                const int rl = (int)(r - r0);
+#pragma unroll
+                for (int k = 0; k < K1; ++k) {
+                    const int e = rl * K1 + k;
+                    rowbuf[e * 32 + (lane ^ (e & 31))] = racc[k];
+                }
             }
         }
         const int kmax = PASS == 1 ? K1 : 1;
@@ -193,13 +208,25 @@ k_adj_pass(const BwdParamsT<T> B)
 #pragma unroll
             for (int j = 0; j < 4; ++j)
 #pragma unroll
-                for (int k = 0; k < K1; ++k) red[warp][k][lane * 4 + j] = cacc[j][k];
+                for (int k = 0; k < K1; ++k) red[(warp * K1 + k) * kBCols + lane * 4 + j] = cacc[j][k];
             __syncthreads();
+            // row sums: one thread per (row, term) item adds the 32 lane partials
+            const int nitem = (int)(r1 - r0) * K1;
+            for (int e = threadIdx.x; e < nitem; e += 256) {
+                const int rl = e / K1, k = e - rl * K1;
+                if (PASS == 2 && k == 0) continue;   // pass 2 has no row term 0
+                const float *it = rowbuf + e * 32;
+                const int sw = e & 31;
+                float a = 0.0f;
+#pragma unroll
+                for (int l = 0; l < 32; ++l) a += it[l ^ sw];
+                if (a != 0.0f) atomicAdd(B.acc_row + (r0 + rl) * K1 + k, (double)a);
+            }
             for (int e = threadIdx.x; e < K1 * kBCols; e += 256) {
                 const int k = e / kBCols, cl = e % kBCols;
                 float a = 0.0f;
 #pragma unroll
-                for (int w = 0; w < 8; ++w) a += red[w][k][cl];
+                for (int w = 0; w < 8; ++w) a += red[(w * K1 + k) * kBCols + cl];
                 const long long c = stripe * kBCols + cl;
                 if (c < N && k < kmax && a != 0.0f) atomicAdd(B.acc_col + c * K1 + k, (double)a);
             }
@@ -264,16 +291,24 @@ k_adj_fold(const BwdParamsT<T> B)
 
 struct BwdKernels {
     const void *pass1, *pass2, *fold1, *fold2;
+    size_t smem;   // dynamic shared memory of the passes
 };
+
+// dynamic shared memory of k_adj_pass: the FP32 row items and column partials, none in FP64
+template <typename T, int NP> constexpr size_t bwd_smem_bytes()
+{
+    return std::is_same<T, double>::value ? 0 : (size_t)(kBRows * 32 + 8 * kBCols) * (NP + 1) * sizeof(float);
+}
 
 // reverse mode is compiled for n <= 10 (padded widths 2, 4, 5, 8, 10), FP32 or FP64 multipliers
 template <typename TS, int NP> BwdKernels make_bwd()
 {
     if constexpr (NP <= 10 && (std::is_same<TS, float>::value || std::is_same<TS, double>::value))
         return BwdKernels{(const void *)k_adj_pass<TS, NP, 1>, (const void *)k_adj_pass<TS, NP, 2>,
-                          (const void *)k_adj_fold<TS, NP, 1>, (const void *)k_adj_fold<TS, NP, 2>};
+                          (const void *)k_adj_fold<TS, NP, 1>, (const void *)k_adj_fold<TS, NP, 2>,
+                          bwd_smem_bytes<TS, NP>()};
     else
-        return BwdKernels{nullptr, nullptr, nullptr, nullptr};
+        return BwdKernels{nullptr, nullptr, nullptr, nullptr, 0};
 }
 
 }  // namespace crk

@@ -1589,6 +1589,11 @@ static cr_status backward_impl(cr_handle h, const float *dL_dyhat, float *dL_dyb
     const long long S128 = (N + crk::kBCols - 1) / crk::kBCols;
     const long long ntask = S128 * ((N + crk::kBRows - 1) / crk::kBRows);
     const int gpass = (int)std::min<long long>(ntask, (long long)h->num_sms * 8);
+    const size_t bsm = h->ks.bwd.smem;
+    if (bsm > 0) {
+        CR_CUDA(h, cudaFuncSetAttribute(h->ks.bwd.pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
+        CR_CUDA(h, cudaFuncSetAttribute(h->ks.bwd.pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
+    }
     const int gfold = (int)std::max<long long>(1, std::min<long long>((N + 255) / 256, (long long)h->num_sms * 8));
     const long long nseg = (K + k - 1) / k;
     cr_status status = CR_OK;
@@ -1669,9 +1674,9 @@ static cr_status backward_impl(cr_handle h, const float *dL_dyhat, float *dL_dyb
             B.ccolb_out = ccolb;
             B.xib_out = xib;
             void *args[] = {&B};
-            CR_CUDA(h, cudaLaunchKernel(h->ks.bwd.pass1, dim3(gpass), dim3(256), args, 0, h->stream));
+            CR_CUDA(h, cudaLaunchKernel(h->ks.bwd.pass1, dim3(gpass), dim3(256), args, bsm, h->stream));
             CR_CUDA(h, cudaLaunchKernel(h->ks.bwd.fold1, dim3(gfold), dim3(256), args, 0, h->stream));
-            CR_CUDA(h, cudaLaunchKernel(h->ks.bwd.pass2, dim3(gpass), dim3(256), args, 0, h->stream));
+            CR_CUDA(h, cudaLaunchKernel(h->ks.bwd.pass2, dim3(gpass), dim3(256), args, bsm, h->stream));
             CR_CUDA(h, cudaLaunchKernel(h->ks.bwd.fold2, dim3(gfold), dim3(256), args, 0, h->stream));
         }
     }
