@@ -1555,8 +1555,8 @@ static cr_status backward_impl(cr_handle h, const float *dL_dyhat, float *dL_dyb
     std::vector<T *> segTh(k + 1), segRec(k), segCcol(k), segXi(k);
     std::vector<double *> segV(k + 2), segMu(k + 2);
     T *bb[2], *yb2, *ccolb, *xib;
-    double *mub[2], *acc_row, *acc_col, *ybar_acc, *X_acc;
-    bool ok = true;
+    double *mub[2], *acc_row, *acc_col, *ybar_acc, *X_acc, *segBeta;
+    bool ok = al((void **)&segBeta, sizeof(double) * k);
     for (long long i = 0; i <= k && ok; ++i) ok = al((void **)&segTh[i], thb);
     for (long long i = 0; i < k && ok; ++i)
         ok = al((void **)&segRec[i], sizeof(T) * N * REC) && al((void **)&segCcol[i], sizeof(T) * N) &&
@@ -1622,9 +1622,16 @@ static cr_status backward_impl(cr_handle h, const float *dL_dyhat, float *dL_dyb
             CR_CUDA(h, cudaMemcpyAsync(segXi[q - 1], xi2, sizeof(T) * N * NP, cudaMemcpyDeviceToDevice, h->stream));
             CR_CUDA(h, cudaMemcpyAsync(segV[q + 1], h->P.v[ell & 1], sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
             CR_CUDA(h, cudaMemcpyAsync(segMu[q + 1], h->P.mu[ell & 1], sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+            // the momentum weight of this iteration, read back once per segment
+            CR_CUDA(h, cudaMemcpyAsync(segBeta + (q - 1), &h->P.st->scal[ell & 1].beta, sizeof(double),
+                                       cudaMemcpyDeviceToDevice, h->stream));
+        }
+        {
+            std::vector<double> hb((size_t)(e - c));
+            CR_CUDA(h, cudaMemcpyAsync(hb.data(), segBeta, sizeof(double) * (e - c), cudaMemcpyDeviceToHost, h->stream));
             DevState st;
-            CR_TRY(read_state(h, &st));
-            beta[ell] = st.scal[ell & 1].beta;
+            CR_TRY(read_state(h, &st));   // synchronizes the stream and checks the recompute's error flag
+            for (long long ell = c + 1; ell <= e; ++ell) beta[ell] = hb[(size_t)(ell - c - 1)];
         }
         // reverse the segment
         for (long long ell = e; ell > c; --ell) {
