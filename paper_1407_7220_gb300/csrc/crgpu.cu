@@ -257,8 +257,10 @@ double max_block_eig(const std::vector<double> &X, long long N, int n)
     for (long long l = 0; l < N; ++l)
         for (int i = 0; i < n; ++i) {
             const double di = X[(size_t)l * n + i] - mean[i];
-            for (int j = 0; j < n; ++j) cov[(size_t)i * n + j] += di * (X[(size_t)l * n + j] - mean[j]);
+            for (int j = i; j < n; ++j) cov[(size_t)i * n + j] += di * (X[(size_t)l * n + j] - mean[j]);
         }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < i; ++j) cov[(size_t)i * n + j] = cov[(size_t)j * n + i];   // the same sums
     for (double &c : cov) c /= (double)N;
     sym_eig(cov, V, n);
     std::vector<double> lam(n), z(n);
@@ -267,8 +269,12 @@ double max_block_eig(const std::vector<double> &X, long long N, int n)
         lam[i] = cov[(size_t)i * n + i];
         lmax = std::max(lmax, lam[i]);
     }
-    double best = 0.0;
-    for (long long l = 0; l < N; ++l) {
+    // The bisection only shrinks the bracket, so N (lmax + ||z||^2) bounds a point's result from
+    // above; ||z|| = ||xbar - x_l|| (Q is orthogonal), taken directly and enlarged by 1e-12 to
+    // cover its rounding.  The point with the largest bound is solved first, then every point
+    // whose bound reaches the largest root found so far: the maximum is the same, bit for bit,
+    // as over every point.
+    auto zvec = [&](long long l) {
         double zz = 0.0;
         for (int i = 0; i < n; ++i) {
             double s = 0.0;
@@ -276,6 +282,24 @@ double max_block_eig(const std::vector<double> &X, long long N, int n)
             z[i] = s;
             zz += s * s;
         }
+        return zz;
+    };
+    std::vector<double> zzs((size_t)N);
+    long long l0 = 0;
+    for (long long l = 0; l < N; ++l) {
+        double dd = 0.0;
+        for (int k = 0; k < n; ++k) {
+            const double d = mean[k] - X[(size_t)l * n + k];
+            dd += d * d;
+        }
+        zzs[(size_t)l] = dd * (1.0 + 1e-12);
+        if (zzs[(size_t)l] > zzs[(size_t)l0]) l0 = l;
+    }
+    double best = 0.0;
+    for (long long j = -1; j < N; ++j) {
+        const long long l = j < 0 ? l0 : j;
+        if ((j >= 0 && l == l0) || (double)N * (lmax + zzs[(size_t)l]) < best) continue;
+        const double zz = zvec(l);
         double lo = lmax, hi = lmax + zz;
         for (int it = 0; it < 200 && hi > lo; ++it) {
             const double mid = 0.5 * (lo + hi);

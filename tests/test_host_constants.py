@@ -41,3 +41,28 @@ def test_bad_inputs_are_rejected(built):
         with pytest.raises(crg.CrError) as e:
             crg.problem_constants(*args)
         assert e.value.status == crg.CR_EINVAL
+
+
+@pytest.mark.parametrize("case", ["anisotropic", "ties", "one_far_point"])
+def test_largest_block_found_where_it_is_not_the_farthest_point(built, case):
+    # ||A_2||^2 = max over points of the largest eigenvalue of their block.  The library bounds
+    # each point's value by N (lambda_max(cov) + ||x_l - xbar||^2) and solves the secular
+    # equation only where that bound reaches the best value so far; these layouts put the
+    # largest block away from the farthest point, or make several points tie.
+    rng = np.random.default_rng(11)
+    N, n = 240, 3
+    if case == "anisotropic":
+        X = np.clip(rng.normal(size=(N, n)) * np.array([4.0, 0.1, 0.1]), -7.0, 7.0)
+        X[0] = [0.0, 9.0, 0.0]        # farthest from the mean, along a thin axis
+        X[1] = [8.5, 0.0, 0.0]        # nearer, along the wide axis: the largest block
+        d = X - X.mean(axis=0)
+        lam = [np.linalg.eigvalsh(d.T @ d + N * np.outer(v, v))[-1] for v in d]
+        assert np.argmax(lam) == 1 and np.argmax((d * d).sum(axis=1)) == 0
+    elif case == "ties":
+        X = np.repeat(rng.uniform(-1, 1, size=(N // 4, n)), 4, axis=0)
+    else:
+        X = rng.uniform(-1, 1, size=(N, n))
+        X[17] = [40.0, -3.0, 5.0]
+    yb = rng.normal(size=N)
+    c = crg.problem_constants(X, yb, 0.1)
+    assert c["sigma2_A2"] == pytest.approx(A.sigma2_A2(X), rel=1e-10)
