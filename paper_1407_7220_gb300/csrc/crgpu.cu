@@ -1558,6 +1558,49 @@ cr_status cr_profile(cr_handle h, int32_t kind, double *ms, int64_t *launches)
 
 }  // extern "C"
 
+// The FP32 multiplier arrays' tensor map (the same box and options as at creation) for another
+// array of the same shape, used by the reverse mode's segment recompute.
+static cr_status encode_theta_map(cr_ctx *h, CUtensorMap *m, const void *base)
+{
+    auto encode = tensor_map_encoder();
+    if (!encode) return fail(h, CR_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    cuuint64_t gdim[2] = {(cuuint64_t)h->N, (cuuint64_t)h->N};
+    cuuint64_t gstride[1] = {(cuuint64_t)h->ld * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)crk::kW, (cuuint32_t)crk::kRS};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), gdim, gstride, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, CR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return CR_OK;
+}
+
+// Puts back the multiplier pointers and tensor maps of a handle when the recompute ends, on the
+// error paths too.
+struct ThetaViewGuard {
+    cr_ctx *h;
+    void *saved_theta[2];
+    CUtensorMap saved_map[2];
+    bool active = true;
+    explicit ThetaViewGuard(cr_ctx *hh) : h(hh)
+    {
+        for (int b = 0; b < 2; ++b) {
+            saved_theta[b] = h->P.theta[b];
+            saved_map[b] = h->P.tmap[b];
+        }
+    }
+    void restore()
+    {
+        if (!active) return;
+        for (int b = 0; b < 2; ++b) {
+            h->P.theta[b] = saved_theta[b];
+            h->P.tmap[b] = saved_map[b];
+        }
+        active = false;
+    }
+    ~ThetaViewGuard() { restore(); }
+};
+
 // Reverse mode over FP32 (T = float) or FP64 (T = double) multipliers: the saved forward data of
 // every recomputed iteration (multipliers, row records, column data) have the storage type.
 template <typename T>
@@ -1631,11 +1674,24 @@ static cr_status backward_impl(cr_handle h, const float *dL_dyhat, float *dL_dyb
         CR_CUDA(h, cudaMemcpyAsync(segMu[0], h->P.mu[(c + 1) & 1], sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
         CR_CUDA(h, cudaMemcpyAsync(segV[1], h->P.v[c & 1], sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
         CR_CUDA(h, cudaMemcpyAsync(segMu[1], h->P.mu[c & 1], sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
-        // recompute the segment (bit for bit: same kernels, same partition, same rounding seeds)
+        // recompute the segment (bit for bit: same kernels, same partition, same rounding seeds).
+        // FP32: the pass loads theta1_{l-1} and theta1_{l-2} through the tensor maps of
+        // P.theta[(l + 1) & 1] and P.theta[l & 1] and stores theta1_l through the pointer
+        // P.theta[l & 1], so the maps are pointed at the segment's entries q and q - 1 and the
+        // pointer at entry q + 1: the iteration writes its result where the reverse steps read it
+        // (the FP64 pass reads and writes its arrays in place and copies instead)
+        ThetaViewGuard guard(h);
         for (long long ell = c + 1; ell <= e; ++ell) {
-            CR_TRY(run_iters(h, 1));
             const long long q = ell - c;
-            if (ell < e)
+            if constexpr (!F64) {
+                const int p = (int)(ell & 1), cc = 1 - p;
+                CR_TRY(encode_theta_map(h, &h->P.tmap[cc], segTh[q]));
+                CR_TRY(encode_theta_map(h, &h->P.tmap[p], segTh[q - 1]));
+                h->P.theta[cc] = segTh[q];
+                h->P.theta[p] = ell < e ? (void *)segTh[q + 1] : guard.saved_theta[p];
+            }
+            CR_TRY(run_iters(h, 1));
+            if (F64 && ell < e)
                 CR_CUDA(h, cudaMemcpyAsync(segTh[q + 1], h->P.theta[ell & 1], thb, cudaMemcpyDeviceToDevice, h->stream));
             // the row and column data this iteration's pair pass read (FP64 copies for FP64 multipliers)
             const void *rec = F64 ? (const void *)h->P.rec64 : (const void *)h->P.rowrec;
@@ -1650,6 +1706,7 @@ static cr_status backward_impl(cr_handle h, const float *dL_dyhat, float *dL_dyb
             CR_CUDA(h, cudaMemcpyAsync(segBeta + (q - 1), &h->P.st->scal[ell & 1].beta, sizeof(double),
                                        cudaMemcpyDeviceToDevice, h->stream));
         }
+        guard.restore();
         {
             std::vector<double> hb((size_t)(e - c));
             CR_CUDA(h, cudaMemcpyAsync(hb.data(), segBeta, sizeof(double) * (e - c), cudaMemcpyDeviceToHost, h->stream));
