@@ -1652,7 +1652,6 @@ static cr_status backward_impl(cr_handle h, const float *dL_dyhat, float *dL_dyb
     fin.full = true;
     CR_TRY(ckpt_save(h, fin));
     std::vector<double> beta(K + 3, 0.0);
-    const int prev_driver = h->opt.driver;
     const long long S128 = (N + crk::kBCols - 1) / crk::kBCols;
     const long long ntask = S128 * ((N + crk::kBRows - 1) / crk::kBRows);
     const int gpass = (int)std::min<long long>(ntask, (long long)h->num_sms * 8);
@@ -1768,7 +1767,6 @@ static cr_status backward_impl(cr_handle h, const float *dL_dyhat, float *dL_dyb
             CR_CUDA(h, cudaLaunchKernel(h->ks.bwd.fold2, dim3(gfold), dim3(256), args, 0, h->stream));
         }
     }
-    h->opt.driver = prev_driver;
     {
         long long NN = N;
         int nn = n;
