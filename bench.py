@@ -168,6 +168,7 @@ def run_reference(args):
 TRAFFIC_BYTES_PER_PAIR = {
     ("cuda_cores", "f32", 10): (517.621504e6 + 221.631232e6) / (8000 * 7999),
     ("tensor_cores", "bf16", 20): (593.554432e6 + 253.502976e6) / (12000 * 11999),
+    ("tensor_cores", "f16", 20): (593.816576e6 + 253.565952e6) / (12000 * 11999),
 }
 
 
