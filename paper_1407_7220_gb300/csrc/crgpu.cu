@@ -1575,12 +1575,13 @@ static cr_status encode_theta_map(cr_ctx *h, CUtensorMap *m, const void *base)
     return CR_OK;
 }
 
-// Puts back the multiplier pointers and tensor maps of a handle when the recompute ends, on the
-// error paths too.
+// Puts back the multiplier pointers, their tensor maps and the row / column record pointers of a
+// handle when the recompute ends, on the error paths too.
 struct ThetaViewGuard {
     cr_ctx *h;
     void *saved_theta[2];
     CUtensorMap saved_map[2];
+    float *saved_rowrec, *saved_ccol2, *saved_xi2;
     bool active = true;
     explicit ThetaViewGuard(cr_ctx *hh) : h(hh)
     {
@@ -1588,6 +1589,9 @@ struct ThetaViewGuard {
             saved_theta[b] = h->P.theta[b];
             saved_map[b] = h->P.tmap[b];
         }
+        saved_rowrec = h->P.rowrec;
+        saved_ccol2 = h->P.ccol2;
+        saved_xi2 = h->P.xi2;
     }
     void restore()
     {
@@ -1596,6 +1600,9 @@ struct ThetaViewGuard {
             h->P.theta[b] = saved_theta[b];
             h->P.tmap[b] = saved_map[b];
         }
+        h->P.rowrec = saved_rowrec;
+        h->P.ccol2 = saved_ccol2;
+        h->P.xi2 = saved_xi2;
         active = false;
     }
     ~ThetaViewGuard() { restore(); }
@@ -1639,6 +1646,9 @@ static cr_status backward_impl(cr_handle h, const float *dL_dyhat, float *dL_dyb
         (void)cudaGetLastError();
         return fail(h, CR_ENOMEM, "reverse-mode workspace allocation failed");
     }
+    if constexpr (!F64)   // the constant X columns of the row records the recompute writes into
+        for (long long i = 0; i < k; ++i)
+            CR_CUDA(h, cudaMemcpyAsync(segRec[i], h->P.rowrec, sizeof(T) * N * REC, cudaMemcpyDeviceToDevice, h->stream));
     CR_CUDA(h, cudaMemsetAsync(acc_row, 0, sizeof(double) * N * K1, h->stream));
     CR_CUDA(h, cudaMemsetAsync(acc_col, 0, sizeof(double) * N * K1, h->stream));
     CR_CUDA(h, cudaMemsetAsync(ybar_acc, 0, sizeof(double) * N, h->stream));
@@ -1688,17 +1698,21 @@ static cr_status backward_impl(cr_handle h, const float *dL_dyhat, float *dL_dyb
                 CR_TRY(encode_theta_map(h, &h->P.tmap[p], segTh[q - 1]));
                 h->P.theta[cc] = segTh[q];
                 h->P.theta[p] = ell < e ? (void *)segTh[q + 1] : guard.saved_theta[p];
+                // foldB writes the row and column data the pair pass reads straight into the
+                // segment's entry (the X columns of its row records were filled once)
+                h->P.rowrec = segRec[q - 1];
+                h->P.ccol2 = segCcol[q - 1];
+                h->P.xi2 = segXi[q - 1];
             }
             CR_TRY(run_iters(h, 1));
-            if (F64 && ell < e)
-                CR_CUDA(h, cudaMemcpyAsync(segTh[q + 1], h->P.theta[ell & 1], thb, cudaMemcpyDeviceToDevice, h->stream));
-            // the row and column data this iteration's pair pass read (FP64 copies for FP64 multipliers)
-            const void *rec = F64 ? (const void *)h->P.rec64 : (const void *)h->P.rowrec;
-            const void *ccol = F64 ? (const void *)h->P.ccol2_64 : (const void *)h->P.ccol2;
-            const void *xi2 = F64 ? (const void *)h->P.xi2_64 : (const void *)h->P.xi2;
-            CR_CUDA(h, cudaMemcpyAsync(segRec[q - 1], rec, sizeof(T) * N * REC, cudaMemcpyDeviceToDevice, h->stream));
-            CR_CUDA(h, cudaMemcpyAsync(segCcol[q - 1], ccol, sizeof(T) * N, cudaMemcpyDeviceToDevice, h->stream));
-            CR_CUDA(h, cudaMemcpyAsync(segXi[q - 1], xi2, sizeof(T) * N * NP, cudaMemcpyDeviceToDevice, h->stream));
+            if constexpr (F64) {
+                if (ell < e)
+                    CR_CUDA(h, cudaMemcpyAsync(segTh[q + 1], h->P.theta[ell & 1], thb, cudaMemcpyDeviceToDevice, h->stream));
+                // the row and column data this iteration's pair pass read (the FP64 copies)
+                CR_CUDA(h, cudaMemcpyAsync(segRec[q - 1], h->P.rec64, sizeof(T) * N * REC, cudaMemcpyDeviceToDevice, h->stream));
+                CR_CUDA(h, cudaMemcpyAsync(segCcol[q - 1], h->P.ccol2_64, sizeof(T) * N, cudaMemcpyDeviceToDevice, h->stream));
+                CR_CUDA(h, cudaMemcpyAsync(segXi[q - 1], h->P.xi2_64, sizeof(T) * N * NP, cudaMemcpyDeviceToDevice, h->stream));
+            }
             CR_CUDA(h, cudaMemcpyAsync(segV[q + 1], h->P.v[ell & 1], sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
             CR_CUDA(h, cudaMemcpyAsync(segMu[q + 1], h->P.mu[ell & 1], sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
             // the momentum weight of this iteration, read back once per segment
